@@ -1,0 +1,167 @@
+/*
+ * mpspt.h — C ABI of the GB300 MPS-PT library.
+ *
+ * MPS-PT (Sharma & Chan, "A flexible multi-reference perturbation theory by
+ * minimizing the Hylleraas functional with matrix product states") obtains
+ * the second-order energy E2 as the minimum of the Hylleraas functional
+ *     H[Psi1] = <Psi1|H0 - E0|Psi1> + 2 <Psi1|Q V|Psi0>            (Eq. 1)
+ * over matrix product states Psi1 (Eq. 3) of bond dimension M, by a two-site
+ * DMRG-like sweep whose local step solves the linear equation of Fig. 1C by
+ * conjugate gradient; E3 follows from Psi1 by Wigner's 2n+1 rule (Eq. 5).
+ *
+ * Conventions shared by every call:
+ *  - spatial orbitals p = 0..k-1, k = k_act + k_virt; active orbitals first,
+ *    then virtual orbitals; no core orbitals;
+ *  - one MPS site per spatial orbital, local basis |0>,|a>,|b>,|ab> (codes
+ *    0..3), many-body states are creators in ascending spin-orbital order
+ *    (p0a, p0b, p1a, ...) applied to the vacuum;
+ *  - quantum numbers (N, 2Sz); a bond index carries the QN of the part of the
+ *    chain to its left;
+ *  - Psi1 lies in the space X of determinants with one or two electrons in
+ *    virtual orbitals, so Q acts as the identity on it and -QV Psi0 = -P_X H Psi0.
+ *
+ * Error behaviour: no call throws or aborts across the ABI.  On error the
+ * output arguments are left untouched and the status says why;
+ * mpspt_status_string() gives a message.  All device work is ordered on the
+ * stream given in mpspt_options (0 = the legacy default stream); every call
+ * returns only after its host-visible results are final.
+ * Ownership: input arrays are copied, the caller keeps them.  Handles
+ * (mpspt_ctx, mpspt_mps) are owned by the caller and released with
+ * mpspt_destroy / mpspt_mps_free.
+ */
+#ifndef MPSPT_H
+#define MPSPT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpspt_ctx mpspt_ctx;
+typedef struct mpspt_mps mpspt_mps;
+
+typedef enum {
+    MPSPT_OK = 0,
+    MPSPT_ERR_INVALID = -1,        /* bad argument or NaN/Inf in an input     */
+    MPSPT_ERR_OOM = -2,            /* device memory exhausted / arena cap hit */
+    MPSPT_ERR_NOT_SPD = -3,        /* CG met p^T A p <= 0 (H0 - E0 not > 0)   */
+    MPSPT_ERR_NOT_CONVERGED = -4,  /* CG or sweep iteration cap reached       */
+    MPSPT_ERR_TIMEOUT = -5,        /* a bounded device wait gave up           */
+    MPSPT_ERR_CUDA = -6,           /* a CUDA runtime call failed              */
+    MPSPT_ERR_STATE = -7           /* call out of order (e.g. no integrals)   */
+} mpspt_status;
+
+/* Zeroth-order Hamiltonian.  DYALL: H_act + sum_a eps_a n_a (NEVPT-type,
+ * E0 = <Psi0|H_act|Psi0>, E1 = 0).  FOCK: sum_tu f_tu E_tu + sum_a eps_a n_a
+ * (CASPT2-type one-body Fock operator between many-body projectors; E0 =
+ * sum f_tu gamma_tu).  eps_a are the eigenvalues of the generalised Fock
+ * matrix in the virtual block (semicanonical virtuals). */
+typedef enum { MPSPT_H0_FOCK = 0, MPSPT_H0_DYALL = 1 } mpspt_h0;
+
+/* Arithmetic of the local solver.  FP64: every contraction in float64.
+ * FP32: contractions in float32, CG vectors float64, final energy float64.
+ * MIXED_BF16: sigma contractions as three-term split-bfloat16 products on
+ * the tensor cores with float32 accumulation inside a float64-refined CG;
+ * the residual and the Hylleraas value are evaluated in float64. */
+typedef enum { MPSPT_FP64 = 0, MPSPT_FP32 = 1, MPSPT_MIXED_BF16 = 2 } mpspt_prec;
+
+typedef struct {
+    int device;                 /* CUDA device ordinal                          */
+    void* stream;               /* cudaStream_t, 0 = default stream             */
+    mpspt_prec prec;
+    int max_sweeps;             /* full (left->right->left) sweeps, <= 64       */
+    double e_tol;               /* |E2(sweep n) - E2(sweep n-1)| stop criterion */
+    double cg_tol;              /* relative residual |r| <= cg_tol |g|          */
+    int cg_max_iter;            /* per local solve                              */
+    unsigned long long seed;    /* initial Psi1 (counter-based, see below)      */
+    int use_learned;            /* learned block preconditioner (0 = Jacobi)    */
+    int verbose;                /* 1: one line per sweep on stderr              */
+} mpspt_options;
+
+typedef struct {
+    int n_sweeps;
+    double e2_per_sweep[64];
+    double max_discarded_weight; /* over the last sweep                          */
+    long long cg_iters;          /* total CG iterations (all local solves)       */
+    long long sigma_calls;       /* applications of A_loc (any precision)        */
+    double sigma_flops;          /* algorithmic flops of those applications      */
+    double sigma_ms;             /* device time inside them (CUDA events)        */
+    double wall_ms;              /* wall time of the minimisation                */
+    int max_bond_dim;
+} mpspt_report;
+
+/* Fills *opt with defaults: device 0, default stream, FP64, 30 sweeps,
+ * e_tol 1e-10, cg_tol 1e-10, 1000 CG iterations, seed 1408. */
+void mpspt_default_options(mpspt_options* opt);
+
+/* Creates a context bound to opt->device.  *ctx owned by the caller. */
+mpspt_status mpspt_create(mpspt_ctx** ctx, const mpspt_options* opt);
+void mpspt_destroy(mpspt_ctx* ctx);   /* frees everything the context owns */
+
+/* Integrals (host float64, copied).  h: k*k row-major symmetric one-electron
+ * integrals; L: n_chol*k*k with (pq|rs) = sum_Q L[Q,p,q] L[Q,r,s] (the form
+ * of Eq. 1's H = H0 + V before partitioning).  n_elec active electrons
+ * (even; the reference is a singlet with Sz = 0). */
+mpspt_status mpspt_set_integrals(mpspt_ctx* ctx, int k_act, int k_virt, int n_elec,
+                                 const double* h, const double* L, int n_chol);
+
+/* Reference Psi0 (Eq. 1) as a dense host vector over the 4^k_act active
+ * occupation strings (index = sum_p code_p 4^(k_act-1-p)), copied.  The
+ * library computes gamma_tu, the generalised Fock matrix, rotates the
+ * virtual orbitals to the semicanonical basis and converts Psi0 to an exact
+ * MPS.  Requires mpspt_set_integrals.  n_ci must equal 4^k_act. */
+mpspt_status mpspt_set_reference(mpspt_ctx* ctx, const double* ci, long long n_ci);
+
+/* E0 = <Psi0|H0|Psi0>, E1 = <Psi0|V|Psi0> = E_ref - E0 and E_ref =
+ * <Psi0|H|Psi0> for the chosen H0 (Eqs. 1, 5).  Any output may be NULL. */
+mpspt_status mpspt_energies(mpspt_ctx* ctx, mpspt_h0 h0, double* e0, double* e1,
+                            double* e_ref);
+
+/* The hot path: minimises Eq. 1 over MPS of bond dimension <= M with the
+ * two-site sweep (paper: "the standard DMRG sweep algorithm ... instead of an
+ * eigenvalue problem, a linear equation is solved at each step").  Writes E2
+ * = the Hylleraas value of the last local step (float64; an upper bound to
+ * the uncontracted E2 when H0 - E0 > 0 on X).  If psi1 is not NULL, *psi1
+ * receives the final first-order MPS (free with mpspt_mps_free).  rep may be
+ * NULL.  Initial Psi1: see the sector rule and SplitMix64 values documented
+ * in the library source (seed from the options). */
+mpspt_status mpspt_minimize_hylleraas(mpspt_ctx* ctx, mpspt_h0 h0, int M, double* e2,
+                                      mpspt_mps** psi1, mpspt_report* rep);
+
+/* Eq. 5: E3 = <Psi1|V|Psi1> - E1 <Psi1|Psi1> with V = H - H0 (full
+ * Hamiltonian MPO restricted to X), by one transfer sweep. */
+mpspt_status mpspt_third_order(mpspt_ctx* ctx, mpspt_h0 h0, const mpspt_mps* psi1,
+                               double* e3);
+
+void mpspt_mps_free(mpspt_mps* mps);
+
+/* MPS exchange in a dense, QN-labelled form.  bond_dims[c], c = 0..nsite:
+ * bond dimensions (bond_dims[0] = bond_dims[nsite] = 1).  bond_qn: for every
+ * bond index of every cut in order, the pair (N, 2Sz); indices of one QN
+ * must be contiguous and sectors ascending in (N, 2Sz).  tensors[c]:
+ * bond_dims[c]*4*bond_dims[c+1] doubles, row-major (l, s, r); entries that
+ * violate QN conservation must be zero.  Import copies; export writes into
+ * caller buffers sized from mpspt_mps_shape(). */
+mpspt_status mpspt_mps_import(mpspt_ctx* ctx, int nsite, const int* bond_dims,
+                              const int* bond_qn, const double* const* tensors,
+                              mpspt_mps** out);
+mpspt_status mpspt_mps_shape(const mpspt_mps* mps, int* nsite, int* bond_dims);
+mpspt_status mpspt_mps_export(const mpspt_mps* mps, int* bond_qn, double* const* tensors);
+
+/* Local operators at bond (i, i+1) of a given Psi1 (the Fig. 1C terms): with
+ * environments of Psi1 built from both ends, and x a dense host two-site
+ * tensor (bond_dims[i]*16*bond_dims[i+2], row-major (l, s1, s2, r)):
+ *   MPSPT_LOCAL_SIGMA: out = A_loc x   (A_loc = projection of H0 - E0)
+ *   MPSPT_LOCAL_RHS:   out = g_loc     (projection of V Psi0; x ignored)
+ *   MPSPT_LOCAL_DIAG:  out = diag(A_loc) (Jacobi preconditioner)
+ * Entries outside the QN-allowed blocks are written as zero.  Uses the
+ * context's precision for SIGMA. */
+typedef enum { MPSPT_LOCAL_SIGMA = 0, MPSPT_LOCAL_RHS = 1, MPSPT_LOCAL_DIAG = 2 } mpspt_local_op;
+mpspt_status mpspt_local_apply(mpspt_ctx* ctx, mpspt_h0 h0, const mpspt_mps* psi1, int i,
+                               mpspt_local_op op, const double* x, double* out);
+
+const char* mpspt_status_string(mpspt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPSPT_H */

@@ -1,0 +1,205 @@
+"""ctypes binding of include/mpspt.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps.  Arrays are
+numpy float64 / int32 on the host; the library copies them.  The product path
+has no CPU fallback: if libmpspt.so is missing or no CUDA device is present,
+the calls fail.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpspt.so")
+
+MPSPT_OK = 0
+MPSPT_H0_FOCK = 0
+MPSPT_H0_DYALL = 1
+MPSPT_FP64 = 0
+MPSPT_FP32 = 1
+MPSPT_MIXED_BF16 = 2
+MPSPT_LOCAL_SIGMA = 0
+MPSPT_LOCAL_RHS = 1
+MPSPT_LOCAL_DIAG = 2
+H0 = {"fock": MPSPT_H0_FOCK, "dyall": MPSPT_H0_DYALL}
+PREC = {"fp64": MPSPT_FP64, "fp32": MPSPT_FP32, "mixed": MPSPT_MIXED_BF16}
+STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "NOT_SPD", -4: "NOT_CONVERGED",
+          -5: "TIMEOUT", -6: "CUDA", -7: "STATE"}
+
+
+class mpspt_options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("prec", ctypes.c_int),
+                ("max_sweeps", ctypes.c_int), ("e_tol", ctypes.c_double), ("cg_tol", ctypes.c_double),
+                ("cg_max_iter", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("use_learned", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class mpspt_report(ctypes.Structure):
+    _fields_ = [("n_sweeps", ctypes.c_int), ("e2_per_sweep", ctypes.c_double * 64),
+                ("max_discarded_weight", ctypes.c_double), ("cg_iters", ctypes.c_longlong),
+                ("sigma_calls", ctypes.c_longlong), ("sigma_flops", ctypes.c_double),
+                ("sigma_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
+                ("max_bond_dim", ctypes.c_int)]
+
+
+class MpsptError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"mpspt status {status} ({STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1408_5092_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "mpspt_default_options": (None, [ctypes.POINTER(mpspt_options)]),
+            "mpspt_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(mpspt_options)]),
+            "mpspt_destroy": (None, [vp]),
+            "mpspt_set_integrals": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]),
+            "mpspt_set_reference": (ctypes.c_int, [vp, dp, ctypes.c_longlong]),
+            "mpspt_energies": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, dp]),
+            "mpspt_minimize_hylleraas": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(vp),
+                                                        ctypes.POINTER(mpspt_report)]),
+            "mpspt_third_order": (ctypes.c_int, [vp, ctypes.c_int, vp, dp]),
+            "mpspt_mps_free": (None, [vp]),
+            "mpspt_mps_import": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(vp)]),
+            "mpspt_mps_shape": (ctypes.c_int, [vp, ip, ip]),
+            "mpspt_mps_export": (ctypes.c_int, [vp, ip, ctypes.POINTER(dp)]),
+            "mpspt_local_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, dp, dp]),
+            "mpspt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def declared_symbols():
+    """Entry points declared in include/mpspt.h (parsed from the header)."""
+    import re
+    hdr = os.path.join(os.path.dirname(HERE), "include", "mpspt.h")
+    text = open(hdr).read()
+    pat = r"^\s*(?:mpspt_status|void|const char\s*\*)\s+(mpspt_[a-z0-9_]+)\s*\("
+    return sorted(set(re.findall(pat, text, flags=re.M)))
+
+
+def _check(st):
+    if st != MPSPT_OK:
+        msg = load().mpspt_status_string(st)
+        raise MpsptError(st, msg.decode() if msg else "")
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def mpspt_default_options():
+    o = mpspt_options()
+    load().mpspt_default_options(ctypes.byref(o))
+    return o
+
+
+def mpspt_create(opt=None):
+    o = opt if opt is not None else mpspt_default_options()
+    h = ctypes.c_void_p()
+    _check(load().mpspt_create(ctypes.byref(h), ctypes.byref(o)))
+    return h
+
+
+def mpspt_destroy(ctx):
+    load().mpspt_destroy(ctx)
+
+
+def mpspt_set_integrals(ctx, k_act, k_virt, n_elec, h, L):
+    h = _f64(h)
+    L = _f64(L)
+    _check(load().mpspt_set_integrals(ctx, k_act, k_virt, n_elec, _dp(h), _dp(L), L.shape[0]))
+
+
+def mpspt_set_reference(ctx, ci):
+    ci = _f64(ci)
+    _check(load().mpspt_set_reference(ctx, _dp(ci), ci.size))
+
+
+def mpspt_energies(ctx, h0):
+    e = [ctypes.c_double() for _ in range(3)]
+    _check(load().mpspt_energies(ctx, H0.get(h0, h0), *[ctypes.byref(x) for x in e]))
+    return tuple(x.value for x in e)
+
+
+def mpspt_minimize_hylleraas(ctx, h0, M, want_psi1=True):
+    e2 = ctypes.c_double()
+    psi = ctypes.c_void_p()
+    rep = mpspt_report()
+    _check(load().mpspt_minimize_hylleraas(ctx, H0.get(h0, h0), M, ctypes.byref(e2),
+                                           ctypes.byref(psi) if want_psi1 else None, ctypes.byref(rep)))
+    return e2.value, (psi if want_psi1 else None), rep
+
+
+def mpspt_third_order(ctx, h0, psi1):
+    e3 = ctypes.c_double()
+    _check(load().mpspt_third_order(ctx, H0.get(h0, h0), psi1, ctypes.byref(e3)))
+    return e3.value
+
+
+def mpspt_mps_free(psi):
+    load().mpspt_mps_free(psi)
+
+
+def mpspt_mps_import(ctx, tensors, labels):
+    """tensors: list of (D_l, 4, D_r) arrays; labels: list of (D_c, 2) int arrays."""
+    n = len(tensors)
+    dims = np.array([len(q) for q in labels], dtype=np.int32)
+    qn = np.ascontiguousarray(np.concatenate([np.asarray(q).reshape(-1, 2) for q in labels]), dtype=np.int32)
+    ts = [_f64(t) for t in tensors]
+    arr = (ctypes.POINTER(ctypes.c_double) * n)(*[_dp(t) for t in ts])
+    out = ctypes.c_void_p()
+    _check(load().mpspt_mps_import(ctx, n, dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                   qn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), arr, ctypes.byref(out)))
+    return out
+
+
+def mpspt_mps_shape(psi):
+    n = ctypes.c_int()
+    _check(load().mpspt_mps_shape(psi, ctypes.byref(n), None))
+    dims = np.zeros(n.value + 1, dtype=np.int32)
+    _check(load().mpspt_mps_shape(psi, ctypes.byref(n), dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return n.value, dims
+
+
+def mpspt_mps_export(psi):
+    n, dims = mpspt_mps_shape(psi)
+    qn = np.zeros((int(dims.sum()), 2), dtype=np.int32)
+    ts = [np.zeros((dims[c], 4, dims[c + 1])) for c in range(n)]
+    arr = (ctypes.POINTER(ctypes.c_double) * n)(*[_dp(t) for t in ts])
+    _check(load().mpspt_mps_export(psi, qn.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), arr))
+    labels = np.split(qn, np.cumsum(dims)[:-1])
+    return ts, labels
+
+
+def mpspt_local_apply(ctx, h0, psi1, i, op, x=None, shape=None):
+    out = np.zeros(shape)
+    xp = _dp(_f64(x)) if x is not None else None
+    xa = _f64(x) if x is not None else None
+    if xa is not None:
+        xp = _dp(xa)
+    _check(load().mpspt_local_apply(ctx, H0.get(h0, h0), psi1, i, op, xp, _dp(out)))
+    return out
+
+
+def mpspt_status_string(st):
+    return load().mpspt_status_string(st).decode()

@@ -1,0 +1,168 @@
+// Core types of the MPS-PT library: quantum numbers, bond bases, errors,
+// stream-ordered device buffers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/mpspt.h"
+
+namespace mpspt {
+
+struct Error : std::runtime_error {
+    mpspt_status status;
+    Error(mpspt_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define MPSPT_CUDA(call)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            if (e_ == cudaErrorMemoryAllocation)                                          \
+                throw ::mpspt::Error(MPSPT_ERR_OOM, std::string(#call) + ": " +           \
+                                                        cudaGetErrorString(e_));          \
+            throw ::mpspt::Error(MPSPT_ERR_CUDA,                                          \
+                                 std::string(#call) + ": " + cudaGetErrorString(e_));     \
+        }                                                                                 \
+    } while (0)
+
+inline void require(bool ok, const std::string& msg, mpspt_status s = MPSPT_ERR_INVALID) {
+    if (!ok) throw Error(s, msg);
+}
+
+// (N, 2Sz) of a left part of the chain, or a change of it.
+struct QN {
+    int n = 0, sz = 0;
+    QN() = default;
+    QN(int n_, int sz_) : n(n_), sz(sz_) {}
+    QN operator+(const QN& o) const { return {n + o.n, sz + o.sz}; }
+    QN operator-(const QN& o) const { return {n - o.n, sz - o.sz}; }
+    bool operator==(const QN& o) const { return n == o.n && sz == o.sz; }
+    bool operator!=(const QN& o) const { return !(*this == o); }
+    bool operator<(const QN& o) const { return n < o.n || (n == o.n && sz < o.sz); }
+};
+
+// Local site basis |0>, |a>, |b>, |ab>.
+inline QN site_qn(int s) {
+    static const int N[4] = {0, 1, 1, 2};
+    static const int S[4] = {0, 1, -1, 0};
+    return {N[s], S[s]};
+}
+
+struct Sector {
+    QN q;
+    int dim = 0;
+    int off = 0;  // position of the sector's first index in the bond basis
+};
+
+// Bond basis at one cut: QN sectors sorted ascending, contiguous indices.
+struct Bond {
+    std::vector<Sector> sec;
+    int total = 0;
+    int find(const QN& q) const {
+        int lo = 0, hi = (int)sec.size() - 1;
+        while (lo <= hi) {
+            int mid = (lo + hi) / 2;
+            if (sec[mid].q == q) return mid;
+            if (sec[mid].q < q) lo = mid + 1; else hi = mid - 1;
+        }
+        return -1;
+    }
+    void finalize() {
+        total = 0;
+        for (auto& s : sec) { s.off = total; total += s.dim; }
+    }
+    int nsec() const { return (int)sec.size(); }
+};
+
+// Registry of live device allocations.  Task lists are validated against it
+// before launch (every pointer range a kernel will touch must lie inside one
+// live allocation), so a planner error becomes a status, not a bad access.
+struct Registry {
+    std::mutex mu;
+    std::map<uintptr_t, size_t> live;
+    static Registry& get() { static Registry r; return r; }
+    void add(const void* p, size_t n) { std::lock_guard<std::mutex> g(mu); live[(uintptr_t)p] = n; }
+    void remove(const void* p) { std::lock_guard<std::mutex> g(mu); live.erase((uintptr_t)p); }
+    bool contains(const void* p, size_t bytes) {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = live.upper_bound((uintptr_t)p);
+        if (it == live.begin()) return false;
+        --it;
+        return (uintptr_t)p >= it->first && (uintptr_t)p + bytes <= it->first + it->second;
+    }
+};
+
+// Bounds checks are on unless MPSPT_CHECK=0.
+inline bool checks_enabled() {
+    static int on = [] { const char* e = std::getenv("MPSPT_CHECK"); return (e && e[0] == '0') ? 0 : 1; }();
+    return on != 0;
+}
+
+inline void check_range(const void* p, size_t bytes, const char* what) {
+    if (!checks_enabled() || bytes == 0) return;
+    if (!Registry::get().contains(p, bytes))
+        throw Error(MPSPT_ERR_INVALID, std::string("planner bounds check failed: ") + what);
+}
+
+// Stream-ordered device allocation (cudaMallocAsync), released on the same
+// stream.  Sizes in bytes.
+class DBuf {
+  public:
+    DBuf() = default;
+    DBuf(size_t bytes, cudaStream_t st) { alloc(bytes, st); }
+    ~DBuf() { release(); }
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept { *this = std::move(o); }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p_ = o.p_; n_ = o.n_; st_ = o.st_;
+            o.p_ = nullptr; o.n_ = 0;
+        }
+        return *this;
+    }
+    void alloc(size_t bytes, cudaStream_t st) {
+        release();
+        st_ = st;
+        n_ = bytes;
+        if (bytes) {
+            MPSPT_CUDA(cudaMallocAsync(&p_, bytes, st));
+            Registry::get().add(p_, bytes);
+        }
+    }
+    void ensure(size_t bytes, cudaStream_t st) {
+        if (bytes > n_) alloc(bytes + bytes / 4, st);
+    }
+    void release() {
+        if (p_) { Registry::get().remove(p_); cudaFreeAsync(p_, st_); }
+        p_ = nullptr;
+        n_ = 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p_); }
+    void* get() const { return p_; }
+    size_t bytes() const { return n_; }
+
+  private:
+    void* p_ = nullptr;
+    size_t n_ = 0;
+    cudaStream_t st_ = 0;
+};
+
+template <class T>
+inline void upload(DBuf& dst, const std::vector<T>& v, cudaStream_t st) {
+    dst.ensure(v.size() * sizeof(T) + 16, st);
+    if (!v.empty())
+        MPSPT_CUDA(cudaMemcpyAsync(dst.get(), v.data(), v.size() * sizeof(T),
+                                   cudaMemcpyHostToDevice, st));
+}
+
+}  // namespace mpspt

@@ -1,0 +1,1049 @@
+// MPS-PT engine (host orchestration; device kernels do the contractions).
+#include "engine.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "hostla.h"
+
+namespace mpspt {
+
+// ------------------------------------------------------------------ context
+Ctx::Ctx(const mpspt_options& o) : opt(o) {
+    MPSPT_CUDA(cudaSetDevice(o.device));
+    st = static_cast<cudaStream_t>(o.stream);
+    red.alloc(4 * 1024 * sizeof(double), st);
+    cnt.alloc(64, st);
+    MPSPT_CUDA(cudaMemsetAsync(cnt.get(), 0, 64, st));
+    cg.alloc(sizeof(CgState), st);
+    scal.alloc(16 * sizeof(double), st);
+    MPSPT_CUDA(cudaMallocHost(&cg_host, sizeof(CgState)));
+    MPSPT_CUDA(cudaMallocHost(&scal_host, 16 * sizeof(double)));
+}
+
+Ctx::~Ctx() {
+    cudaStreamSynchronize(st);
+    if (cg_host) cudaFreeHost(cg_host);
+    if (scal_host) cudaFreeHost(scal_host);
+}
+
+double Ctx::e0(int h0) const {
+    if (h0 == MPSPT_H0_DYALL) return P.e_ref;
+    double s = 0.0;
+    for (int t = 0; t < P.ka; ++t)
+        for (int u = 0; u < P.ka; ++u) s += P.f[(size_t)t * P.k + u] * P.gamma[(size_t)t * P.ka + u];
+    return s;
+}
+
+const MPO& Ctx::A_mpo(int h0) {
+    auto it = mpoA.find(h0);
+    if (it != mpoA.end()) return it->second;
+    std::vector<Term> t;
+    const int k = P.k, ka = P.ka;
+    if (h0 == MPSPT_H0_DYALL) {
+        add_one_body(t, P.h, k, 0, ka, 0, ka);
+        add_two_body(t, P.eri, k, 0, ka, 0, ka, -1);
+    } else {
+        add_one_body(t, P.f, k, 0, ka, 0, ka);
+    }
+    add_number(t, P.eps, ka, k);
+    Term c{-e0(h0), 0, {}};
+    t.push_back(c);
+    return mpoA[h0] = build_mpo(t, k, ka);
+}
+
+const MPO& Ctx::V_mpo() {
+    auto it = mpoV.find(0);
+    if (it != mpoV.end()) return it->second;
+    std::vector<Term> t;
+    const int k = P.k, ka = P.ka;
+    add_one_body(t, P.h, k, ka, k, 0, ka);          // c+_a c_t
+    add_two_body(t, P.eri, k, 0, k, 0, ka, ka);     // >= 1 virtual creator, active annihilators
+    return mpoV[0] = build_mpo(t, k, ka);
+}
+
+const MPO& Ctx::H_mpo() {
+    if (!mpoH) {
+        std::vector<Term> t;
+        add_one_body(t, P.h, P.k, 0, P.k, 0, P.k);
+        add_two_body(t, P.eri, P.k, 0, P.k, 0, P.k, -1);
+        mpoH.reset(new MPO(build_mpo(t, P.k, P.ka)));
+    }
+    return *mpoH;
+}
+
+const MPO& Ctx::I_mpo() {
+    if (!mpoI) {
+        std::vector<Term> t;
+        t.push_back(Term{1.0, 0, {}});
+        mpoI.reset(new MPO(build_mpo(t, P.k, P.ka)));
+    }
+    return *mpoI;
+}
+
+// ------------------------------------------------------------- integrals
+void set_integrals(Ctx& c, int ka, int kv, int nel, const double* h, const double* L, int nq) {
+    require(ka >= 1 && kv >= 0 && nq >= 1, "bad orbital / Cholesky dimensions");
+    require(nel >= 2 && nel % 2 == 0 && nel <= 2 * ka, "n_elec must be even, 2 <= n_elec <= 2 k_act");
+    require(ka <= 14, "k_act > 14 not supported by the dense reference input");
+    require(h && L, "null integral array");
+    const int k = ka + kv;
+    Problem& P = c.P;
+    P = Problem();
+    P.k = k; P.ka = ka; P.kv = kv; P.nel = nel; P.nq = nq;
+    P.h_in.assign(h, h + (size_t)k * k);
+    P.L_in.assign(L, L + (size_t)nq * k * k);
+    for (double v : P.h_in) require(std::isfinite(v), "non-finite one-electron integral");
+    for (double v : P.L_in) require(std::isfinite(v), "non-finite Cholesky vector");
+    for (int p = 0; p < k; ++p)
+        for (int q = 0; q < p; ++q)
+            require(std::fabs(P.h_in[(size_t)p * k + q] - P.h_in[(size_t)q * k + p]) < 1e-12,
+                    "h must be symmetric");
+    P.have_int = true;
+    c.mpoA.clear(); c.mpoV.clear(); c.mpoH.reset(); c.mpoI.reset();
+}
+
+namespace {
+
+// Occupation-string helpers on the 4^ka active space (site 0 most significant).
+inline int code_at(long long idx, int p, int ka) { return (int)((idx >> (2 * (ka - 1 - p))) & 3); }
+
+// c_j or c+_j (j = 2p + s) on a string; returns -1 if it vanishes.
+inline long long apply1(long long idx, int j, bool dag, int ka, int& sign) {
+    const int p = j / 2, s = j % 2;
+    const int code = code_at(idx, p, ka);
+    const int bit = 1 << s;
+    if (dag == ((code & bit) != 0)) return -1;
+    int below = 0;
+    for (int q = 0; q < p; ++q) below += __builtin_popcount(code_at(idx, q, ka));
+    if (s == 1) below += code & 1;
+    if (below & 1) sign = -sign;
+    const int nc = code ^ bit;
+    const int sh = 2 * (ka - 1 - p);
+    return (idx & ~(3LL << sh)) | ((long long)nc << sh);
+}
+
+void one_rdm_and_energy(Problem& P) {
+    const int ka = P.ka, k = P.k;
+    const long long n = 1LL << (2 * ka);
+    std::vector<long long> nz;
+    for (long long i = 0; i < n; ++i) if (P.ci[i] != 0.0) nz.push_back(i);
+    P.gamma.assign((size_t)ka * ka, 0.0);
+    double e1 = 0.0, e2 = 0.0;
+    for (long long d : nz) {
+        const double cd = P.ci[d];
+        for (int s = 0; s < 2; ++s)
+            for (int u = 0; u < ka; ++u) {
+                int sg1 = 1;
+                long long d1 = apply1(d, 2 * u + s, false, ka, sg1);
+                if (d1 < 0) continue;
+                for (int t = 0; t < ka; ++t) {
+                    int sg2 = sg1;
+                    long long d2 = apply1(d1, 2 * t + s, true, ka, sg2);
+                    if (d2 < 0) continue;
+                    P.gamma[(size_t)t * ka + u] += P.ci[d2] * cd * sg2;
+                }
+                // two-body: 1/2 (tu|vw) c+_ts c+_vr c_wr c_us
+                for (int r = 0; r < 2; ++r)
+                    for (int w = 0; w < ka; ++w) {
+                        int sg2 = sg1;
+                        long long d2 = apply1(d1, 2 * w + r, false, ka, sg2);
+                        if (d2 < 0) continue;
+                        for (int v = 0; v < ka; ++v) {
+                            int sg3 = sg2;
+                            long long d3 = apply1(d2, 2 * v + r, true, ka, sg3);
+                            if (d3 < 0) continue;
+                            for (int t = 0; t < ka; ++t) {
+                                int sg4 = sg3;
+                                long long d4 = apply1(d3, 2 * t + s, true, ka, sg4);
+                                if (d4 < 0) continue;
+                                const double g = P.eri[(((size_t)t * k + u) * k + v) * k + w];
+                                e2 += 0.5 * g * P.ci[d4] * cd * sg4;
+                            }
+                        }
+                    }
+            }
+    }
+    for (int t = 0; t < ka; ++t)
+        for (int u = 0; u < ka; ++u) e1 += P.h[(size_t)t * k + u] * P.gamma[(size_t)t * ka + u];
+    P.e_ref = e1 + e2;
+}
+
+void build_eri(Problem& P) {
+    const int k = P.k;
+    P.eri.assign((size_t)k * k * k * k, 0.0);
+    for (int Q = 0; Q < P.nq; ++Q) {
+        const double* Lq = &P.L[(size_t)Q * k * k];
+        for (size_t pq = 0; pq < (size_t)k * k; ++pq) {
+            const double a = Lq[pq];
+            if (a == 0.0) continue;
+            double* row = &P.eri[pq * k * k];
+            for (size_t rs = 0; rs < (size_t)k * k; ++rs) row[rs] += a * Lq[rs];
+        }
+    }
+}
+
+// Exact QN-blocked MPS of a dense active-space vector (density-matrix form
+// of the left-to-right SVD); keeps eigenvalues above keep_rel * max.
+void ci_to_mps(const Problem& P, MpsHost& out) {
+    const int ka = P.ka;
+    out.nsite = ka;
+    out.bond.assign(ka + 1, Bond());
+    out.T.assign(ka, {});
+    out.bond[0].sec.push_back({QN(0, 0), 1, 0});
+    out.bond[0].finalize();
+    std::vector<double> T(P.ci);      // Dl x R
+    long long R = (long long)T.size();
+    for (int c = 0; c < ka - 1; ++c) {
+        const Bond& bl = out.bond[c];
+        const int Dl = bl.total;
+        const long long Rn = R / 4;
+        // row (l, s) of X = T[l][s * Rn + rest]
+        std::vector<QN> rq(Dl * 4);
+        for (const auto& sec : bl.sec)
+            for (int i = 0; i < sec.dim; ++i)
+                for (int s = 0; s < 4; ++s) rq[(sec.off + i) * 4 + s] = sec.q + site_qn(s);
+        std::map<QN, std::vector<int>> groups;
+        for (int r = 0; r < Dl * 4; ++r) groups[rq[r]].push_back(r);
+        struct Kept { QN q; std::vector<double> U; int nr; int nk; std::vector<int> rows; };
+        std::vector<Kept> kept;
+        for (auto& g : groups) {
+            const auto& rows = g.second;
+            const int nr = (int)rows.size();
+            std::vector<double> rho((size_t)nr * nr, 0.0);
+            for (int a = 0; a < nr; ++a) {
+                const double* xa = &T[(size_t)(rows[a] / 4) * R + (size_t)(rows[a] % 4) * Rn];
+                for (int b = a; b < nr; ++b) {
+                    const double* xb = &T[(size_t)(rows[b] / 4) * R + (size_t)(rows[b] % 4) * Rn];
+                    double s = 0.0;
+                    for (long long z = 0; z < Rn; ++z) s += xa[z] * xb[z];
+                    rho[(size_t)a * nr + b] = rho[(size_t)b * nr + a] = s;
+                }
+            }
+            std::vector<double> w, V;
+            jacobi_eigh(nr, rho, w, V);
+            double wmax = 0.0;
+            for (double v : w) wmax = std::max(wmax, v);
+            Kept kp{g.first, {}, nr, 0, rows};
+            for (int j = nr - 1; j >= 0; --j) {
+                if (!(w[j] > 1e-14 * wmax) || w[j] <= 0.0) continue;
+                for (int a = 0; a < nr; ++a) kp.U.push_back(V[(size_t)a * nr + j]);  // column-major store
+                kp.nk++;
+            }
+            if (kp.nk) kept.push_back(std::move(kp));
+        }
+        Bond nb;
+        for (auto& kp : kept) nb.sec.push_back({kp.q, kp.nk, 0});
+        nb.finalize();
+        std::vector<double> A((size_t)Dl * 4 * nb.total, 0.0);
+        std::vector<double> Tn((size_t)nb.total * Rn, 0.0);
+        for (size_t si = 0; si < kept.size(); ++si) {
+            const auto& kp = kept[si];
+            const int off = nb.sec[si].off;
+            for (int j = 0; j < kp.nk; ++j) {
+                for (int a = 0; a < kp.nr; ++a) {
+                    const double u = kp.U[(size_t)j * kp.nr + a];
+                    const int row = kp.rows[a];
+                    A[(size_t)row * nb.total + off + j] = u;
+                    const double* xa = &T[(size_t)(row / 4) * R + (size_t)(row % 4) * Rn];
+                    double* tn = &Tn[(size_t)(off + j) * Rn];
+                    for (long long z = 0; z < Rn; ++z) tn[z] += u * xa[z];
+                }
+            }
+        }
+        out.T[c] = std::move(A);
+        out.bond[c + 1] = nb;
+        T.swap(Tn);
+        R = Rn;
+    }
+    // last site
+    const Bond& bl = out.bond[ka - 1];
+    const QN tot(P.nel, 0);
+    Bond last;
+    last.sec.push_back({tot, 1, 0});
+    last.finalize();
+    std::vector<double> A((size_t)bl.total * 4, 0.0);
+    for (const auto& sec : bl.sec)
+        for (int i = 0; i < sec.dim; ++i)
+            for (int s = 0; s < 4; ++s)
+                if (sec.q + site_qn(s) == tot) A[(size_t)(sec.off + i) * 4 + s] = T[(size_t)(sec.off + i) * 4 + s];
+    out.T[ka - 1] = std::move(A);
+    out.bond[ka] = last;
+}
+
+}  // namespace
+
+void set_reference(Ctx& c, const double* ci, long long n) {
+    Problem& P = c.P;
+    require(P.have_int, "mpspt_set_integrals must come first", MPSPT_ERR_STATE);
+    require(ci != nullptr && n == (1LL << (2 * P.ka)), "n_ci must equal 4^k_act");
+    P.ci.assign(ci, ci + n);
+    double nrm = 0.0;
+    for (double v : P.ci) { require(std::isfinite(v), "non-finite CI coefficient"); nrm += v * v; }
+    require(nrm > 0.0, "zero reference vector");
+    nrm = std::sqrt(nrm);
+    for (double& v : P.ci) v /= nrm;
+    // QN check: every nonzero string has N = n_elec, Sz = 0
+    for (long long i = 0; i < n; ++i) {
+        if (P.ci[i] == 0.0) continue;
+        int nn = 0, sz = 0;
+        for (int p = 0; p < P.ka; ++p) { int cd = code_at(i, p, P.ka); nn += __builtin_popcount(cd); sz += (cd & 1) - ((cd >> 1) & 1); }
+        require(nn == P.nel && sz == 0, "reference has components outside (N, Sz = 0)");
+    }
+    const int k = P.k, ka = P.ka, kv = P.kv;
+    // gamma and f in the original basis (f needs only (pq|tu), (pu|tq) with t,u active)
+    P.h = P.h_in;
+    P.L = P.L_in;
+    build_eri(P);
+    one_rdm_and_energy(P);      // gamma, E_ref (active block, untouched by the rotation)
+    std::vector<double> f((size_t)k * k);
+    for (int p = 0; p < k; ++p)
+        for (int q = 0; q < k; ++q) {
+            double s = P.h[(size_t)p * k + q];
+            for (int t = 0; t < ka; ++t)
+                for (int u = 0; u < ka; ++u) {
+                    const double g = P.gamma[(size_t)t * ka + u];
+                    if (g == 0.0) continue;
+                    s += g * (P.eri[(((size_t)p * k + q) * k + t) * k + u] -
+                              0.5 * P.eri[(((size_t)p * k + u) * k + t) * k + q]);
+                }
+            f[(size_t)p * k + q] = s;
+        }
+    // semicanonical virtuals: rotate by the eigenvectors of f_vv (ascending)
+    if (kv > 0) {
+        std::vector<double> fvv((size_t)kv * kv), w, U;
+        for (int a = 0; a < kv; ++a)
+            for (int b = 0; b < kv; ++b) fvv[(size_t)a * kv + b] = f[(size_t)(ka + a) * k + ka + b];
+        jacobi_eigh(kv, fvv, w, U);
+        std::vector<double> C((size_t)k * k, 0.0);
+        for (int t = 0; t < ka; ++t) C[(size_t)t * k + t] = 1.0;
+        for (int a = 0; a < kv; ++a)
+            for (int b = 0; b < kv; ++b) C[(size_t)(ka + a) * k + ka + b] = U[(size_t)a * kv + b];
+        auto rotate = [&](const double* M, double* out) {
+            std::vector<double> tmp((size_t)k * k, 0.0);
+            for (int p = 0; p < k; ++p)
+                for (int j = 0; j < k; ++j) {
+                    double s = 0.0;
+                    for (int q = 0; q < k; ++q) s += M[(size_t)p * k + q] * C[(size_t)q * k + j];
+                    tmp[(size_t)p * k + j] = s;
+                }
+            for (int i = 0; i < k; ++i)
+                for (int j = 0; j < k; ++j) {
+                    double s = 0.0;
+                    for (int p = 0; p < k; ++p) s += C[(size_t)p * k + i] * tmp[(size_t)p * k + j];
+                    out[(size_t)i * k + j] = s;
+                }
+        };
+        std::vector<double> hr((size_t)k * k), fr((size_t)k * k);
+        rotate(P.h.data(), hr.data());
+        rotate(f.data(), fr.data());
+        P.h.swap(hr);
+        f.swap(fr);
+        for (int Q = 0; Q < P.nq; ++Q) rotate(&P.L_in[(size_t)Q * k * k], &P.L[(size_t)Q * k * k]);
+        build_eri(P);
+    }
+    P.f = f;
+    P.eps.resize(k);
+    for (int p = 0; p < k; ++p) P.eps[p] = f[(size_t)p * k + p];
+    // exact MPS of Psi0 on the full chain (empty virtual sites)
+    MpsHost h0;
+    ci_to_mps(P, h0);
+    const QN tot(P.nel, 0);
+    for (int a = 0; a < kv; ++a) {
+        Bond b;
+        b.sec.push_back({tot, 1, 0});
+        b.finalize();
+        h0.bond.push_back(b);
+        std::vector<double> T(4, 0.0);
+        T[0] = 1.0;
+        h0.T.push_back(T);
+    }
+    h0.nsite = k;
+    c.psi0 = std::move(*mps_upload(h0, c.st));
+    P.have_ref = true;
+    c.mpoA.clear(); c.mpoV.clear(); c.mpoH.reset(); c.mpoI.reset();
+    c.sync();
+}
+
+// ---------------------------------------------------------------- MPS I/O
+std::unique_ptr<MpsD> mps_upload(const MpsHost& h, cudaStream_t st) {
+    std::unique_ptr<MpsD> m(new MpsD);
+    m->nsite = h.nsite;
+    m->bond = h.bond;
+    m->A.resize(h.nsite);
+    for (int c = 0; c < h.nsite; ++c) {
+        SiteT& A = m->A[c];
+        const Bond &L = h.bond[c], &R = h.bond[c + 1];
+        A.build(L, R, st);
+        std::vector<double> buf(A.n);
+        const int Dr = R.total;
+        for (const auto& b : A.blk) {
+            const int rl = L.sec[b.sl].dim, rr = R.sec[b.sr].dim;
+            for (int i = 0; i < rl; ++i)
+                for (int j = 0; j < rr; ++j)
+                    buf[b.off + (size_t)i * rr + j] =
+                        h.T[c][((size_t)(L.sec[b.sl].off + i) * 4 + b.s) * Dr + R.sec[b.sr].off + j];
+        }
+        if (A.n) MPSPT_CUDA(cudaMemcpyAsync(A.d.get(), buf.data(), A.n * sizeof(double),
+                                            cudaMemcpyHostToDevice, st));
+        MPSPT_CUDA(cudaStreamSynchronize(st));
+    }
+    return m;
+}
+
+MpsHost mps_download(const MpsD& m, cudaStream_t st) {
+    MpsHost h;
+    h.nsite = m.nsite;
+    h.bond = m.bond;
+    h.T.resize(m.nsite);
+    for (int c = 0; c < m.nsite; ++c) {
+        const SiteT& A = m.A[c];
+        const Bond &L = m.bond[c], &R = m.bond[c + 1];
+        std::vector<double> buf(A.n);
+        if (A.n) MPSPT_CUDA(cudaMemcpyAsync(buf.data(), A.d.get(), A.n * sizeof(double),
+                                            cudaMemcpyDeviceToHost, st));
+        MPSPT_CUDA(cudaStreamSynchronize(st));
+        h.T[c].assign((size_t)L.total * 4 * R.total, 0.0);
+        for (const auto& b : A.blk) {
+            const int rl = L.sec[b.sl].dim, rr = R.sec[b.sr].dim;
+            for (int i = 0; i < rl; ++i)
+                for (int j = 0; j < rr; ++j)
+                    h.T[c][((size_t)(L.sec[b.sl].off + i) * 4 + b.s) * R.total + R.sec[b.sr].off + j] =
+                        buf[b.off + (size_t)i * rr + j];
+        }
+    }
+    return h;
+}
+
+// ----------------------------------------------------------- initial Psi1
+namespace {
+
+inline uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+inline double init_value(uint64_t seed, int c, int s, int l, int r) {
+    uint64_t x = (seed << 48) + ((uint64_t)(4 * c + s) << 38) + ((uint64_t)l << 19) + (uint64_t)r;
+    return (double)(splitmix64(x) >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+}
+
+// Allowed-N filter per cut (empty = no filter).
+std::vector<std::vector<int>> cut_filters(const Problem& P) {
+    std::vector<std::vector<int>> f(P.k + 1);
+    if (P.kv > 0) f[P.ka] = {P.nel - 1, P.nel - 2};
+    return f;
+}
+
+// Initial bond sectors: w_q = min(nL, nR, M); proportional cap to M.
+std::vector<Bond> initial_bonds(int nsite, QN target, const std::vector<std::vector<int>>& filt, int M) {
+    const long long CAP = 1LL << 40;
+    std::vector<std::map<QN, long long>> nL(nsite + 1), nR(nsite + 1);
+    auto pass = [&](int cut, const QN& q) {
+        if (filt[cut].empty()) return true;
+        for (int v : filt[cut]) if (v == q.n) return true;
+        return false;
+    };
+    nL[0][QN(0, 0)] = 1;
+    for (int c = 0; c < nsite; ++c) {
+        for (auto& kv : nL[c])
+            for (int s = 0; s < 4; ++s) {
+                QN q = kv.first + site_qn(s);
+                long long& v = nL[c + 1][q];
+                v = std::min(CAP, v + kv.second);
+            }
+        for (auto it = nL[c + 1].begin(); it != nL[c + 1].end();)
+            it = pass(c + 1, it->first) ? std::next(it) : nL[c + 1].erase(it);
+    }
+    nR[nsite][target] = 1;
+    for (int c = nsite - 1; c >= 0; --c) {
+        for (auto& kv : nR[c + 1])
+            for (int s = 0; s < 4; ++s) {
+                QN q = kv.first - site_qn(s);
+                long long& v = nR[c][q];
+                v = std::min(CAP, v + kv.second);
+            }
+        for (auto it = nR[c].begin(); it != nR[c].end();)
+            it = pass(c, it->first) ? std::next(it) : nR[c].erase(it);
+    }
+    std::vector<Bond> out(nsite + 1);
+    for (int c = 0; c <= nsite; ++c) {
+        std::vector<std::pair<QN, long long>> w;
+        long long tot = 0;
+        for (auto& kv : nL[c]) {
+            auto it = nR[c].find(kv.first);
+            if (it == nR[c].end()) continue;
+            long long v = std::min(std::min(kv.second, it->second), (long long)M);
+            if (v > 0) { w.push_back({kv.first, v}); tot += v; }
+        }
+        for (auto& e : w) {
+            long long d = e.second;
+            if (tot > M) d = std::min(d, std::max(1LL, ((long long)M * e.second) / tot));
+            out[c].sec.push_back({e.first, (int)d, 0});
+        }
+        out[c].finalize();
+    }
+    return out;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ sweep
+namespace {
+
+struct Work {
+    DBuf x, g, b, r, z, p, Ap, minv, x0;
+    void ensure(size_t n, size_t n0, cudaStream_t st) {
+        const size_t by = (n + 1) * sizeof(double);
+        x.ensure(by, st); g.ensure(by, st); b.ensure(by, st); r.ensure(by, st); z.ensure(by, st);
+        p.ensure(by, st); Ap.ensure(by, st); minv.ensure(by, st);
+        x0.ensure((n0 + 1) * sizeof(double), st);
+    }
+};
+
+struct Env {
+    EnvT LA, LV, RA, RV;
+};
+
+// Composite sector of a two-site split.
+struct Comp {
+    QN q;
+    struct Mem { int a, b; int roff; int dim; };   // (sl,s1) or (s2,sr)
+    std::vector<Mem> mem;
+    int dim = 0;
+    size_t rho_off = 0;
+};
+
+// Validates copy tasks (column indices are read back from the host copy).
+void check_copies(const std::vector<CopyTask>& ct, const std::vector<int>& colv, const int* colp) {
+    if (!checks_enabled()) return;
+    for (const auto& t : ct) {
+        check_range(t.dst, ((size_t)(t.rows - 1) * t.ldd + t.cols_n) * sizeof(double), "copy dst");
+        int maxc = (t.trans ? t.rows : t.cols_n) - 1;
+        if (t.cols) {
+            const size_t base = (size_t)(t.cols - colp);
+            const int nsel = t.trans ? t.rows : t.cols_n;
+            require(base + nsel <= colv.size(), "copy column list out of range");
+            maxc = 0;
+            for (int q = 0; q < nsel; ++q) maxc = std::max(maxc, colv[base + q]);
+        }
+        const int nrow = t.trans ? t.cols_n : t.rows;
+        check_range(t.src, ((size_t)(nrow - 1) * t.lds + maxc + 1) * sizeof(double), "copy src");
+    }
+}
+
+struct Sweeper {
+    Ctx& c;
+    const Problem& P;
+    int h0, M;
+    const MPO& WA;
+    const MPO& WV;
+    MpsD& psi;
+    const MpsD& psi0;
+    std::vector<std::vector<int>> filt;
+    std::vector<EnvT> LA, LV, RA, RV;
+    Work w;
+    TwoT X, X0;
+    Omega omA, omV;
+    TwoSitePlan sig, rhs;
+    DiagPlan dia;
+    GemmPlan prod, prod0, gr, gc;
+    EnvPlan envp;
+    DBuf rho, V, wv, ctasks, cols, etasks;
+    SweepResult* res = nullptr;
+    cudaEvent_t ev0, ev1;
+
+    Sweeper(Ctx& c_, int h0_, int M_, MpsD& psi_)
+        : c(c_), P(c_.P), h0(h0_), M(M_), WA(c_.A_mpo(h0_)), WV(c_.V_mpo()), psi(psi_), psi0(c_.psi0) {
+        filt = cut_filters(P);
+        const int k = P.k;
+        LA.resize(k + 1); LV.resize(k + 1); RA.resize(k + 1); RV.resize(k + 1);
+        MPSPT_CUDA(cudaEventCreate(&ev0));
+        MPSPT_CUDA(cudaEventCreate(&ev1));
+    }
+    ~Sweeper() { cudaEventDestroy(ev0); cudaEventDestroy(ev1); }
+
+    void boundary_envs() {
+        const int k = P.k;
+        auto one = [&](EnvT& E, const std::vector<QN>& dq, const Bond& b, const Bond& k0) {
+            E.build(dq, b, k0, c.st);
+            const double v = 1.0;
+            MPSPT_CUDA(cudaMemcpyAsync(E.d.get(), &v, sizeof(double), cudaMemcpyHostToDevice, c.st));
+            MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        };
+        one(LA[0], WA.dq[0], psi.bond[0], psi.bond[0]);
+        one(LV[0], WV.dq[0], psi.bond[0], psi0.bond[0]);
+        one(RA[k], WA.dq[k], psi.bond[k], psi.bond[k]);
+        one(RV[k], WV.dq[k], psi.bond[k], psi0.bond[k]);
+    }
+
+    void update_left(int i) {   // L[i+1] from L[i] and site i
+        LA[i + 1].build(WA.dq[i + 1], psi.bond[i + 1], psi.bond[i + 1], c.st);
+        envp.build_left(WA, i, LA[i], psi.A[i], psi.A[i], psi.bond[i], psi.bond[i], psi.bond[i + 1],
+                        psi.bond[i + 1], LA[i + 1], c.st);
+        envp.run(c.st);
+        LV[i + 1].build(WV.dq[i + 1], psi.bond[i + 1], psi0.bond[i + 1], c.st);
+        envp.build_left(WV, i, LV[i], psi.A[i], psi0.A[i], psi.bond[i], psi0.bond[i], psi.bond[i + 1],
+                        psi0.bond[i + 1], LV[i + 1], c.st);
+        envp.run(c.st);
+    }
+
+    void update_right(int i) {  // R[i] from R[i+1] and site i
+        RA[i].build(WA.dq[i], psi.bond[i], psi.bond[i], c.st);
+        envp.build_right(WA, i, RA[i + 1], psi.A[i], psi.A[i], psi.bond[i], psi.bond[i], psi.bond[i + 1],
+                         psi.bond[i + 1], RA[i], c.st);
+        envp.run(c.st);
+        RV[i].build(WV.dq[i], psi.bond[i], psi0.bond[i], c.st);
+        envp.build_right(WV, i, RV[i + 1], psi.A[i], psi0.A[i], psi.bond[i], psi0.bond[i], psi.bond[i + 1],
+                         psi0.bond[i + 1], RV[i], c.st);
+        envp.run(c.st);
+    }
+
+    // x (device, X layout) -> new A_i, A_{i+1}, bond i+1.  dir 0: left-to-right.
+    double split(int i, int dir, int Mkeep, const TwoT& Xl, const double* xd) {
+        const Bond &bL = psi.bond[i], &bR = psi.bond[i + 2];
+        const std::vector<int>& fm = filt[i + 1];
+        std::map<QN, Comp> comps;
+        // members that appear in the layout
+        for (const auto& b : Xl.blk) {
+            QN q;
+            int ma, mb, dim;
+            if (dir == 0) { q = bL.sec[b.sl].q + site_qn(b.s1); ma = b.sl; mb = b.s1; dim = b.rows; }
+            else { q = bR.sec[b.sr].q - site_qn(b.s2); ma = b.s2; mb = b.sr; dim = b.cols; }
+            Comp& cp = comps[q];
+            cp.q = q;
+            bool have = false;
+            for (auto& m : cp.mem) if (m.a == ma && m.b == mb) { have = true; break; }
+            if (!have) { cp.mem.push_back({ma, mb, cp.dim, dim}); cp.dim += dim; }
+        }
+        std::vector<Comp> cl;
+        size_t rs = 0;
+        for (auto& kv : comps) {
+            if (!fm.empty() && std::find(fm.begin(), fm.end(), kv.first.n) == fm.end()) continue;
+            kv.second.rho_off = rs;
+            rs += (size_t)kv.second.dim * kv.second.dim;
+            cl.push_back(kv.second);
+        }
+        rho.ensure((rs + 1) * sizeof(double), c.st);
+        V.ensure((rs + 1) * sizeof(double), c.st);
+        size_t wsz = 0;
+        for (auto& cp : cl) wsz += cp.dim;
+        wv.ensure((wsz + 1) * sizeof(double), c.st);
+        double* rhop = rho.as<double>();
+        // rho blocks
+        gr.clear();
+        auto member_index = [&](const Comp& cp, int a, int b) {
+            for (int t = 0; t < (int)cp.mem.size(); ++t) if (cp.mem[t].a == a && cp.mem[t].b == b) return t;
+            return -1;
+        };
+        (void)member_index;
+        for (auto& cp : cl) {
+            for (auto& m1 : cp.mem)
+                for (auto& m2 : cp.mem) {
+                    int m0 = gr.mark();
+                    if (dir == 0) {
+                        for (int s2 = 0; s2 < 4; ++s2) {
+                            int b1 = Xl.find(m1.a, m1.b, s2), b2 = Xl.find(m2.a, m2.b, s2);
+                            if (b1 < 0 || b2 < 0) continue;
+                            const auto &B1 = Xl.blk[b1], &B2 = Xl.blk[b2];
+                            gr.op(xd + B1.off, B1.cols, xd + B2.off, B2.cols, B1.cols, 2, 1.0);
+                        }
+                    } else {
+                        for (int sl = 0; sl < bL.nsec(); ++sl)
+                            for (int s1 = 0; s1 < 4; ++s1) {
+                                int b1 = Xl.find(sl, s1, m1.a), b2 = Xl.find(sl, s1, m2.a);
+                                if (b1 < 0 || b2 < 0) continue;
+                                const auto &B1 = Xl.blk[b1], &B2 = Xl.blk[b2];
+                                if (B1.sr != m1.b || B2.sr != m2.b) continue;
+                                gr.op(xd + B1.off, B1.cols, xd + B2.off, B2.cols, B1.rows, 1, 1.0);
+                            }
+                    }
+                    gr.block(rhop + cp.rho_off + (size_t)m1.roff * cp.dim + m2.roff, cp.dim, m1.dim, m2.dim, 0, m0);
+                }
+        }
+        gr.upload(c.st);
+        gr.run(c.st);
+        // eigen-decomposition per composite sector
+        std::vector<EigTask> et;
+        size_t wo = 0;
+        std::vector<size_t> woff;
+        for (auto& cp : cl) {
+            et.push_back({rhop + cp.rho_off, V.as<double>() + cp.rho_off, wv.as<double>() + wo, cp.dim, 0});
+            woff.push_back(wo);
+            wo += cp.dim;
+        }
+        for (const auto& t : et) {
+            require(t.n <= 2048, "density-matrix sector larger than 2048");
+            check_range(t.A, (size_t)t.n * t.n * sizeof(double), "eig A");
+            check_range(t.V, (size_t)t.n * t.n * sizeof(double), "eig V");
+            check_range(t.w, (size_t)t.n * sizeof(double), "eig w");
+        }
+        upload(etasks, et, c.st);
+        launch_eig(etasks.as<EigTask>(), (int)et.size(), c.st);
+        std::vector<double> wh(wsz);
+        if (wsz) MPSPT_CUDA(cudaMemcpyAsync(wh.data(), wv.get(), wsz * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        // selection: keep the Mkeep largest (ties at the cut dropped as a group)
+        struct Cand { double lam; int ci; int rank; int col; };
+        std::vector<Cand> cand;
+        double tr = 0.0;
+        std::vector<std::vector<int>> order(cl.size());
+        for (size_t ci = 0; ci < cl.size(); ++ci) {
+            const int n = cl[ci].dim;
+            std::vector<int> ord(n);
+            std::iota(ord.begin(), ord.end(), 0);
+            const double* w_ = wh.data() + woff[ci];
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return w_[a] > w_[b]; });
+            order[ci] = ord;
+            for (int j = 0; j < n; ++j) tr += w_[j];
+        }
+        for (size_t ci = 0; ci < cl.size(); ++ci) {
+            const double* w_ = wh.data() + woff[ci];
+            for (int r = 0; r < cl[ci].dim; ++r) {
+                const double lam = w_[order[ci][r]];
+                if (lam > 1e-13 * tr) cand.push_back({lam, (int)ci, r, order[ci][r]});
+            }
+        }
+        std::sort(cand.begin(), cand.end(), [&](const Cand& a, const Cand& b) {
+            if (a.lam != b.lam) return a.lam > b.lam;
+            if (!(cl[a.ci].q == cl[b.ci].q)) return cl[a.ci].q < cl[b.ci].q;
+            return a.rank < b.rank;
+        });
+        int m = std::min<int>(Mkeep, (int)cand.size());
+        if (m < (int)cand.size()) {
+            int m0 = m;
+            while (m > 0 && cand[m - 1].lam <= cand[m].lam * (1.0 + 1e-8)) --m;
+            if (m == 0) m = m0;
+        }
+        require(m > 0, "truncation kept no state (zero two-site tensor)", MPSPT_ERR_NOT_CONVERGED);
+        double kept_w = 0.0;
+        std::vector<std::vector<int>> kcols(cl.size());
+        std::vector<std::pair<int, int>> krank;   // (ci, rank) sorted later
+        for (int t = 0; t < m; ++t) { kept_w += cand[t].lam; krank.push_back({cand[t].ci, cand[t].rank}); }
+        std::sort(krank.begin(), krank.end());
+        for (auto& kr : krank) kcols[kr.first].push_back(order[kr.first][kr.second]);
+        // new bond at cut i+1
+        Bond nb;
+        std::vector<int> nsec_of(cl.size(), -1);
+        for (size_t ci = 0; ci < cl.size(); ++ci)
+            if (!kcols[ci].empty()) { nsec_of[ci] = nb.nsec(); nb.sec.push_back({cl[ci].q, (int)kcols[ci].size(), 0}); }
+        nb.finalize();
+        std::vector<int> colv;
+        std::vector<size_t> coff(cl.size(), 0);
+        for (size_t ci = 0; ci < cl.size(); ++ci) { coff[ci] = colv.size(); colv.insert(colv.end(), kcols[ci].begin(), kcols[ci].end()); }
+        upload(cols, colv, c.st);
+        const int* colp = cols.as<int>();
+        psi.bond[i + 1] = nb;
+        SiteT An, Bn;
+        An.build(bL, nb, c.st);
+        Bn.build(nb, bR, c.st);
+        std::vector<CopyTask> ct;
+        gc.clear();
+        if (dir == 0) {
+            MPSPT_CUDA(cudaMemsetAsync(An.d.get(), 0, An.n * sizeof(double) + 8, c.st));
+            for (const auto& b : An.blk) {
+                const int ci = std::find_if(cl.begin(), cl.end(), [&](const Comp& cp) { return cp.q == nb.sec[b.sr].q; }) - cl.begin();
+                const Comp& cp = cl[ci];
+                for (const auto& mm : cp.mem)
+                    if (mm.a == b.sl && mm.b == b.s)
+                        ct.push_back({V.as<double>() + cp.rho_off + (size_t)mm.roff * cp.dim, An.ptr(b),
+                                      colp + coff[ci], mm.dim, nb.sec[b.sr].dim, cp.dim, nb.sec[b.sr].dim, 0, 0});
+            }
+            check_copies(ct, colv, colp);
+            upload(ctasks, ct, c.st);
+            launch_copy(ctasks.as<CopyTask>(), (int)ct.size(), c.st);
+            // carry: B(Q, s2, sr) = sum_(sl,s1) A(sl,s1,Q)^T x(sl,s1,s2)
+            for (const auto& b : Bn.blk) {
+                int m0 = gc.mark();
+                const Comp* cp = nullptr;
+                for (auto& cc : cl) if (cc.q == nb.sec[b.sl].q) cp = &cc;
+                const int kq = nb.sec[b.sl].dim;
+                for (const auto& mm : cp->mem) {
+                    int xb = Xl.find(mm.a, mm.b, b.s);
+                    int ab = An.find(mm.a, mm.b);
+                    if (xb < 0 || ab < 0 || Xl.blk[xb].sr != b.sr) continue;
+                    const auto& XB = Xl.blk[xb];
+                    gc.op(An.ptr(An.blk[ab]), kq, xd + XB.off, XB.cols, XB.rows, 1, 1.0);
+                }
+                gc.block(Bn.ptr(b), bR.sec[b.sr].dim, kq, bR.sec[b.sr].dim, 0, m0);
+            }
+        } else {
+            MPSPT_CUDA(cudaMemsetAsync(Bn.d.get(), 0, Bn.n * sizeof(double) + 8, c.st));
+            for (const auto& b : Bn.blk) {
+                const int ci = std::find_if(cl.begin(), cl.end(), [&](const Comp& cp) { return cp.q == nb.sec[b.sl].q; }) - cl.begin();
+                const Comp& cp = cl[ci];
+                for (const auto& mm : cp.mem)
+                    if (mm.a == b.s && mm.b == b.sr)
+                        ct.push_back({V.as<double>() + cp.rho_off + (size_t)mm.roff * cp.dim, Bn.ptr(b),
+                                      colp + coff[ci], nb.sec[b.sl].dim, mm.dim, cp.dim, mm.dim, 1, 0});
+            }
+            check_copies(ct, colv, colp);
+            upload(ctasks, ct, c.st);
+            launch_copy(ctasks.as<CopyTask>(), (int)ct.size(), c.st);
+            // carry: A(sl, s1, Q) = sum_(s2,sr) x(sl,s1,s2,sr) B(Q,s2,sr)^T
+            for (const auto& b : An.blk) {
+                int m0 = gc.mark();
+                const Comp* cp = nullptr;
+                for (auto& cc : cl) if (cc.q == nb.sec[b.sr].q) cp = &cc;
+                const int kq = nb.sec[b.sr].dim;
+                for (const auto& mm : cp->mem) {
+                    int xb = Xl.find(b.sl, b.s, mm.a);
+                    int bb = Bn.find(b.sr, mm.a);
+                    if (xb < 0 || bb < 0 || Xl.blk[xb].sr != mm.b || Bn.blk[bb].sr != mm.b) continue;
+                    const auto& XB = Xl.blk[xb];
+                    gc.op(xd + XB.off, XB.cols, Bn.ptr(Bn.blk[bb]), XB.cols, XB.cols, 2, 1.0);
+                }
+                gc.block(An.ptr(b), kq, bL.sec[b.sl].dim, kq, 0, m0);
+            }
+        }
+        gc.upload(c.st);
+        gc.run(c.st);
+        psi.A[i] = std::move(An);
+        psi.A[i + 1] = std::move(Bn);
+        MPSPT_CUDA(cudaStreamSynchronize(c.st));   // plans above reference host vectors
+        return tr > 0 ? std::max(0.0, (tr - kept_w) / tr) : 0.0;
+    }
+
+    // x0 = A_i A_{i+1} on layout Xl into xd
+    void product(GemmPlan& g, const MpsD& m, int i, const TwoT& Xl, double* xd) {
+        g.clear();
+        plan_product(g, Xl, xd, m.bond[i + 1], m.A[i], m.A[i + 1], m.bond[i]);
+        g.upload(c.st);
+        g.run(c.st);
+    }
+
+    void right_canonicalize() {
+        for (int i = P.k - 2; i >= 0; --i) {
+            X.build(psi.bond[i], psi.bond[i + 2], filt[i + 1]);
+            w.ensure(X.n, 1, c.st);
+            product(prod, psi, i, X, w.x.as<double>());
+            split(i, 1, 1 << 30, X, w.x.as<double>());
+        }
+    }
+
+    double sigma(double* in_out_dummy = nullptr) {
+        (void)in_out_dummy;
+        MPSPT_CUDA(cudaEventRecord(ev0, c.st));
+        sig.run(c.st);
+        MPSPT_CUDA(cudaEventRecord(ev1, c.st));
+        res->sigma_calls++;
+        res->sigma_flops += sig.flops();
+        return 0.0;
+    }
+
+    void add_sigma_time() {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) res->sigma_ms += ms;
+    }
+
+    double dot(const double* a, const double* b, size_t n, int slot) {
+        vec_dot(a, b, n, c.scal.as<double>() + slot, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
+        return 0.0;
+    }
+
+    // one bond step; returns h_loc
+    double step(int i, int dir) {
+        const Bond &bL = psi.bond[i], &bR = psi.bond[i + 2];
+        X.build(bL, bR, filt[i + 1]);
+        X0.build(psi0.bond[i], psi0.bond[i + 2], {});
+        const size_t n = X.n;
+        w.ensure(n, X0.n, c.st);
+        double* x = w.x.as<double>();
+        product(prod, psi, i, X, x);
+        product(prod0, psi0, i, X0, w.x0.as<double>());
+        omA.build(WA, i);
+        omV.build(WV, i);
+        rhs.build(omV, X, X0, bL, psi0.bond[i], bR, psi0.bond[i + 2], LV[i], RV[i + 2], WV.dq[i + 2],
+                  w.x0.as<double>(), w.g.as<double>(), c.st);
+        rhs.run(c.st);
+        sig.build(omA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
+                  w.Ap.as<double>(), c.st);
+        dia.build(omA, X, bL, bR, LA[i], RA[i + 2], WA.dq[i], WA.dq[i + 2], w.minv.as<double>(), c.st);
+        dia.run(c.st);
+        make_minv(w.minv.as<double>(), w.minv.as<double>(), n, c.st);
+        vec_scale_mask(w.b.as<double>(), w.g.as<double>(), -1.0, n, c.st);
+        // CG on A x = -g from the warm start
+        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+        sigma();
+        CgState* S = c.cg.as<CgState>();
+        cg_init(w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.b.as<double>(), w.Ap.as<double>(),
+                w.minv.as<double>(), n, S, c.opt.cg_tol, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
+        MPSPT_CUDA(cudaMemcpyAsync(c.cg_host, S, sizeof(CgState), cudaMemcpyDeviceToHost, c.st));
+        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        add_sigma_time();
+        int it = 0;
+        while (!c.cg_host->done && it < c.opt.cg_max_iter) {
+            sigma();
+            cg_step(x, w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.Ap.as<double>(),
+                    w.minv.as<double>(), n, S, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
+            MPSPT_CUDA(cudaMemcpyAsync(c.cg_host, S, sizeof(CgState), cudaMemcpyDeviceToHost, c.st));
+            MPSPT_CUDA(cudaStreamSynchronize(c.st));
+            add_sigma_time();
+            ++it;
+        }
+        require(!c.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
+                MPSPT_ERR_NOT_SPD);
+        res->cg_iters += it;
+        // Hylleraas value h = x.Ax + 2 x.g in float64
+        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+        sigma();
+        dot(x, w.Ap.as<double>(), n, 0);
+        dot(x, w.g.as<double>(), n, 1);
+        MPSPT_CUDA(cudaMemcpyAsync(c.scal_host, c.scal.get(), 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        add_sigma_time();
+        const double h = c.scal_host[0] + 2.0 * c.scal_host[1];
+        const double disc = split(i, dir, M, X, x);
+        res->max_disc = std::max(res->max_disc, disc);
+        res->max_bond = std::max(res->max_bond, psi.bond[i + 1].total);
+        if (dir == 0) update_left(i);
+        else update_right(i + 1);
+        return h;
+    }
+};
+
+}  // namespace
+
+std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
+    require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
+    require(M >= 1, "bond dimension M must be >= 1");
+    require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
+    require(c.opt.prec == MPSPT_FP64, "only the float64 local solver is available in this build",
+            MPSPT_ERR_INVALID);
+    const auto t0 = std::chrono::steady_clock::now();
+    const Problem& P = c.P;
+    // initial Psi1
+    MpsHost ih;
+    ih.nsite = P.k;
+    ih.bond = initial_bonds(P.k, QN(P.nel, 0), cut_filters(P), M);
+    ih.T.resize(P.k);
+    for (int s = 0; s < P.k; ++s) {
+        const Bond &L = ih.bond[s], &R = ih.bond[s + 1];
+        ih.T[s].assign((size_t)L.total * 4 * R.total, 0.0);
+        for (const auto& sl : L.sec)
+            for (int t = 0; t < 4; ++t) {
+                int sr = R.find(sl.q + site_qn(t));
+                if (sr < 0) continue;
+                const auto& rs = R.sec[sr];
+                for (int a = 0; a < sl.dim; ++a)
+                    for (int b = 0; b < rs.dim; ++b)
+                        ih.T[s][((size_t)(sl.off + a) * 4 + t) * R.total + rs.off + b] =
+                            init_value(c.opt.seed, s, t, sl.off + a, rs.off + b);
+            }
+    }
+    std::unique_ptr<MpsD> psi = mps_upload(ih, c.st);
+    Sweeper sw(c, h0, M, *psi);
+    sw.res = &res;
+    sw.right_canonicalize();
+    sw.boundary_envs();
+    for (int i = P.k - 1; i >= 1; --i) sw.update_right(i);
+    double prev = 0.0;
+    const int maxs = std::min(64, std::max(1, c.opt.max_sweeps));
+    for (int s = 0; s < maxs; ++s) {
+        res.max_disc = 0.0;
+        double e = 0.0;
+        for (int i = 0; i <= P.k - 2; ++i) e = sw.step(i, 0);
+        for (int i = P.k - 2; i >= 0; --i) e = sw.step(i, 1);
+        res.e2_sweep.push_back(e);
+        if (c.opt.verbose)
+            fprintf(stderr, "[mpspt] sweep %d  E2 = %.12f  max discarded %.3e  cg %lld\n", s, e,
+                    res.max_disc, res.cg_iters);
+        if (s > 0 && std::fabs(e - prev) < c.opt.e_tol) break;
+        prev = e;
+    }
+    res.e2 = res.e2_sweep.back();
+    res.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return psi;
+}
+
+double expectation(Ctx& c, const MPO& W, const MpsD& bra, const MpsD& ket) {
+    EnvT L, Ln;
+    L.build(W.dq[0], bra.bond[0], ket.bond[0], c.st);
+    const double one = 1.0;
+    MPSPT_CUDA(cudaMemcpyAsync(L.d.get(), &one, sizeof(double), cudaMemcpyHostToDevice, c.st));
+    EnvPlan ep;
+    for (int i = 0; i < bra.nsite; ++i) {
+        Ln.build(W.dq[i + 1], bra.bond[i + 1], ket.bond[i + 1], c.st);
+        ep.build_left(W, i, L, bra.A[i], ket.A[i], bra.bond[i], ket.bond[i], bra.bond[i + 1],
+                      ket.bond[i + 1], Ln, c.st);
+        ep.run(c.st);
+        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        std::swap(L, Ln);
+    }
+    double v = 0.0;
+    if (!L.blk.empty())
+        MPSPT_CUDA(cudaMemcpyAsync(&v, L.d.get(), sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    MPSPT_CUDA(cudaStreamSynchronize(c.st));
+    return v;
+}
+
+double third_order(Ctx& c, int h0, const MpsD& psi1) {
+    require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
+    const double n2 = expectation(c, c.I_mpo(), psi1, psi1);
+    const double eh = expectation(c, c.H_mpo(), psi1, psi1);
+    const double ea = expectation(c, c.A_mpo(h0), psi1, psi1);
+    return eh - ea - c.P.e_ref * n2;   // <H> - <A> - (E0 + E1) <1>
+}
+
+void local_apply(Ctx& c, int h0, const MpsD& psi1_in, int i, int op, const double* xh, double* out) {
+    require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
+    require(psi1_in.nsite == c.P.k, "MPS length differs from the orbital count");
+    require(i >= 0 && i + 1 < c.P.k, "bond index out of range");
+    MpsD& psi1 = const_cast<MpsD&>(psi1_in);
+    SweepResult res;
+    Sweeper sw(c, h0, 1 << 30, psi1);
+    sw.res = &res;
+    sw.boundary_envs();
+    for (int s = 0; s < i; ++s) sw.update_left(s);
+    for (int s = c.P.k - 1; s >= i + 2; --s) sw.update_right(s);
+    const Bond &bL = psi1.bond[i], &bR = psi1.bond[i + 2];
+    TwoT X;
+    X.build(bL, bR, sw.filt[i + 1]);
+    const size_t n = X.n;
+    std::vector<double> xb(n, 0.0), ob(n, 0.0);
+    const int DL = bL.total, DR = bR.total;
+    auto dense_index = [&](const TwoT::B& b, int r, int q) {
+        return (((size_t)(bL.sec[b.sl].off + r) * 4 + b.s1) * 4 + b.s2) * DR + bR.sec[b.sr].off + q;
+    };
+    if (xh)
+        for (const auto& b : X.blk)
+            for (int r = 0; r < b.rows; ++r)
+                for (int q = 0; q < b.cols; ++q) xb[b.off + (size_t)r * b.cols + q] = xh[dense_index(b, r, q)];
+    sw.w.ensure(n, 1, c.st);
+    MPSPT_CUDA(cudaMemcpyAsync(sw.w.p.get(), xb.data(), n * sizeof(double), cudaMemcpyHostToDevice, c.st));
+    double* dout = sw.w.Ap.as<double>();
+    if (op == MPSPT_LOCAL_SIGMA) {
+        sw.omA.build(sw.WA, i);
+        sw.sig.build(sw.omA, X, X, bL, bL, bR, bR, sw.LA[i], sw.RA[i + 2], sw.WA.dq[i + 2],
+                     sw.w.p.as<double>(), dout, c.st);
+        sw.sig.run(c.st);
+    } else if (op == MPSPT_LOCAL_RHS) {
+        TwoT X0;
+        X0.build(c.psi0.bond[i], c.psi0.bond[i + 2], {});
+        sw.w.ensure(n, X0.n, c.st);
+        sw.product(sw.prod0, c.psi0, i, X0, sw.w.x0.as<double>());
+        sw.omV.build(sw.WV, i);
+        sw.rhs.build(sw.omV, X, X0, bL, c.psi0.bond[i], bR, c.psi0.bond[i + 2], sw.LV[i], sw.RV[i + 2],
+                     sw.WV.dq[i + 2], sw.w.x0.as<double>(), dout, c.st);
+        sw.rhs.run(c.st);
+    } else if (op == MPSPT_LOCAL_DIAG) {
+        sw.omA.build(sw.WA, i);
+        sw.dia.build(sw.omA, X, bL, bR, sw.LA[i], sw.RA[i + 2], sw.WA.dq[i], sw.WA.dq[i + 2], dout, c.st);
+        sw.dia.run(c.st);
+    } else {
+        throw Error(MPSPT_ERR_INVALID, "unknown local operator");
+    }
+    MPSPT_CUDA(cudaMemcpyAsync(ob.data(), dout, n * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    MPSPT_CUDA(cudaStreamSynchronize(c.st));
+    std::fill(out, out + (size_t)DL * 16 * DR, 0.0);
+    for (const auto& b : X.blk)
+        for (int r = 0; r < b.rows; ++r)
+            for (int q = 0; q < b.cols; ++q) out[dense_index(b, r, q)] = ob[b.off + (size_t)r * b.cols + q];
+}
+
+}  // namespace mpspt

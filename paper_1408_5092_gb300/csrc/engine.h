@@ -1,0 +1,83 @@
+// MPS-PT engine: problem set-up, the two-site Hylleraas sweep, expectation
+// values.  Host code orchestrates; every contraction runs in the kernels.
+#pragma once
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "core.h"
+#include "kernels.h"
+#include "mpo.h"
+#include "plans.h"
+#include "tensors.h"
+
+namespace mpspt {
+
+struct MpsD {
+    int nsite = 0;
+    std::vector<Bond> bond;      // nsite + 1 cuts
+    std::vector<SiteT> A;        // nsite sites
+};
+
+// Host copy of a QN-labelled MPS (dense tensors, for import / export / init).
+struct MpsHost {
+    int nsite = 0;
+    std::vector<Bond> bond;
+    std::vector<std::vector<double>> T;  // dense D_l x 4 x D_r
+};
+
+struct Problem {
+    int k = 0, ka = 0, kv = 0, nel = 0, nq = 0;
+    std::vector<double> h, L, eri;       // semicanonical virtual basis
+    std::vector<double> gamma, f, eps;   // 1-RDM (ka x ka), Fock (k x k), diag(f)
+    double e_ref = 0.0;
+    bool have_int = false, have_ref = false;
+    std::vector<double> h_in, L_in;      // as given
+    std::vector<double> ci;
+};
+
+struct Ctx {
+    mpspt_options opt;
+    cudaStream_t st = 0;
+    Problem P;
+    MpsD psi0;                            // reference on the full chain
+    std::map<int, MPO> mpoA, mpoV;        // keyed by H0 choice
+    std::unique_ptr<MPO> mpoH, mpoI;
+    // reduction scratch and CG scalars
+    DBuf red, cnt, cg;
+    CgState* cg_host = nullptr;           // pinned mirror
+    double* scal_host = nullptr;          // pinned scalars
+    DBuf scal;
+    std::string last_error;
+
+    explicit Ctx(const mpspt_options& o);
+    ~Ctx();
+    double e0(int h0) const;
+    const MPO& A_mpo(int h0);
+    const MPO& V_mpo();
+    const MPO& H_mpo();
+    const MPO& I_mpo();
+    void sync() { MPSPT_CUDA(cudaStreamSynchronize(st)); }
+};
+
+void set_integrals(Ctx& c, int ka, int kv, int nel, const double* h, const double* L, int nq);
+void set_reference(Ctx& c, const double* ci, long long n);
+
+struct SweepResult {
+    double e2 = 0.0;
+    std::vector<double> e2_sweep;
+    double max_disc = 0.0;
+    long long cg_iters = 0, sigma_calls = 0;
+    double sigma_flops = 0.0, sigma_ms = 0.0, wall_ms = 0.0;
+    int max_bond = 0;
+};
+
+std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res);
+double expectation(Ctx& c, const MPO& W, const MpsD& bra, const MpsD& ket);
+double third_order(Ctx& c, int h0, const MpsD& psi1);
+void local_apply(Ctx& c, int h0, const MpsD& psi1, int i, int op, const double* x, double* out);
+
+std::unique_ptr<MpsD> mps_upload(const MpsHost& h, cudaStream_t st);
+MpsHost mps_download(const MpsD& m, cudaStream_t st);
+
+}  // namespace mpspt

@@ -1,0 +1,432 @@
+// CUDA-core kernels of the MPS-PT hot path (sm_103a): grouped block GEMM
+// (float64 / float32) driven by task lists, Jacobi diagonal, batched Jacobi
+// eigensolver for the density-matrix blocks, block copies, and the CG vector
+// kernels with deterministic (fixed-order) reductions.
+#include "kernels.h"
+
+#include <cstdio>
+
+namespace mpspt {
+namespace {
+
+constexpr int TK = 16;
+constexpr int NT = 256;
+
+// Grouped GEMM: one CTA per output tile, looping over the tile's K-list.
+// 16x16 threads, each owns rows ty+16i, cols tx+16j (i, j < 4).
+template <class T, class Task, class Op>
+__global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks,
+                                             const Op* __restrict__ ops,
+                                             const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const Task t = tasks[blockIdx.x];
+    __shared__ T As[TK][GEMM_TM + 1];
+    __shared__ T Bs[TK][GEMM_TN + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    const int mrem = min(GEMM_TM, t.m - t.r0);
+    const int nrem = min(GEMM_TN, t.n - t.c0);
+    for (int o = t.op0; o < t.op1; ++o) {
+        const Op op = ops[o];
+        const bool ta = op.trans & 1, tb = op.trans & 2;
+        for (int k0 = 0; k0 < op.k; k0 += TK) {
+            const int krem = min(TK, op.k - k0);
+            for (int e = threadIdx.x; e < GEMM_TM * TK; e += NT) {
+                int i, kk;
+                if (ta) { i = e % GEMM_TM; kk = e / GEMM_TM; }
+                else { kk = e % TK; i = e / TK; }
+                T v = T(0);
+                if (i < mrem && kk < krem) {
+                    const int row = t.r0 + i, kg = k0 + kk;
+                    v = ta ? op.A[(size_t)kg * op.lda + row] : op.A[(size_t)row * op.lda + kg];
+                    v *= op.alpha;
+                }
+                As[kk][i] = v;
+            }
+            for (int e = threadIdx.x; e < GEMM_TN * TK; e += NT) {
+                int j, kk;
+                if (tb) { kk = e % TK; j = e / TK; }
+                else { j = e % GEMM_TN; kk = e / GEMM_TN; }
+                T v = T(0);
+                if (j < nrem && kk < krem) {
+                    const int col = t.c0 + j, kg = k0 + kk;
+                    v = tb ? op.B[(size_t)col * op.ldb + kg] : op.B[(size_t)kg * op.ldb + col];
+                }
+                Bs[kk][j] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < TK; ++kk) {
+                T a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = ty + 16 * i;
+        if (r >= mrem) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = tx + 16 * j;
+            if (c >= nrem) continue;
+            T* dst = t.C + (size_t)(t.r0 + r) * t.ldc + (t.c0 + c);
+            *dst = t.accumulate ? *dst + acc[i][j] : acc[i][j];
+        }
+    }
+}
+
+__global__ void k_diag(const DiagTask* __restrict__ tasks, const DiagTerm* __restrict__ terms) {
+    const DiagTask t = tasks[blockIdx.x];
+    const int n = t.rows * t.cols;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int l = e / t.cols, r = e % t.cols;
+        double s = 0.0;
+        for (int k = t.t0; k < t.t1; ++k) {
+            const DiagTerm d = terms[k];
+            s += d.coef * d.L[(size_t)l * (d.ldL + 1)] * d.R[(size_t)r * (d.ldR + 1)];
+        }
+        t.out[e] = s;
+    }
+}
+
+__global__ void k_copy(const CopyTask* __restrict__ tasks) {
+    const CopyTask t = tasks[blockIdx.x];
+    const int n = t.rows * t.cols_n;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int i = e / t.cols_n, j = e % t.cols_n;
+        double v;
+        if (t.trans) v = t.src[(size_t)j * t.lds + (t.cols ? t.cols[i] : i)];
+        else v = t.src[(size_t)i * t.lds + (t.cols ? t.cols[j] : j)];
+        t.dst[(size_t)i * t.ldd + j] = v;
+    }
+}
+
+// Cyclic two-sided Jacobi with the round-robin parallel ordering: in each of
+// the m-1 rounds of a sweep, m/2 disjoint (p, q) rotations are applied at
+// once (rows, then columns).  Works in global memory (L2-resident blocks).
+constexpr int EIG_MAXN = 2048;
+__global__ void __launch_bounds__(512) k_eig(const EigTask* __restrict__ tasks) {
+    const EigTask t = tasks[blockIdx.x];
+    const int n = t.n;
+    double* A = t.A;
+    double* V = t.V;
+    __shared__ int Pp[EIG_MAXN / 2], Qq[EIG_MAXN / 2];
+    __shared__ double Cc[EIG_MAXN / 2], Ss[EIG_MAXN / 2];
+    __shared__ double red[2][32];
+    __shared__ int stop;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e / n == e % n) ? 1.0 : 0.0;
+    if (n > 1) {
+        const int m = n + (n & 1);
+        const int half = m / 2;
+        for (int sweep = 0; sweep < 30; ++sweep) {
+            // convergence: off-diagonal Frobenius norm relative to the whole
+            double off = 0.0, all = 0.0;
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+                const double v = A[e];
+                all += v * v;
+                if (e / n != e % n) off += v * v;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                off += __shfl_xor_sync(0xffffffffu, off, o);
+                all += __shfl_xor_sync(0xffffffffu, all, o);
+            }
+            if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = off; red[1][threadIdx.x >> 5] = all; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double so = 0.0, sa = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { so += red[0][w]; sa += red[1][w]; }
+                stop = (so <= 1e-30 * sa) || sa == 0.0;
+            }
+            __syncthreads();
+            if (stop) break;
+            for (int r = 0; r < m - 1; ++r) {
+                for (int k = threadIdx.x; k < half; k += blockDim.x) {
+                    const int pa = (k == 0) ? 0 : ((k - 1 + r) % (m - 1)) + 1;
+                    const int pb = ((m - 1 - k - 1 + r) % (m - 1)) + 1;
+                    int p = min(pa, pb), q = max(pa, pb);
+                    double c = 1.0, s = 0.0;
+                    if (q < n) {
+                        const double apq = A[(size_t)p * n + q];
+                        if (apq != 0.0) {
+                            const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                            const double th = (aqq - app) / (2.0 * apq);
+                            const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                            c = 1.0 / sqrt(tt * tt + 1.0);
+                            s = tt * c;
+                        }
+                    } else {
+                        q = p;  // dummy player: no rotation
+                    }
+                    Pp[k] = p; Qq[k] = q; Cc[k] = c; Ss[k] = s;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < half * n; e += blockDim.x) {
+                    const int k = e / n, j = e % n;
+                    const int p = Pp[k], q = Qq[k];
+                    if (p == q || Ss[k] == 0.0) continue;
+                    const double c = Cc[k], s = Ss[k];
+                    const double apj = A[(size_t)p * n + j], aqj = A[(size_t)q * n + j];
+                    A[(size_t)p * n + j] = c * apj - s * aqj;
+                    A[(size_t)q * n + j] = s * apj + c * aqj;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < half * n; e += blockDim.x) {
+                    const int k = e % half, i = e / half;
+                    const int p = Pp[k], q = Qq[k];
+                    if (p == q || Ss[k] == 0.0) continue;
+                    const double c = Cc[k], s = Ss[k];
+                    const double aip = A[(size_t)i * n + p], aiq = A[(size_t)i * n + q];
+                    A[(size_t)i * n + p] = c * aip - s * aiq;
+                    A[(size_t)i * n + q] = s * aip + c * aiq;
+                    const double vip = V[(size_t)i * n + p], viq = V[(size_t)i * n + q];
+                    V[(size_t)i * n + p] = c * vip - s * viq;
+                    V[(size_t)i * n + q] = s * vip + c * viq;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t.w[i] = A[(size_t)i * n + i];
+}
+
+// ----------------------------------------------------------------- vectors
+constexpr int RB = 256;        // threads per reduction block
+constexpr int RG_MAX = 1024;   // max reduction blocks
+
+inline int red_grid(size_t n) {
+    size_t g = (n + (size_t)RB * 4 - 1) / ((size_t)RB * 4);
+    if (g < 1) g = 1;
+    if (g > RG_MAX) g = RG_MAX;
+    return (int)g;
+}
+
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double (*sh)[RB / 32]) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[q][threadIdx.x >> 5] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < RB / 32; ++w) s += sh[q][w];
+            v[q] = s;
+        }
+}
+
+// Last-block-done pattern: every block stores its partial sums, the last one
+// to finish adds them in block order (deterministic) and runs `fin`.
+template <int NV>
+__device__ bool last_block(double (&v)[NV], double* scratch, unsigned* counter, double (&tot)[NV]) {
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) scratch[q * RG_MAX + blockIdx.x] = v[q];
+        __threadfence();
+        unsigned prev = atomicAdd(counter, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    if (threadIdx.x == 0) {
+        __threadfence();
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double*)scratch)[q * RG_MAX + b];
+            tot[q] = s;
+        }
+        *counter = 0;
+    }
+    return threadIdx.x == 0;
+}
+
+__global__ void k_dot(const double* __restrict__ x, const double* __restrict__ y, size_t n,
+                      double* out, double* scratch, unsigned* counter) {
+    __shared__ double sh[1][RB / 32];
+    double v[1] = {0.0};
+    for (size_t i = blockIdx.x * (size_t)RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB)
+        v[0] += x[i] * y[i];
+    block_sum<1>(v, sh);
+    double tot[1];
+    if (last_block<1>(v, scratch, counter, tot)) *out = tot[0];
+}
+
+__global__ void k_cg_init(double* r, double* z, double* p, const double* __restrict__ b,
+                          const double* __restrict__ Ax, const double* __restrict__ minv, size_t n,
+                          CgState* S, double tol, double* scratch, unsigned* counter) {
+    __shared__ double sh[3][RB / 32];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (size_t i = blockIdx.x * (size_t)RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB) {
+        const double ri = b[i] - Ax[i];
+        const double zi = minv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        p[i] = zi;
+        v[0] += ri * zi;
+        v[1] += ri * ri;
+        v[2] += b[i] * b[i];
+    }
+    block_sum<3>(v, sh);
+    double tot[3];
+    if (last_block<3>(v, scratch, counter, tot)) {
+        S->rz = tot[0];
+        S->rr = tot[1];
+        S->bb = tot[2];
+        S->tol2 = tol * tol;
+        S->iters = 0;
+        S->not_spd = 0;
+        S->done = (tot[1] <= tol * tol * tot[2]) || tot[2] == 0.0;
+    }
+}
+
+__global__ void k_cg_pap(const double* __restrict__ p, const double* __restrict__ Ap, size_t n,
+                         CgState* S, double* scratch, unsigned* counter) {
+    if (S->done) return;
+    __shared__ double sh[1][RB / 32];
+    double v[1] = {0.0};
+    for (size_t i = blockIdx.x * (size_t)RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB)
+        v[0] += p[i] * Ap[i];
+    block_sum<1>(v, sh);
+    double tot[1];
+    if (last_block<1>(v, scratch, counter, tot)) {
+        S->pAp = tot[0];
+        if (!(tot[0] > 0.0)) { S->not_spd = 1; S->done = 1; }
+        else S->alpha = S->rz / tot[0];
+    }
+}
+
+__global__ void k_cg_update(double* x, double* r, double* z, const double* __restrict__ p,
+                            const double* __restrict__ Ap, const double* __restrict__ minv,
+                            size_t n, CgState* S, double* scratch, unsigned* counter) {
+    if (S->done) return;
+    __shared__ double sh[2][RB / 32];
+    const double a = S->alpha;
+    double v[2] = {0.0, 0.0};
+    for (size_t i = blockIdx.x * (size_t)RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB) {
+        x[i] += a * p[i];
+        const double ri = r[i] - a * Ap[i];
+        const double zi = minv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        v[0] += ri * zi;
+        v[1] += ri * ri;
+    }
+    block_sum<2>(v, sh);
+    double tot[2];
+    if (last_block<2>(v, scratch, counter, tot)) {
+        S->rz_new = tot[0];
+        S->rr = tot[1];
+        S->beta = tot[0] / S->rz;
+        S->rz = tot[0];
+        S->iters += 1;
+        if (tot[1] <= S->tol2 * S->bb) S->done = 2;
+    }
+}
+
+__global__ void k_cg_dir(double* p, const double* __restrict__ z, size_t n, const CgState* S) {
+    if (S->done == 1) return;
+    const double be = S->beta;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + be * p[i];
+}
+
+__global__ void k_axpy(double* y, const double* __restrict__ x, double a, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+__global__ void k_scale(double* y, const double* __restrict__ x, double a, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i];
+}
+__global__ void k_zero(double* y, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = 0.0;
+}
+__global__ void k_minv(double* y, const double* __restrict__ d, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = d[i] > 0.0 ? 1.0 / d[i] : 0.0;
+}
+__global__ void k_d2f(float* y, const double* __restrict__ x, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+__global__ void k_f2d(double* y, const float* __restrict__ x, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = (double)x[i];
+}
+
+inline int ew_grid(size_t n) {
+    size_t g = (n + 255) / 256;
+    if (g < 1) g = 1;
+    if (g > 152 * 8) g = 152 * 8;
+    return (int)g;
+}
+
+}  // namespace
+
+void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st) {
+    if (ntask > 0) k_gemm<double, GemmTask, GemmOp><<<ntask, NT, 0, st>>>(tasks, ops, nullptr);
+}
+void launch_gemm_f32(const GemmTaskF* tasks, int ntask, const GemmOpF* ops, cudaStream_t st) {
+    if (ntask > 0) k_gemm<float, GemmTaskF, GemmOpF><<<ntask, NT, 0, st>>>(tasks, ops, nullptr);
+}
+void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaStream_t st) {
+    if (ntask > 0) k_diag<<<ntask, 256, 0, st>>>(tasks, terms);
+}
+void launch_eig(const EigTask* tasks, int ntask, cudaStream_t st) {
+    if (ntask > 0) k_eig<<<ntask, 512, 0, st>>>(tasks);
+}
+void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st) {
+    if (ntask > 0) k_copy<<<ntask, 256, 0, st>>>(tasks);
+}
+void vec_zero(double* x, size_t n, cudaStream_t st) { if (n) k_zero<<<ew_grid(n), 256, 0, st>>>(x, n); }
+void vec_scale_mask(double* y, const double* x, double a, size_t n, cudaStream_t st) {
+    if (n) k_scale<<<ew_grid(n), 256, 0, st>>>(y, x, a, n);
+}
+void vec_axpy(double* y, const double* x, double a, size_t n, cudaStream_t st) {
+    if (n) k_axpy<<<ew_grid(n), 256, 0, st>>>(y, x, a, n);
+}
+void vec_dot(const double* x, const double* y, size_t n, double* out, double* scratch,
+             unsigned* counter, cudaStream_t st) {
+    k_dot<<<red_grid(n), RB, 0, st>>>(x, y, n, out, scratch, counter);
+}
+void f64_to_f32(float* y, const double* x, size_t n, cudaStream_t st) {
+    if (n) k_d2f<<<ew_grid(n), 256, 0, st>>>(y, x, n);
+}
+void f32_to_f64(double* y, const float* x, size_t n, cudaStream_t st) {
+    if (n) k_f2d<<<ew_grid(n), 256, 0, st>>>(y, x, n);
+}
+void make_minv(double* minv, const double* diag, size_t n, cudaStream_t st) {
+    if (n) k_minv<<<ew_grid(n), 256, 0, st>>>(minv, diag, n);
+}
+void cg_init(double* r, double* z, double* p, const double* b, const double* Ax,
+             const double* minv, size_t n, CgState* S, double tol, double* scratch,
+             unsigned* counter, cudaStream_t st) {
+    k_cg_init<<<red_grid(n), RB, 0, st>>>(r, z, p, b, Ax, minv, n, S, tol, scratch, counter);
+}
+void cg_step(double* x, double* r, double* z, double* p, const double* Ap, const double* minv,
+             size_t n, CgState* S, double* scratch, unsigned* counter, cudaStream_t st) {
+    k_cg_pap<<<red_grid(n), RB, 0, st>>>(p, Ap, n, S, scratch, counter);
+    k_cg_update<<<red_grid(n), RB, 0, st>>>(x, r, z, p, Ap, minv, n, S, scratch, counter);
+    k_cg_dir<<<ew_grid(n), 256, 0, st>>>(p, z, n, S);
+}
+
+}  // namespace mpspt

@@ -1,0 +1,116 @@
+// Device kernels of the MPS-PT hot path and their task descriptors.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace mpspt {
+
+// One K-contribution of a grouped block GEMM: C_tile += alpha * op(A) op(B).
+// trans bit 0: A is stored k x m (use A^T); bit 1: B is stored n x k (use B^T).
+struct GemmOp {
+    const double* A;
+    const double* B;
+    int lda, ldb, k, trans;
+    double alpha;
+};
+
+// One output tile (rows [r0, r0+TM) x cols [c0, c0+TN) of an m x n block C).
+struct GemmTask {
+    double* C;
+    int ldc, m, n;
+    int r0, c0;
+    int op0, op1;      // range of GemmOp
+    int accumulate;    // 1: C += sum, 0: C = sum
+    int pad;
+};
+
+// Float32 variant (same layout, float pointers).
+struct GemmOpF {
+    const float* A;
+    const float* B;
+    int lda, ldb, k, trans;
+    float alpha;
+    int pad;
+};
+struct GemmTaskF {
+    float* C;
+    int ldc, m, n;
+    int r0, c0;
+    int op0, op1;
+    int accumulate;
+    int pad;
+};
+
+constexpr int GEMM_TM = 64;
+constexpr int GEMM_TN = 64;
+
+// Jacobi diagonal of A_loc: out[l, r] += sum coef * L[l*(ldL+1)] * R[r*(ldR+1)]
+struct DiagTerm {
+    const double* L;
+    const double* R;
+    int ldL, ldR;
+    double coef;
+};
+struct DiagTask {
+    double* out;
+    int rows, cols;
+    int t0, t1;
+};
+
+// Symmetric eigenproblem of one dense n x n row-major block (in place).
+struct EigTask {
+    double* A;      // n*n, destroyed (diagonal holds eigenvalues on exit)
+    double* V;      // n*n eigenvectors (columns)
+    double* w;      // n eigenvalues (unsorted)
+    int n;
+    int pad;
+};
+
+// Block copy with optional column selection and transpose:
+//   trans 0: dst[i*ldd + j] = src[i*lds + col(j)]
+//   trans 1: dst[i*ldd + j] = src[j*lds + col(i)]      col(x) = cols ? cols[x] : x
+struct CopyTask {
+    const double* src;
+    double* dst;
+    const int* cols;
+    int rows, cols_n;   // shape of dst
+    int lds, ldd;
+    int trans;
+    int pad;
+};
+
+// CG scalar block living in device memory.
+struct CgState {
+    double rz, rz_new, pAp, alpha, beta, rr, bb, tol2;
+    int done, iters, not_spd, pad;
+};
+
+void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st);
+void launch_gemm_f32(const GemmTaskF* tasks, int ntask, const GemmOpF* ops, cudaStream_t st);
+void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaStream_t st);
+void launch_eig(const EigTask* tasks, int ntask, cudaStream_t st);
+void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
+
+// Vector kernels (n doubles).  Reductions are deterministic (fixed order).
+void vec_zero(double* x, size_t n, cudaStream_t st);
+void vec_scale_mask(double* y, const double* x, double a, size_t n, cudaStream_t st);  // y = a*x
+void vec_axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);       // y += a*x
+// out[slot] = x.y  (partial sums in scratch, which needs >= 1024 doubles)
+void vec_dot(const double* x, const double* y, size_t n, double* out, double* scratch,
+             unsigned* counter, cudaStream_t st);
+void f64_to_f32(float* y, const double* x, size_t n, cudaStream_t st);
+void f32_to_f64(double* y, const float* x, size_t n, cudaStream_t st);
+
+// Preconditioned CG building blocks on device scalars.
+// r = b - Ax ; z = Minv r ; p = z ; rz = r.z ; rr = r.r ; bb = b.b
+void cg_init(double* r, double* z, double* p, const double* b, const double* Ax,
+             const double* minv, size_t n, CgState* S, double tol, double* scratch,
+             unsigned* counter, cudaStream_t st);
+// pAp = p.Ap ; alpha = rz / pAp ; x += alpha p ; r -= alpha Ap ; z = Minv r ;
+// rz_new = r.z ; rr = r.r ; done if rr <= tol2 bb ; p = z + (rz_new/rz) p
+void cg_step(double* x, double* r, double* z, double* p, const double* Ap, const double* minv,
+             size_t n, CgState* S, double* scratch, unsigned* counter, cudaStream_t st);
+void make_minv(double* minv, const double* diag, size_t n, cudaStream_t st);
+
+}  // namespace mpspt

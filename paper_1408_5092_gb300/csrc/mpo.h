@@ -1,0 +1,51 @@
+// Matrix product operators (Eq. 4) built from second-quantised term lists.
+#pragma once
+#include <array>
+#include <vector>
+
+#include "core.h"
+
+namespace mpspt {
+
+struct FOp {      // elementary fermion operator on spin-orbital j = 2p + s
+    int j;
+    bool dag;
+};
+
+struct Term {     // c * op[0] op[1] ... op[n-1] (product order)
+    double c;
+    int n;
+    FOp op[4];
+};
+
+using Mat4 = std::array<double, 16>;   // row-major <n|o|n'> on |0>,|a>,|b>,|ab>
+
+struct MpoEntry {
+    int a, b;     // state at cut p, state at cut p+1
+    int op;       // index into MPO::ops
+    double coef;
+};
+
+struct MPO {
+    int nsite = 0;
+    std::vector<int> dim;                    // states per cut, cut = 0..nsite
+    std::vector<std::vector<QN>> dq;         // QN change carried by each state
+    std::vector<std::vector<MpoEntry>> W;    // per site
+    std::vector<Mat4> ops;                   // local operator table
+};
+
+// Builds the MPO of sum(terms) on nsite sites.  Sites >= k_split are the
+// "virtual" region (the centre rule differs there, see mpo.cpp).
+MPO build_mpo(const std::vector<Term>& terms, int nsite, int k_split);
+
+// Term generators (orbital index = site index).
+void add_one_body(std::vector<Term>& out, const std::vector<double>& t, int k,
+                  int p0, int p1, int q0, int q1);
+// 1/2 sum (pq|rs) c+_ps c+_rt c_st c_qs over p in [p0,p1), q in [q0,q1),
+// r in [p0,p1), s in [q0,q1), optionally keeping only quadruples with
+// p >= vmin or r >= vmin.
+void add_two_body(std::vector<Term>& out, const std::vector<double>& eri, int k,
+                  int p0, int p1, int q0, int q1, int vmin);
+void add_number(std::vector<Term>& out, const std::vector<double>& eps, int a0, int a1);
+
+}  // namespace mpspt

@@ -1,0 +1,78 @@
+// Planner: turns each contraction of the sweep into device task lists.
+#pragma once
+#include <vector>
+
+#include "kernels.h"
+#include "tensors.h"
+
+namespace mpspt {
+
+struct GemmPlan {
+    std::vector<GemmTask> tasks;
+    std::vector<GemmOp> ops;
+    double flops = 0.0;   // algorithmic: sum over ops of 2 m n k (each product once)
+    DBuf dtasks, dops;
+    void clear() { tasks.clear(); ops.clear(); flops = 0.0; }
+    int mark() const { return (int)ops.size(); }
+    void op(const double* A, int lda, const double* B, int ldb, int k, int trans, double alpha) {
+        if (k <= 0) return;
+        ops.push_back({A, B, lda, ldb, k, trans, alpha});
+    }
+    // close the output block C (m x n) whose K-list is ops[op0, end)
+    void block(double* C, int ldc, int m, int n, int accumulate, int op0);
+    void upload(cudaStream_t st);
+    void run(cudaStream_t st) const;
+};
+
+// Two-site operator sum_{a,c} L_a (Omega_ac) R_c with Omega_ac = sum_b W1_ab (x) W2_bc.
+struct Omega {
+    struct E { int a, c, out, in; double v; };   // out/in = s1*4 + s2
+    std::vector<E> e;                              // sorted by (out, a, c, in)
+    std::vector<int> first;                        // first entry per out (17 entries)
+    void build(const MPO& W, int i);
+};
+
+// sigma-type application: out(bra layout) = sum L_a Omega_ac R_c x(ket layout).
+// T holds x R_c^T for every c (scratch sized by the plan).
+struct TwoSitePlan {
+    GemmPlan g1, g2;
+    DBuf T;
+    size_t tsize = 0;
+    void build(const Omega& om, const TwoT& bra, const TwoT& ket, const Bond& braL,
+               const Bond& ketL, const Bond& braR, const Bond& ketR, const EnvT& L,
+               const EnvT& R, const std::vector<QN>& dqR, const double* x, double* out,
+               cudaStream_t st);
+    void run(cudaStream_t st) const { g1.run(st); g2.run(st); }
+    double flops() const { return g1.flops + g2.flops; }
+};
+
+// Jacobi diagonal of sum L_a Omega_ac R_c on the bra layout.
+struct DiagPlan {
+    std::vector<DiagTask> tasks;
+    std::vector<DiagTerm> terms;
+    DBuf dt, dterm;
+    void build(const Omega& om, const TwoT& x, const Bond& L, const Bond& R, const EnvT& Le,
+               const EnvT& Re, const std::vector<QN>& dqL, const std::vector<QN>& dqR,
+               double* out, cudaStream_t st);
+    void run(cudaStream_t st) const;
+};
+
+// x[sl,s1,s2,sr] = A_i[sl,s1,sm] A_{i+1}[sm,s2,sr]
+void plan_product(GemmPlan& g, const TwoT& x, double* xd, const Bond& mid, const SiteT& A,
+                  const SiteT& B, const Bond& L);
+
+// Left transfer: Lnew_b = sum (a,s,t) W_ab[s,t] Abra(s)^T L_a Aket(t); Y scratch.
+struct EnvPlan {
+    GemmPlan g1, g2;
+    DBuf Y;
+    void build_left(const MPO& W, int site, const EnvT& L, const SiteT& Abra, const SiteT& Aket,
+                    const Bond& braL, const Bond& ketL, const Bond& braR, const Bond& ketR,
+                    EnvT& Lnew, cudaStream_t st);
+    void build_right(const MPO& W, int site, const EnvT& R, const SiteT& Abra, const SiteT& Aket,
+                     const Bond& braL, const Bond& ketL, const Bond& braR, const Bond& ketR,
+                     EnvT& Rnew, cudaStream_t st);
+    void run(cudaStream_t st) const { g1.run(st); g2.run(st); }
+    double flops() const { return g1.flops + g2.flops; }
+};
+
+}  // namespace mpspt

@@ -1,0 +1,65 @@
+"""Writes the stored oracle energies used by the GPU parity tests.
+
+Calls only oracle/ (and the seeded inputs of synthetic/).  Run from the repo
+root:  python tests/golden/make_golden.py [tiny|medium64]
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import synthetic  # noqa: E402
+from oracle.brute import ExactFirstOrder  # noqa: E402
+from oracle.mps import HylleraasSweep, third_order  # noqa: E402
+from oracle.operators import Problem  # noqa: E402
+
+
+def tiny():
+    h, L, c = synthetic.config_integrals("tiny")
+    ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
+    out = {"config": "tiny", "seed": synthetic.integrals.EVAL_SEED if hasattr(synthetic.integrals, "EVAL_SEED") else 1408, "h0": {}}
+    for h0 in ("fock", "dyall"):
+        p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
+        ex = ExactFirstOrder(p)
+        ranks = ex.schmidt_ranks()
+        d = {"E_ref": p.E_ref, "E0": p.E0, "E1": p.E1, "E2_exact": ex.e2(), "E3_exact": ex.e3(),
+             "M_exact": max(ranks), "runs": {}}
+        for M in (16, 32, max(ranks)):
+            t = time.time()
+            sw = HylleraasSweep(p, M)
+            e2 = sw.run()
+            d["runs"][str(M)] = {"E2": e2, "E3": third_order(sw), "sweeps": len(sw.history),
+                                 "history": sw.history, "oracle_s": time.time() - t}
+            print(h0, M, e2, flush=True)
+        out["h0"][h0] = d
+    return out
+
+
+def medium(M, h0):
+    h, L, c = synthetic.config_integrals("medium")
+    ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
+    p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
+    t = time.time()
+    sw = HylleraasSweep(p, M, tol_e=1e-9, verbose=True)
+    e2 = sw.run()
+    return {"config": "medium", "h0": h0, "M": M, "E_ref": p.E_ref, "E0": p.E0, "E1": p.E1,
+            "E2": e2, "sweeps": len(sw.history), "history": sw.history, "tol_e": 1e-9,
+            "oracle_s": time.time() - t}
+
+
+if __name__ == "__main__":
+    what = sys.argv[1] if len(sys.argv) > 1 else "tiny"
+    if what == "tiny":
+        res = tiny()
+        name = "oracle_tiny.json"
+    else:
+        M = int(what.replace("medium", ""))
+        h0 = sys.argv[2] if len(sys.argv) > 2 else "fock"
+        res = medium(M, h0)
+        name = f"oracle_medium_{h0}_M{M}.json"
+    with open(os.path.join(HERE, name), "w") as f:
+        json.dump(res, f, indent=1)
+    print("wrote", name)

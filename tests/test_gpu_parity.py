@@ -1,0 +1,144 @@
+"""GPU library vs the CPU oracle on the same seeded inputs.
+
+Local operators (Fig. 1C terms) are compared element by element on a shared
+Psi1; energies (E2, E3) at equal bond dimension against stored oracle values
+(tests/golden/make_golden.py) to 1e-8 Eh (float64 path)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "oracle_tiny.json")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1408_5092_gb300 import _lib
+    _lib.load()
+    return _lib
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    h, Lc, c = synthetic.config_integrals("tiny")
+    ci, _ = synthetic.fci_reference(h, Lc, c["k_act"], c["n_elec"])
+    return h, Lc, c, ci
+
+
+@pytest.fixture(scope="module")
+def gold():
+    with open(GOLD) as f:
+        return json.load(f)
+
+
+def _session(L, tiny, **opts):
+    h, Lc, c, ci = tiny
+    o = L.mpspt_default_options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    ctx = L.mpspt_create(o)
+    L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
+    L.mpspt_set_reference(ctx, ci)
+    return ctx
+
+
+@pytest.mark.parametrize("h0", ["fock", "dyall"])
+def test_reference_energies(L, tiny, gold, h0):
+    ctx = _session(L, tiny)
+    e0, e1, eref = L.mpspt_energies(ctx, h0)
+    g = gold["h0"][h0]
+    assert abs(eref - g["E_ref"]) < 1e-11
+    assert abs(e0 - g["E0"]) < 1e-11
+    assert abs(e1 - g["E1"]) < 1e-11
+    L.mpspt_destroy(ctx)
+
+
+@pytest.mark.parametrize("h0", ["fock", "dyall"])
+def test_local_operators_match_oracle(L, tiny, h0):
+    from oracle.mps import HylleraasSweep, two_site_apply, two_site_diag, two_site_mask
+    from oracle.operators import Problem
+    h, Lc, c, ci = tiny
+    p = Problem(h, Lc, c["k_act"], c["n_elec"], ci, h0=h0)
+    sw = HylleraasSweep(p, 24, seed=7)
+    ctx = _session(L, tiny)
+    psi = L.mpspt_mps_import(ctx, sw.psi1.A, sw.psi1.q)
+    rng = np.random.default_rng(3)
+    for i in range(p.k - 1):
+        # oracle environments for bond i from the shared Psi1
+        for s in range(i):
+            sw._update_left(s)
+        ql, qr = sw.psi1.q[i], sw.psi1.q[i + 2]
+        mask = two_site_mask(ql, qr, sw.allowed.get(i + 1))
+        x = rng.normal(size=mask.shape) * mask
+        ref_sig = two_site_apply(sw.LA[i], sw.WA.W[i], sw.WA.W[i + 1], sw.RA[i + 2], x, sw.WA.dims[i + 1]) * mask
+        p0 = np.einsum("lsm,mtr->lstr", sw.psi0.A[i], sw.psi0.A[i + 1])
+        ref_g = two_site_apply(sw.LV[i], sw.WV.W[i], sw.WV.W[i + 1], sw.RV[i + 2], p0, sw.WV.dims[i + 1]) * mask
+        ref_d = two_site_diag(sw.LA[i], sw.WA.W[i], sw.WA.W[i + 1], sw.RA[i + 2], x.shape, sw.WA.dims[i + 1]) * mask
+        got_sig = L.mpspt_local_apply(ctx, h0, psi, i, L.MPSPT_LOCAL_SIGMA, x, x.shape)
+        got_g = L.mpspt_local_apply(ctx, h0, psi, i, L.MPSPT_LOCAL_RHS, None, x.shape)
+        got_d = L.mpspt_local_apply(ctx, h0, psi, i, L.MPSPT_LOCAL_DIAG, None, x.shape)
+        scale = max(1.0, np.abs(ref_sig).max())
+        assert np.abs(got_sig - ref_sig).max() < 1e-12 * scale, i
+        assert np.abs(got_g - ref_g).max() < 1e-12 * max(1.0, np.abs(ref_g).max()), i
+        assert np.abs(got_d - ref_d).max() < 1e-12 * max(1.0, np.abs(ref_d).max()), i
+        # reset the oracle's left environments for the next bond
+        sw.LA[1:] = [None] * (len(sw.LA) - 1)
+        sw.LV[1:] = [None] * (len(sw.LV) - 1)
+    L.mpspt_mps_free(psi)
+    L.mpspt_destroy(ctx)
+
+
+@pytest.mark.parametrize("h0", ["fock", "dyall"])
+@pytest.mark.parametrize("which", ["16", "32", "exact"])
+def test_e2_e3_match_oracle(L, tiny, gold, h0, which):
+    g = gold["h0"][h0]
+    M = g["M_exact"] if which == "exact" else int(which)
+    run = g["runs"][str(M)]
+    ctx = _session(L, tiny)
+    e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, h0, M)
+    assert abs(e2 - run["E2"]) < 1e-8, (e2, run["E2"])
+    assert e2 >= g["E2_exact"] - 1e-10          # upper bound (Eq. 1 minimum)
+    e3 = L.mpspt_third_order(ctx, h0, psi)
+    assert abs(e3 - run["E3"]) < 1e-8, (e3, run["E3"])
+    if which == "exact":
+        assert abs(e2 - g["E2_exact"]) < 1e-9
+        assert abs(e3 - g["E3_exact"]) < 1e-9
+    assert rep.max_bond_dim <= M
+    L.mpspt_mps_free(psi)
+    L.mpspt_destroy(ctx)
+
+
+def test_errors_are_statuses_not_crashes(L, tiny):
+    h, Lc, c, ci = tiny
+    ctx = L.mpspt_create()
+    with pytest.raises(L.MpsptError) as e:
+        L.mpspt_minimize_hylleraas(ctx, "fock", 16)
+    assert e.value.status == -7                 # STATE: no integrals / reference
+    L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
+    with pytest.raises(L.MpsptError) as e:
+        L.mpspt_set_reference(ctx, ci[:-1])
+    assert e.value.status == -1
+    bad = ci.copy()
+    bad[np.argmax(np.abs(bad))] = np.nan
+    with pytest.raises(L.MpsptError):
+        L.mpspt_set_reference(ctx, bad)
+    L.mpspt_set_reference(ctx, ci)
+    with pytest.raises(L.MpsptError) as e:
+        L.mpspt_minimize_hylleraas(ctx, "fock", 0)
+    assert e.value.status == -1
+    L.mpspt_destroy(ctx)
+
+
+def test_bond_dimension_one_is_an_upper_bound(L, tiny, gold):
+    """Degenerate M = 1: a valid (poor) variational state, still above E2*."""
+    ctx = _session(L, tiny, max_sweeps=4)
+    e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, "fock", 1)
+    assert e2 >= gold["h0"]["fock"]["E2_exact"] - 1e-10
+    assert rep.max_bond_dim == 1
+    L.mpspt_mps_free(psi)
+    L.mpspt_destroy(ctx)
