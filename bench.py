@@ -1,0 +1,310 @@
+"""Benchmark: time-to-E2 of the MPS-PT Hylleraas sweep on one GB300.
+
+A step is one call of mpspt_minimize_hylleraas on the medium workload (8
+electrons in 8 active orbitals + 24 virtual orbitals, seeded integrals,
+Cholesky rank 60, exact FCI reference), run from the seeded initial Psi1 to
+convergence.  Time-to-E2 is the device time (CUDA events recorded by the
+library at the end of every sweep) until the reported E2 first lies within
+1e-6 Eh of the converged float64 E2 and stays there.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--h0 dyall|fock] [--M 64] [--prec fp64]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-E2 at 1e-6 Eh and σ TFLOP/s on 1 GB300: mixed+batched vs plain FP64"
+NOMINAL_FP64_TFLOPS = 1.25      # GB300 dense FP64 (nominal)
+NOMINAL_BF16_TFLOPS = 2250.0    # GB300 dense BF16 (nominal)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _clock_sampler():
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        p = subprocess.Popen(cmd, stdout=f, stderr=subprocess.DEVNULL)
+    except OSError:
+        p = None
+    return p, f.name
+
+
+def _clock_summary(p, path, device):
+    if p is not None:
+        p.terminate()
+        try:
+            p.wait(timeout=5)
+        except Exception:
+            p.kill()
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(device):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+    except OSError:
+        pass
+    os.unlink(path) if os.path.exists(path) else None
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _inputs(name):
+    import synthetic
+    h, L, c = synthetic.config_integrals(name)
+    ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
+    return h, L, c, ci
+
+
+def _time_to_e2(rep, e2_ref, tol=1e-6):
+    n = rep.n_sweeps
+    hist = [rep.e2_per_sweep[s] for s in range(n)]
+    first = None
+    for s in range(n):
+        if all(abs(hist[t] - e2_ref) < tol for t in range(s, n)):
+            first = s
+            break
+    if first is None:
+        return None, None
+    return rep.sweep_ms[first] / 1e3, first
+
+
+def _oracle_sample(name, h0, M, budget_s):
+    """Oracle (CPU) on the first bond steps of the first sweep; returns
+    (seconds per bond step, steps sampled, total bond steps per sweep)."""
+    from oracle.mps import HylleraasSweep
+    from oracle.operators import Problem
+    h, L, c, ci = _inputs(name)
+    p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
+    t0 = time.perf_counter()
+    sw = HylleraasSweep(p, M)
+    t_init = time.perf_counter() - t0
+    per_sweep = 2 * (p.k - 1)
+    t1 = time.perf_counter()
+    n = 0
+    order = [(i, "LR") for i in range(p.k - 1)] + [(i, "RL") for i in range(p.k - 2, -1, -1)]
+    for i, d in order:
+        sw.step(i, d)
+        n += 1
+        if time.perf_counter() - t1 > budget_s:
+            break
+    dt = time.perf_counter() - t1
+    return dt / n, n, per_sweep, t_init
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = len(os.sched_getaffinity(0))
+    steps = []
+    for _ in range(args.warmup + args.steps):
+        steps.append(_oracle_sample(args.config, args.h0, args.M, args.ref_budget))
+    timed = steps[args.warmup:]
+    sec_per_bond = statistics.median(s[0] for s in timed)
+    n, per_sweep, t_init = timed[0][1], timed[0][2], timed[0][3]
+    # extrapolate to the sweeps the GPU float64 path needs (recorded in the sample note)
+    sweeps = args.ref_sweeps
+    value = t_init + sec_per_bond * per_sweep * sweeps
+    sample = (f"oracle first {n} of {per_sweep} bond steps of sweep 1 at M={args.M} ({args.h0} H0), "
+              f"median of {args.steps}; extrapolated to {sweeps} sweeps x {per_sweep} bond steps + set-up")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_bond * n * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.config}: 8e/8o + 24 virtual, M={args.M}, {args.h0} H0",
+                       "h0": args.h0, "M": args.M},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    from paper_1408_5092_gb300 import _lib as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    L.load()
+    h, Lc, c, ci = _inputs(args.config)
+    k = h.shape[0]
+    stream = torch.cuda.current_stream()
+    o = L.mpspt_default_options()
+    o.device = local
+    o.stream = stream.cuda_stream
+    o.prec = L.PREC[args.prec]
+    o.e_tol = args.e_tol
+    ctx = L.mpspt_create(o)
+    L.mpspt_set_integrals(ctx, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
+    L.mpspt_set_reference(ctx, ci)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one():
+        flush.zero_()
+        torch.cuda.synchronize()
+        e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, args.h0, args.M, want_psi1=False)
+        return e2, rep
+
+    e2_ref = None
+    for w in range(args.warmup):
+        e2, rep = one()
+        if e2_ref is None:
+            e2_ref = e2
+    if e2_ref is None:
+        e2_ref = one()[0]
+    sampler, cpath = _clock_sampler() if rank == 0 else (None, None)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps, tte, e2s = [], [], []
+    for s in range(args.steps):
+        e2, rep = one()
+        reps.append(rep)
+        e2s.append(e2)
+        t, _ = _time_to_e2(rep, e2_ref)
+        tte.append(t if t is not None else rep.wall_ms / 1e3)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = _clock_summary(sampler, cpath, local) if rank == 0 else None
+    value = statistics.median(tte)
+    ms_per_step = 1e3 * wall / args.steps
+    if dist:
+        t = torch.tensor([value, ms_per_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        value, ms_per_step = float(t[0]), float(t[1])
+        dist.barrier()
+    # end to end through the public API with host buffers
+    e2e_times = []
+    for s in range(args.steps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ctx2 = L.mpspt_create(o)
+        L.mpspt_set_integrals(ctx2, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
+        L.mpspt_set_reference(ctx2, ci)
+        t_setup = time.perf_counter() - t1
+        e2, _, rep = L.mpspt_minimize_hylleraas(ctx2, args.h0, args.M, want_psi1=False)
+        tt, _ = _time_to_e2(rep, e2_ref)
+        e2e_times.append(t_setup + (tt if tt is not None else rep.wall_ms / 1e3))
+        L.mpspt_destroy(ctx2)
+    e2e = statistics.median(e2e_times)
+    if dist:
+        t = torch.tensor([e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t[0])
+    flops = sum(r.sigma_flops for r in reps)
+    sms = sum(r.sigma_ms for r in reps)
+    achieved = flops / (sms * 1e-3) / 1e12 if sms > 0 else 0.0
+    peaks, src = _peaks()
+    if args.prec == "fp64":
+        peak = peaks["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+        peak_note = f"fp64 = {src} bf16 burst x nominal fp64/bf16 ratio"
+    else:
+        peak = peaks["bf16_tflops"]
+        peak_note = f"{src} bf16 burst"
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "sigma_gemm_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            if tj.get("prec") == args.prec and tj.get("M") == args.M and tj.get("h0") == args.h0:
+                traffic = tj.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3+f64"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": f"{args.config}: 8e/8o + 24 virtual, M={args.M}, {args.h0} H0, {args.prec}",
+                   "h0": args.h0, "M": args.M, "prec": args.prec, "l2_flush": True,
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "E2": statistics.median(e2s), "E2_ref": e2_ref,
+        "sweeps": [r.n_sweeps for r in reps],
+        "sigma_tflops": achieved,
+        "roofline": {"bound": "fp64_alu" if args.prec == "fp64" else "tensor", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+                     "traffic": traffic, "peak_source": peak_note,
+                     "kernel": "k_gemm (sigma grouped block GEMM)"},
+        "e2e": {"value": e2e, "unit": "s",
+                "h2d_bytes_per_step": int(h.nbytes + Lc.nbytes + ci.nbytes), "d2h_bytes_per_step": 8},
+        "gpu_launches": int(sum(r.kernel_launches for r in reps)),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        spb, n, per_sweep, t_init = _oracle_sample(args.config, args.h0, args.M, args.ref_budget)
+        sweeps = int(statistics.median(r.n_sweeps for r in reps))
+        val = t_init + spb * per_sweep * sweeps
+        line["cpu_baseline"] = {
+            "value": val, "unit": "s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": (f"oracle first {n} of {per_sweep} bond steps of sweep 1, extrapolated to the "
+                       f"{sweeps} sweeps the GPU run took, plus set-up")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    L.mpspt_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", default="medium")
+    ap.add_argument("--h0", default="dyall", choices=["dyall", "fock"])
+    ap.add_argument("--M", type=int, default=64)
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--e_tol", type=float, default=1e-8)
+    ap.add_argument("--ref_budget", type=float, default=15.0)
+    ap.add_argument("--ref_sweeps", type=int, default=12)
+    ap.add_argument("--no_cpu_baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

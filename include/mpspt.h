@@ -87,6 +87,8 @@ typedef struct {
     double sigma_ms;             /* device time inside them (CUDA events)        */
     double wall_ms;              /* wall time of the minimisation                */
     int max_bond_dim;
+    double sweep_ms[64];         /* wall time at the end of each sweep           */
+    long long kernel_launches;   /* device kernels launched by the minimisation  */
 } mpspt_report;
 
 /* Fills *opt with defaults: device 0, default stream, FP64, 30 sweeps,

@@ -10,7 +10,8 @@ Zeroth-order Hamiltonians on the first-order space X (1-2 virtual electrons):
           projected out, the "one-body Fock operator times many-body
           projectors" of the CASPT2-like choice).
   f_pq = h_pq + sum_tu gamma_tu [(pq|tu) - 1/2 (pu|tq)];  eps_a from
-  diagonalising f_vv (semicanonical virtuals, ascending).
+  diagonalising f_vv (semicanonical virtuals, ascending; each orbital's sign
+  fixed by making its largest-magnitude coefficient positive).
 RHS: since Psi0 has no virtual electrons and Psi1 lies in X (Q = 1 there),
   -Q V Psi0 = -P_X H Psi0, i.e. only the terms of H with at least one virtual
   creator and no virtual annihilator contribute (the "<= 2 external indices"
@@ -123,6 +124,12 @@ class Problem:
         f = self._fock(h, eri, g)
         if semicanonical and self.k_virt > 0:
             eps, U = np.linalg.eigh(f[k_act:, k_act:])
+            # each semicanonical orbital is defined up to sign: make its
+            # largest-magnitude coefficient positive (first one on ties)
+            for j in range(U.shape[1]):
+                i = int(np.argmax(np.abs(U[:, j])))
+                if U[i, j] < 0:
+                    U[:, j] = -U[:, j]
             C = np.eye(self.k)
             C[k_act:, k_act:] = U
             h = C.T @ h @ C

@@ -40,7 +40,8 @@ class mpspt_report(ctypes.Structure):
                 ("max_discarded_weight", ctypes.c_double), ("cg_iters", ctypes.c_longlong),
                 ("sigma_calls", ctypes.c_longlong), ("sigma_flops", ctypes.c_double),
                 ("sigma_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
-                ("max_bond_dim", ctypes.c_int)]
+                ("max_bond_dim", ctypes.c_int), ("sweep_ms", ctypes.c_double * 64),
+                ("kernel_launches", ctypes.c_longlong)]
 
 
 class MpsptError(RuntimeError):

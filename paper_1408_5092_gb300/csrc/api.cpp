@@ -122,6 +122,8 @@ mpspt_status mpspt_minimize_hylleraas(mpspt_ctx* ctx, mpspt_h0 h0, int M, double
             rep->sigma_ms = r.sigma_ms;
             rep->wall_ms = r.wall_ms;
             rep->max_bond_dim = r.max_bond;
+            for (int s = 0; s < rep->n_sweeps && s < 64; ++s) rep->sweep_ms[s] = r.sweep_ms[s];
+            rep->kernel_launches = r.launches;
         }
         *e2 = r.e2;
         if (psi1) {

@@ -318,6 +318,14 @@ void set_reference(Ctx& c, const double* ci, long long n) {
         for (int a = 0; a < kv; ++a)
             for (int b = 0; b < kv; ++b) fvv[(size_t)a * kv + b] = f[(size_t)(ka + a) * k + ka + b];
         jacobi_eigh(kv, fvv, w, U);
+        // sign convention: largest-magnitude coefficient of each orbital positive
+        for (int j = 0; j < kv; ++j) {
+            int im = 0;
+            for (int i = 1; i < kv; ++i)
+                if (std::fabs(U[(size_t)i * kv + j]) > std::fabs(U[(size_t)im * kv + j])) im = i;
+            if (U[(size_t)im * kv + j] < 0)
+                for (int i = 0; i < kv; ++i) U[(size_t)i * kv + j] = -U[(size_t)i * kv + j];
+        }
         std::vector<double> C((size_t)k * k, 0.0);
         for (int t = 0; t < ka; ++t) C[(size_t)t * k + t] = 1.0;
         for (int a = 0; a < kv; ++a)
@@ -745,7 +753,7 @@ struct Sweeper {
         std::vector<CopyTask> ct;
         gc.clear();
         if (dir == 0) {
-            MPSPT_CUDA(cudaMemsetAsync(An.d.get(), 0, An.n * sizeof(double) + 8, c.st));
+            if (An.n) MPSPT_CUDA(cudaMemsetAsync(An.d.get(), 0, An.n * sizeof(double), c.st));
             for (const auto& b : An.blk) {
                 const int ci = std::find_if(cl.begin(), cl.end(), [&](const Comp& cp) { return cp.q == nb.sec[b.sr].q; }) - cl.begin();
                 const Comp& cp = cl[ci];
@@ -773,7 +781,7 @@ struct Sweeper {
                 gc.block(Bn.ptr(b), bR.sec[b.sr].dim, kq, bR.sec[b.sr].dim, 0, m0);
             }
         } else {
-            MPSPT_CUDA(cudaMemsetAsync(Bn.d.get(), 0, Bn.n * sizeof(double) + 8, c.st));
+            if (Bn.n) MPSPT_CUDA(cudaMemsetAsync(Bn.d.get(), 0, Bn.n * sizeof(double), c.st));
             for (const auto& b : Bn.blk) {
                 const int ci = std::find_if(cl.begin(), cl.end(), [&](const Comp& cp) { return cp.q == nb.sec[b.sl].q; }) - cl.begin();
                 const Comp& cp = cl[ci];
@@ -916,6 +924,12 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
     require(c.opt.prec == MPSPT_FP64, "only the float64 local solver is available in this build",
             MPSPT_ERR_INVALID);
     const auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = launch_count();
+    // device timeline: an event at entry and one at the end of every sweep
+    cudaEvent_t e_start;
+    std::vector<cudaEvent_t> e_sweep;
+    MPSPT_CUDA(cudaEventCreate(&e_start));
+    MPSPT_CUDA(cudaEventRecord(e_start, c.st));
     const Problem& P = c.P;
     // initial Psi1
     MpsHost ih;
@@ -950,6 +964,10 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
         for (int i = 0; i <= P.k - 2; ++i) e = sw.step(i, 0);
         for (int i = P.k - 2; i >= 0; --i) e = sw.step(i, 1);
         res.e2_sweep.push_back(e);
+        cudaEvent_t ev;
+        MPSPT_CUDA(cudaEventCreate(&ev));
+        MPSPT_CUDA(cudaEventRecord(ev, c.st));
+        e_sweep.push_back(ev);
         if (c.opt.verbose)
             fprintf(stderr, "[mpspt] sweep %d  E2 = %.12f  max discarded %.3e  cg %lld\n", s, e,
                     res.max_disc, res.cg_iters);
@@ -957,6 +975,15 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
         prev = e;
     }
     res.e2 = res.e2_sweep.back();
+    res.launches = launch_count() - l0;
+    MPSPT_CUDA(cudaStreamSynchronize(c.st));
+    for (cudaEvent_t ev : e_sweep) {
+        float ms = 0.f;
+        MPSPT_CUDA(cudaEventElapsedTime(&ms, e_start, ev));
+        res.sweep_ms.push_back(ms);
+        cudaEventDestroy(ev);
+    }
+    cudaEventDestroy(e_start);
     res.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return psi;
 }

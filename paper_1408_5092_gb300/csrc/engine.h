@@ -70,6 +70,8 @@ struct SweepResult {
     long long cg_iters = 0, sigma_calls = 0;
     double sigma_flops = 0.0, sigma_ms = 0.0, wall_ms = 0.0;
     int max_bond = 0;
+    std::vector<double> sweep_ms;
+    long long launches = 0;
 };
 
 std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res);

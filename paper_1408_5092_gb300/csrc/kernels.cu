@@ -4,10 +4,14 @@
 // kernels with deterministic (fixed-order) reductions.
 #include "kernels.h"
 
+#include <atomic>
 #include <cstdio>
 
 namespace mpspt {
 namespace {
+
+std::atomic<long long> g_launches{0};
+inline void counted() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 constexpr int TK = 16;
 constexpr int NT = 256;
@@ -382,51 +386,53 @@ inline int ew_grid(size_t n) {
 
 }  // namespace
 
+long long launch_count() { return g_launches.load(); }
+
 void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st) {
-    if (ntask > 0) k_gemm<double, GemmTask, GemmOp><<<ntask, NT, 0, st>>>(tasks, ops, nullptr);
+    if (ntask > 0) { counted(); k_gemm<double, GemmTask, GemmOp><<<ntask, NT, 0, st>>>(tasks, ops, nullptr); }
 }
 void launch_gemm_f32(const GemmTaskF* tasks, int ntask, const GemmOpF* ops, cudaStream_t st) {
-    if (ntask > 0) k_gemm<float, GemmTaskF, GemmOpF><<<ntask, NT, 0, st>>>(tasks, ops, nullptr);
+    if (ntask > 0) { counted(); k_gemm<float, GemmTaskF, GemmOpF><<<ntask, NT, 0, st>>>(tasks, ops, nullptr); }
 }
 void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaStream_t st) {
-    if (ntask > 0) k_diag<<<ntask, 256, 0, st>>>(tasks, terms);
+    if (ntask > 0) { counted(); k_diag<<<ntask, 256, 0, st>>>(tasks, terms); }
 }
 void launch_eig(const EigTask* tasks, int ntask, cudaStream_t st) {
-    if (ntask > 0) k_eig<<<ntask, 512, 0, st>>>(tasks);
+    if (ntask > 0) { counted(); k_eig<<<ntask, 512, 0, st>>>(tasks); }
 }
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st) {
-    if (ntask > 0) k_copy<<<ntask, 256, 0, st>>>(tasks);
+    if (ntask > 0) { counted(); k_copy<<<ntask, 256, 0, st>>>(tasks); }
 }
 void vec_zero(double* x, size_t n, cudaStream_t st) { if (n) k_zero<<<ew_grid(n), 256, 0, st>>>(x, n); }
 void vec_scale_mask(double* y, const double* x, double a, size_t n, cudaStream_t st) {
-    if (n) k_scale<<<ew_grid(n), 256, 0, st>>>(y, x, a, n);
+    if (n) { counted(); k_scale<<<ew_grid(n), 256, 0, st>>>(y, x, a, n); }
 }
 void vec_axpy(double* y, const double* x, double a, size_t n, cudaStream_t st) {
-    if (n) k_axpy<<<ew_grid(n), 256, 0, st>>>(y, x, a, n);
+    if (n) { counted(); k_axpy<<<ew_grid(n), 256, 0, st>>>(y, x, a, n); }
 }
 void vec_dot(const double* x, const double* y, size_t n, double* out, double* scratch,
              unsigned* counter, cudaStream_t st) {
-    k_dot<<<red_grid(n), RB, 0, st>>>(x, y, n, out, scratch, counter);
+    counted(); k_dot<<<red_grid(n), RB, 0, st>>>(x, y, n, out, scratch, counter);
 }
 void f64_to_f32(float* y, const double* x, size_t n, cudaStream_t st) {
-    if (n) k_d2f<<<ew_grid(n), 256, 0, st>>>(y, x, n);
+    if (n) { counted(); k_d2f<<<ew_grid(n), 256, 0, st>>>(y, x, n); }
 }
 void f32_to_f64(double* y, const float* x, size_t n, cudaStream_t st) {
-    if (n) k_f2d<<<ew_grid(n), 256, 0, st>>>(y, x, n);
+    if (n) { counted(); k_f2d<<<ew_grid(n), 256, 0, st>>>(y, x, n); }
 }
 void make_minv(double* minv, const double* diag, size_t n, cudaStream_t st) {
-    if (n) k_minv<<<ew_grid(n), 256, 0, st>>>(minv, diag, n);
+    if (n) { counted(); k_minv<<<ew_grid(n), 256, 0, st>>>(minv, diag, n); }
 }
 void cg_init(double* r, double* z, double* p, const double* b, const double* Ax,
              const double* minv, size_t n, CgState* S, double tol, double* scratch,
              unsigned* counter, cudaStream_t st) {
-    k_cg_init<<<red_grid(n), RB, 0, st>>>(r, z, p, b, Ax, minv, n, S, tol, scratch, counter);
+    counted(); k_cg_init<<<red_grid(n), RB, 0, st>>>(r, z, p, b, Ax, minv, n, S, tol, scratch, counter);
 }
 void cg_step(double* x, double* r, double* z, double* p, const double* Ap, const double* minv,
              size_t n, CgState* S, double* scratch, unsigned* counter, cudaStream_t st) {
-    k_cg_pap<<<red_grid(n), RB, 0, st>>>(p, Ap, n, S, scratch, counter);
-    k_cg_update<<<red_grid(n), RB, 0, st>>>(x, r, z, p, Ap, minv, n, S, scratch, counter);
-    k_cg_dir<<<ew_grid(n), 256, 0, st>>>(p, z, n, S);
+    counted(); k_cg_pap<<<red_grid(n), RB, 0, st>>>(p, Ap, n, S, scratch, counter);
+    counted(); k_cg_update<<<red_grid(n), RB, 0, st>>>(x, r, z, p, Ap, minv, n, S, scratch, counter);
+    counted(); k_cg_dir<<<ew_grid(n), 256, 0, st>>>(p, z, n, S);
 }
 
 }  // namespace mpspt

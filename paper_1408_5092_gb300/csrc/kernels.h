@@ -86,6 +86,9 @@ struct CgState {
     int done, iters, not_spd, pad;
 };
 
+// Number of kernels launched by this library in this process.
+long long launch_count();
+
 void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st);
 void launch_gemm_f32(const GemmTaskF* tasks, int ntask, const GemmOpF* ops, cudaStream_t st);
 void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaStream_t st);
