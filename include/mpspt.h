@@ -87,8 +87,12 @@ typedef struct {
     double sigma_ms;             /* device time inside them (CUDA events)        */
     double wall_ms;              /* wall time of the minimisation                */
     int max_bond_dim;
-    double sweep_ms[64];         /* wall time at the end of each sweep           */
+    double sweep_ms[64];         /* device time at the end of each sweep         */
     long long kernel_launches;   /* device kernels launched by the minimisation  */
+    long long sigma64_calls;     /* float64 applications used for residual       */
+    double sigma64_flops;        /*   refinement and the Hylleraas value when    */
+    double sigma64_ms;           /*   prec != FP64 (sigma_* then count the       */
+                                 /*   inner low-precision applications)          */
 } mpspt_report;
 
 /* Fills *opt with defaults: device 0, default stream, FP64, 30 sweeps,

@@ -41,7 +41,8 @@ class mpspt_report(ctypes.Structure):
                 ("sigma_calls", ctypes.c_longlong), ("sigma_flops", ctypes.c_double),
                 ("sigma_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
                 ("max_bond_dim", ctypes.c_int), ("sweep_ms", ctypes.c_double * 64),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("sigma64_calls", ctypes.c_longlong),
+                ("sigma64_flops", ctypes.c_double), ("sigma64_ms", ctypes.c_double)]
 
 
 class MpsptError(RuntimeError):

@@ -124,6 +124,9 @@ mpspt_status mpspt_minimize_hylleraas(mpspt_ctx* ctx, mpspt_h0 h0, int M, double
             rep->max_bond_dim = r.max_bond;
             for (int s = 0; s < rep->n_sweeps && s < 64; ++s) rep->sweep_ms[s] = r.sweep_ms[s];
             rep->kernel_launches = r.launches;
+            rep->sigma64_calls = r.sigma64_calls;
+            rep->sigma64_flops = r.sigma64_flops;
+            rep->sigma64_ms = r.sigma64_ms;
         }
         *e2 = r.e2;
         if (psi1) {

@@ -20,6 +20,8 @@ Ctx::Ctx(const mpspt_options& o) : opt(o) {
     MPSPT_CUDA(cudaMemsetAsync(cnt.get(), 0, 64, st));
     cg.alloc(sizeof(CgState), st);
     scal.alloc(16 * sizeof(double), st);
+    tcerr.alloc(sizeof(int) * 4, st);
+    MPSPT_CUDA(cudaMemsetAsync(tcerr.get(), 0, sizeof(int) * 4, st));
     MPSPT_CUDA(cudaMallocHost(&cg_host, sizeof(CgState)));
     MPSPT_CUDA(cudaMallocHost(&scal_host, 16 * sizeof(double)));
 }
@@ -505,11 +507,18 @@ std::vector<Bond> initial_bonds(int nsite, QN target, const std::vector<std::vec
 namespace {
 
 struct Work {
-    DBuf x, g, b, r, z, p, Ap, minv, x0;
+    DBuf x, g, b, r, z, p, Ap, minv, x0, d, ri, zero;
+    size_t nzero = 0;
     void ensure(size_t n, size_t n0, cudaStream_t st) {
         const size_t by = (n + 1) * sizeof(double);
         x.ensure(by, st); g.ensure(by, st); b.ensure(by, st); r.ensure(by, st); z.ensure(by, st);
         p.ensure(by, st); Ap.ensure(by, st); minv.ensure(by, st);
+        d.ensure(by, st); ri.ensure(by, st);
+        if (zero.bytes() < by || nzero < n) {
+            zero.ensure(by, st);
+            MPSPT_CUDA(cudaMemsetAsync(zero.get(), 0, zero.bytes(), st));
+            nzero = zero.bytes() / sizeof(double);
+        }
         x0.ensure((n0 + 1) * sizeof(double), st);
     }
 };
@@ -558,8 +567,9 @@ struct Sweeper {
     Work w;
     TwoT X, X0;
     Omega omA, omV;
-    TwoSitePlan sig, rhs;
+    TwoSitePlan sig, sig_lo, rhs;   // sig: float64; sig_lo: inner operator when prec != FP64
     DiagPlan dia;
+    int lo_kind = GEMM_F64;
     GemmPlan prod, prod0, gr, gc;
     EnvPlan envp;
     DBuf rho, V, wv, ctasks, cols, etasks;
@@ -571,6 +581,9 @@ struct Sweeper {
         filt = cut_filters(P);
         const int k = P.k;
         LA.resize(k + 1); LV.resize(k + 1); RA.resize(k + 1); RV.resize(k + 1);
+        if (c.opt.prec == MPSPT_MIXED_BF16) lo_kind = GEMM_TC;
+        else if (c.opt.prec == MPSPT_FP32) lo_kind = GEMM_F32;
+        sig_lo.set_kind(lo_kind, c.tcerr.as<int>());
         MPSPT_CUDA(cudaEventCreate(&ev0));
         MPSPT_CUDA(cudaEventCreate(&ev1));
     }
@@ -834,24 +847,126 @@ struct Sweeper {
         }
     }
 
-    double sigma(double* in_out_dummy = nullptr) {
-        (void)in_out_dummy;
-        MPSPT_CUDA(cudaEventRecord(ev0, c.st));
-        sig.run(c.st);
-        MPSPT_CUDA(cudaEventRecord(ev1, c.st));
-        res->sigma_calls++;
-        res->sigma_flops += sig.flops();
-        return 0.0;
-    }
-
-    void add_sigma_time() {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) res->sigma_ms += ms;
-    }
-
     double dot(const double* a, const double* b, size_t n, int slot) {
         vec_dot(a, b, n, c.scal.as<double>() + slot, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
         return 0.0;
+    }
+
+    void sigma64() {
+        MPSPT_CUDA(cudaEventRecord(ev0, c.st));
+        sig.run(c.st);
+        MPSPT_CUDA(cudaEventRecord(ev1, c.st));
+        res->sigma64_calls++;
+        res->sigma64_flops += sig.flops();
+        pending64 = true;
+    }
+    void sigma_lo() {
+        MPSPT_CUDA(cudaEventRecord(ev0, c.st));
+        sig_lo.run(c.st);
+        MPSPT_CUDA(cudaEventRecord(ev1, c.st));
+        res->sigma_calls++;
+        res->sigma_flops += sig_lo.flops();
+        pending64 = false;
+    }
+    bool pending64 = false;
+    void add_time() {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev0, ev1) != cudaSuccess) return;
+        if (pending64) res->sigma64_ms += ms;
+        else res->sigma_ms += ms;
+    }
+    void sync_state() {
+        MPSPT_CUDA(cudaMemcpyAsync(c.cg_host, c.cg.as<CgState>(), sizeof(CgState), cudaMemcpyDeviceToHost, c.st));
+        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        add_time();
+    }
+    void check_tc() {
+        if (lo_kind != GEMM_TC) return;
+        int e = 0;
+        MPSPT_CUDA(cudaMemcpyAsync(&e, c.tcerr.get(), sizeof(int), cudaMemcpyDeviceToHost, c.st));
+        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        require(e == 0, "tensor-core GEMM: bounded mbarrier wait gave up", MPSPT_ERR_TIMEOUT);
+    }
+
+    // Hylleraas value x.Ax + 2 x.g, Ax already in w.Ap (float64)
+    double hylleraas(size_t n) {
+        double* x = w.x.as<double>();
+        dot(x, w.Ap.as<double>(), n, 0);
+        dot(x, w.g.as<double>(), n, 1);
+        MPSPT_CUDA(cudaMemcpyAsync(c.scal_host, c.scal.get(), 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        return c.scal_host[0] + 2.0 * c.scal_host[1];
+    }
+
+    // Plain float64 Jacobi-PCG on A x = b from the warm start x.
+    double solve_plain(size_t n) {
+        double* x = w.x.as<double>();
+        CgState* S = c.cg.as<CgState>();
+        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+        sigma64();
+        cg_init(w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.b.as<double>(), w.Ap.as<double>(),
+                w.minv.as<double>(), n, S, c.opt.cg_tol, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
+        sync_state();
+        int it = 0;
+        while (!c.cg_host->done && it < c.opt.cg_max_iter) {
+            sigma64();
+            cg_step(x, w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.Ap.as<double>(),
+                    w.minv.as<double>(), n, S, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
+            sync_state();
+            ++it;
+        }
+        require(!c.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
+                MPSPT_ERR_NOT_SPD);
+        res->cg_iters += it;
+        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+        sigma64();
+        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        add_time();
+        return hylleraas(n);
+    }
+
+    // Iterative refinement: float64 residual r = b - A x, inner PCG on
+    // A d = r with the low-precision operator, x += d, until the float64
+    // residual meets cg_tol.  The last float64 A x gives the Hylleraas value.
+    double solve_refined(size_t n) {
+        double* x = w.x.as<double>();
+        CgState* S = c.cg.as<CgState>();
+        const int max_outer = 12;
+        const double tol_in = 1e-4;
+        dot(w.b.as<double>(), w.b.as<double>(), n, 2);
+        for (int outer = 0;; ++outer) {
+            MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+            sigma64();
+            MPSPT_CUDA(cudaMemcpyAsync(w.r.get(), w.b.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+            vec_axpy(w.r.as<double>(), w.Ap.as<double>(), -1.0, n, c.st);
+            dot(w.r.as<double>(), w.r.as<double>(), n, 3);
+            MPSPT_CUDA(cudaMemcpyAsync(c.scal_host, c.scal.get(), 4 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+            MPSPT_CUDA(cudaStreamSynchronize(c.st));
+            add_time();
+            const double bb = c.scal_host[2], rr = c.scal_host[3];
+            if (rr <= c.opt.cg_tol * c.opt.cg_tol * bb || bb == 0.0 || outer == max_outer) break;
+            // inner solve from d = 0 (the Ap buffer is reused by the inner operator)
+            MPSPT_CUDA(cudaMemsetAsync(w.d.get(), 0, n * sizeof(double), c.st));
+            cg_init(w.ri.as<double>(), w.z.as<double>(), w.p.as<double>(), w.r.as<double>(),
+                    w.zero.as<double>(), w.minv.as<double>(), n, S, tol_in, c.red.as<double>(),
+                    c.cnt.as<unsigned>(), c.st);
+            MPSPT_CUDA(cudaMemcpyAsync(c.cg_host, S, sizeof(CgState), cudaMemcpyDeviceToHost, c.st));
+            MPSPT_CUDA(cudaStreamSynchronize(c.st));
+            int it = 0;
+            while (!c.cg_host->done && it < c.opt.cg_max_iter) {
+                sigma_lo();
+                cg_step(w.d.as<double>(), w.ri.as<double>(), w.z.as<double>(), w.p.as<double>(),
+                        w.Ap.as<double>(), w.minv.as<double>(), n, S, c.red.as<double>(),
+                        c.cnt.as<unsigned>(), c.st);
+                sync_state();
+                ++it;
+            }
+            require(!c.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
+                    MPSPT_ERR_NOT_SPD);
+            res->cg_iters += it;
+            vec_axpy(x, w.d.as<double>(), 1.0, n, c.st);
+        }
+        return hylleraas(n);   // w.Ap holds the float64 A x of the final x
     }
 
     // one bond step; returns h_loc
@@ -875,37 +990,11 @@ struct Sweeper {
         dia.run(c.st);
         make_minv(w.minv.as<double>(), w.minv.as<double>(), n, c.st);
         vec_scale_mask(w.b.as<double>(), w.g.as<double>(), -1.0, n, c.st);
-        // CG on A x = -g from the warm start
-        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
-        sigma();
-        CgState* S = c.cg.as<CgState>();
-        cg_init(w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.b.as<double>(), w.Ap.as<double>(),
-                w.minv.as<double>(), n, S, c.opt.cg_tol, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
-        MPSPT_CUDA(cudaMemcpyAsync(c.cg_host, S, sizeof(CgState), cudaMemcpyDeviceToHost, c.st));
-        MPSPT_CUDA(cudaStreamSynchronize(c.st));
-        add_sigma_time();
-        int it = 0;
-        while (!c.cg_host->done && it < c.opt.cg_max_iter) {
-            sigma();
-            cg_step(x, w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.Ap.as<double>(),
-                    w.minv.as<double>(), n, S, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
-            MPSPT_CUDA(cudaMemcpyAsync(c.cg_host, S, sizeof(CgState), cudaMemcpyDeviceToHost, c.st));
-            MPSPT_CUDA(cudaStreamSynchronize(c.st));
-            add_sigma_time();
-            ++it;
-        }
-        require(!c.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
-                MPSPT_ERR_NOT_SPD);
-        res->cg_iters += it;
-        // Hylleraas value h = x.Ax + 2 x.g in float64
-        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
-        sigma();
-        dot(x, w.Ap.as<double>(), n, 0);
-        dot(x, w.g.as<double>(), n, 1);
-        MPSPT_CUDA(cudaMemcpyAsync(c.scal_host, c.scal.get(), 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
-        MPSPT_CUDA(cudaStreamSynchronize(c.st));
-        add_sigma_time();
-        const double h = c.scal_host[0] + 2.0 * c.scal_host[1];
+        if (lo_kind != GEMM_F64)
+            sig_lo.build(omA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
+                         w.Ap.as<double>(), c.st);
+        const double h = (lo_kind == GEMM_F64) ? solve_plain(n) : solve_refined(n);
+        check_tc();
         const double disc = split(i, dir, M, X, x);
         res->max_disc = std::max(res->max_disc, disc);
         res->max_bond = std::max(res->max_bond, psi.bond[i + 1].total);
@@ -921,8 +1010,8 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
     require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
     require(M >= 1, "bond dimension M must be >= 1");
     require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
-    require(c.opt.prec == MPSPT_FP64, "only the float64 local solver is available in this build",
-            MPSPT_ERR_INVALID);
+    require(c.opt.prec == MPSPT_FP64 || c.opt.prec == MPSPT_FP32 || c.opt.prec == MPSPT_MIXED_BF16,
+            "unknown precision mode");
     const auto t0 = std::chrono::steady_clock::now();
     const long long l0 = launch_count();
     // device timeline: an event at entry and one at the end of every sweep
@@ -976,6 +1065,9 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
     }
     res.e2 = res.e2_sweep.back();
     res.launches = launch_count() - l0;
+    if (c.opt.prec == MPSPT_FP64) {   // all applications are float64: report them as sigma
+        res.sigma_calls = res.sigma64_calls; res.sigma_flops = res.sigma64_flops; res.sigma_ms = res.sigma64_ms;
+    }
     MPSPT_CUDA(cudaStreamSynchronize(c.st));
     for (cudaEvent_t ev : e_sweep) {
         float ms = 0.f;
@@ -1046,9 +1138,11 @@ void local_apply(Ctx& c, int h0, const MpsD& psi1_in, int i, int op, const doubl
     double* dout = sw.w.Ap.as<double>();
     if (op == MPSPT_LOCAL_SIGMA) {
         sw.omA.build(sw.WA, i);
-        sw.sig.build(sw.omA, X, X, bL, bL, bR, bR, sw.LA[i], sw.RA[i + 2], sw.WA.dq[i + 2],
-                     sw.w.p.as<double>(), dout, c.st);
-        sw.sig.run(c.st);
+        TwoSitePlan& pl = (sw.lo_kind == GEMM_F64) ? sw.sig : sw.sig_lo;
+        pl.build(sw.omA, X, X, bL, bL, bR, bR, sw.LA[i], sw.RA[i + 2], sw.WA.dq[i + 2],
+                 sw.w.p.as<double>(), dout, c.st);
+        pl.run(c.st);
+        sw.check_tc();
     } else if (op == MPSPT_LOCAL_RHS) {
         TwoT X0;
         X0.build(c.psi0.bond[i], c.psi0.bond[i + 2], {});

@@ -48,6 +48,7 @@ struct Ctx {
     CgState* cg_host = nullptr;           // pinned mirror
     double* scal_host = nullptr;          // pinned scalars
     DBuf scal;
+    DBuf tcerr;                           // tensor-core kernel error flag
     std::string last_error;
 
     explicit Ctx(const mpspt_options& o);
@@ -72,6 +73,8 @@ struct SweepResult {
     int max_bond = 0;
     std::vector<double> sweep_ms;
     long long launches = 0;
+    long long sigma64_calls = 0;
+    double sigma64_flops = 0.0, sigma64_ms = 0.0;
 };
 
 std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res);

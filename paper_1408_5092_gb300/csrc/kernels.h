@@ -88,6 +88,15 @@ struct CgState {
 
 // Number of kernels launched by this library in this process.
 long long launch_count();
+void count_launch();
+
+// Split-bfloat16 tcgen05 variant of the grouped GEMM (tiles 128 x 64; same
+// task format).  *err is set to 1 if a bounded mbarrier wait gave up.
+int tc_tile_m();
+int tc_tile_n();
+void launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmOp* ops, int* err, cudaStream_t st);
+// Float32-arithmetic variant of the float64 grouped GEMM (float64 in/out).
+void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st);
 
 void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st);
 void launch_gemm_f32(const GemmTaskF* tasks, int ntask, const GemmOpF* ops, cudaStream_t st);

@@ -11,8 +11,8 @@ void GemmPlan::block(double* C, int ldc, int m, int n, int accumulate, int op0) 
     if (m <= 0 || n <= 0) return;
     const int op1 = (int)ops.size();
     for (int o = op0; o < op1; ++o) flops += 2.0 * m * n * ops[o].k;
-    for (int r0 = 0; r0 < m; r0 += GEMM_TM)
-        for (int c0 = 0; c0 < n; c0 += GEMM_TN)
+    for (int r0 = 0; r0 < m; r0 += tm)
+        for (int c0 = 0; c0 < n; c0 += tn)
             tasks.push_back({C, ldc, m, n, r0, c0, op0, op1, accumulate, 0});
 }
 
@@ -37,7 +37,9 @@ void GemmPlan::upload(cudaStream_t st) {
 }
 
 void GemmPlan::run(cudaStream_t st) const {
-    launch_gemm_f64(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), st);
+    if (kind == GEMM_TC) launch_gemm_tc(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), err, st);
+    else if (kind == GEMM_F32) launch_gemm_f64in_f32(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), st);
+    else launch_gemm_f64(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), st);
 }
 
 void Omega::build(const MPO& W, int i) {

@@ -7,7 +7,17 @@
 
 namespace mpspt {
 
+enum GemmKind { GEMM_F64 = 0, GEMM_F32 = 1, GEMM_TC = 2 };
+
 struct GemmPlan {
+    int tm = GEMM_TM, tn = GEMM_TN;   // output tile (TC kernel: 128 x 64)
+    int kind = GEMM_F64;
+    int* err = nullptr;               // TC kernel error flag (device)
+    void set_kind(int k, int* e) {
+        kind = k;
+        err = e;
+        if (k == GEMM_TC) { tm = tc_tile_m(); tn = tc_tile_n(); } else { tm = GEMM_TM; tn = GEMM_TN; }
+    }
     std::vector<GemmTask> tasks;
     std::vector<GemmOp> ops;
     double flops = 0.0;   // algorithmic: sum over ops of 2 m n k (each product once)
@@ -38,6 +48,7 @@ struct TwoSitePlan {
     GemmPlan g1, g2;
     DBuf T;
     size_t tsize = 0;
+    void set_kind(int k, int* e) { g1.set_kind(k, e); g2.set_kind(k, e); }
     void build(const Omega& om, const TwoT& bra, const TwoT& ket, const Bond& braL,
                const Bond& ketL, const Bond& braR, const Bond& ketR, const EnvT& L,
                const EnvT& R, const std::vector<QN>& dqR, const double* x, double* out,

@@ -142,3 +142,53 @@ def test_bond_dimension_one_is_an_upper_bound(L, tiny, gold):
     assert rep.max_bond_dim == 1
     L.mpspt_mps_free(psi)
     L.mpspt_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("mixed", 2e-4)])
+def test_low_precision_sigma_matches_oracle(L, tiny, prec, tol):
+    """Inner operator of the refined CG: float32 CUDA cores / split-bf16 tensor
+    cores.  Relative max-norm error bounded by the arithmetic: float32 keeps
+    24 bits (2^-24 ~ 6e-8 per product, summed over the K-lists); the three-term
+    bf16 split keeps about 16 bits (3 x 2^-17 ~ 2.3e-5 per product)."""
+    from oracle.mps import HylleraasSweep, two_site_apply, two_site_mask
+    from oracle.operators import Problem
+    h, Lc, c, ci = tiny
+    p = Problem(h, Lc, c["k_act"], c["n_elec"], ci, h0="dyall")
+    sw = HylleraasSweep(p, 32, seed=11)
+    ctx = _session(L, tiny, prec=L.PREC[prec])
+    psi = L.mpspt_mps_import(ctx, sw.psi1.A, sw.psi1.q)
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for i in (0, 2, 3, 4, 6, 10):
+        for s in range(i):
+            sw._update_left(s)
+        mask = two_site_mask(sw.psi1.q[i], sw.psi1.q[i + 2], sw.allowed.get(i + 1))
+        x = rng.normal(size=mask.shape) * mask
+        ref = two_site_apply(sw.LA[i], sw.WA.W[i], sw.WA.W[i + 1], sw.RA[i + 2], x, sw.WA.dims[i + 1]) * mask
+        got = L.mpspt_local_apply(ctx, "dyall", psi, i, L.MPSPT_LOCAL_SIGMA, x, x.shape)
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        worst = max(worst, err)
+        sw.LA[1:] = [None] * (len(sw.LA) - 1)
+        sw.LV[1:] = [None] * (len(sw.LV) - 1)
+    assert worst < tol, worst
+    L.mpspt_mps_free(psi)
+    L.mpspt_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("h0", ["fock", "dyall"])
+def test_refined_e2_matches_oracle(L, tiny, gold, prec, h0):
+    """Float64-refined CG with a low-precision inner operator: E2 and E3 to
+    1e-6 Eh of the float64 oracle at equal M (the Hylleraas value itself is
+    evaluated with a float64 sigma)."""
+    g = gold["h0"][h0]
+    run = g["runs"]["32"]
+    ctx = _session(L, tiny, prec=L.PREC[prec])
+    e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, h0, 32)
+    assert abs(e2 - run["E2"]) < 1e-6, (e2, run["E2"])
+    assert e2 >= g["E2_exact"] - 1e-10
+    e3 = L.mpspt_third_order(ctx, h0, psi)
+    assert abs(e3 - run["E3"]) < 1e-6, (e3, run["E3"])
+    assert rep.sigma_calls > 0 and rep.sigma64_calls > 0
+    L.mpspt_mps_free(psi)
+    L.mpspt_destroy(ctx)
