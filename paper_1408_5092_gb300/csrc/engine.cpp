@@ -907,17 +907,24 @@ struct Sweeper {
         cg_init(w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.b.as<double>(), w.Ap.as<double>(),
                 w.minv.as<double>(), n, S, c.opt.cg_tol, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
         sync_state();
-        int it = 0;
-        while (!c.cg_host->done && it < c.opt.cg_max_iter) {
-            sigma64();
-            cg_step(x, w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.Ap.as<double>(),
-                    w.minv.as<double>(), n, S, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
+        int launched = 0;
+        sig.set_skip(&S->done);
+        while (!c.cg_host->done && launched < c.opt.cg_max_iter) {
+            const int chunk = std::min(c.opt.cg_max_iter - launched, launched < 8 ? 4 : 8);
+            for (int q = 0; q < chunk; ++q) {
+                sigma64();
+                cg_step(x, w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.Ap.as<double>(),
+                        w.minv.as<double>(), n, S, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
+            }
+            launched += chunk;
             sync_state();
-            ++it;
         }
+        sig.set_skip(nullptr);
         require(!c.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
                 MPSPT_ERR_NOT_SPD);
-        res->cg_iters += it;
+        res->cg_iters += c.cg_host->iters;
+        res->sigma64_calls -= launched - c.cg_host->iters;   // skipped launches did no work
+        res->sigma64_flops -= (launched - c.cg_host->iters) * sig.flops();
         MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
         sigma64();
         MPSPT_CUDA(cudaStreamSynchronize(c.st));
@@ -952,25 +959,38 @@ struct Sweeper {
                     c.cnt.as<unsigned>(), c.st);
             MPSPT_CUDA(cudaMemcpyAsync(c.cg_host, S, sizeof(CgState), cudaMemcpyDeviceToHost, c.st));
             MPSPT_CUDA(cudaStreamSynchronize(c.st));
-            int it = 0;
-            while (!c.cg_host->done && it < c.opt.cg_max_iter) {
-                sigma_lo();
-                cg_step(w.d.as<double>(), w.ri.as<double>(), w.z.as<double>(), w.p.as<double>(),
-                        w.Ap.as<double>(), w.minv.as<double>(), n, S, c.red.as<double>(),
-                        c.cnt.as<unsigned>(), c.st);
+            int launched = 0;
+            sig_lo.set_skip(&S->done);
+            while (!c.cg_host->done && launched < c.opt.cg_max_iter) {
+                const int chunk = std::min(c.opt.cg_max_iter - launched, launched < 8 ? 4 : 8);
+                for (int q = 0; q < chunk; ++q) {
+                    sigma_lo();
+                    cg_step(w.d.as<double>(), w.ri.as<double>(), w.z.as<double>(), w.p.as<double>(),
+                            w.Ap.as<double>(), w.minv.as<double>(), n, S, c.red.as<double>(),
+                            c.cnt.as<unsigned>(), c.st);
+                }
+                launched += chunk;
                 sync_state();
-                ++it;
             }
+            sig_lo.set_skip(nullptr);
             require(!c.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
                     MPSPT_ERR_NOT_SPD);
-            res->cg_iters += it;
+            res->cg_iters += c.cg_host->iters;
+            res->sigma_calls -= launched - c.cg_host->iters;
+            res->sigma_flops -= (launched - c.cg_host->iters) * sig_lo.flops();
             vec_axpy(x, w.d.as<double>(), 1.0, n, c.st);
         }
         return hylleraas(n);   // w.Ap holds the float64 A x of the final x
     }
 
     // one bond step; returns h_loc
+    // host-side phase timers (printed with verbose >= 2)
+    double t_plan = 0, t_rhs = 0, t_solve = 0, t_split = 0, t_env = 0;
+    using clk = std::chrono::steady_clock;
+    static double since(clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); }
+
     double step(int i, int dir) {
+        auto t0 = clk::now();
         const Bond &bL = psi.bond[i], &bR = psi.bond[i + 2];
         X.build(bL, bR, filt[i + 1]);
         X0.build(psi0.bond[i], psi0.bond[i + 2], {});
@@ -984,6 +1004,7 @@ struct Sweeper {
         rhs.build(omV, X, X0, bL, psi0.bond[i], bR, psi0.bond[i + 2], LV[i], RV[i + 2], WV.dq[i + 2],
                   w.x0.as<double>(), w.g.as<double>(), c.st);
         rhs.run(c.st);
+        if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(c.st)); t_rhs += since(t0); t0 = clk::now(); }
         sig.build(omA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
                   w.Ap.as<double>(), c.st);
         dia.build(omA, X, bL, bR, LA[i], RA[i + 2], WA.dq[i], WA.dq[i + 2], w.minv.as<double>(), c.st);
@@ -993,13 +1014,17 @@ struct Sweeper {
         if (lo_kind != GEMM_F64)
             sig_lo.build(omA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
                          w.Ap.as<double>(), c.st);
+        if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(c.st)); t_plan += since(t0); t0 = clk::now(); }
         const double h = (lo_kind == GEMM_F64) ? solve_plain(n) : solve_refined(n);
         check_tc();
+        if (c.opt.verbose >= 2) { t_solve += since(t0); t0 = clk::now(); }
         const double disc = split(i, dir, M, X, x);
         res->max_disc = std::max(res->max_disc, disc);
         res->max_bond = std::max(res->max_bond, psi.bond[i + 1].total);
+        if (c.opt.verbose >= 2) { t_split += since(t0); t0 = clk::now(); }
         if (dir == 0) update_left(i);
         else update_right(i + 1);
+        if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(c.st)); t_env += since(t0); }
         return h;
     }
 };
@@ -1060,6 +1085,9 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
         if (c.opt.verbose)
             fprintf(stderr, "[mpspt] sweep %d  E2 = %.12f  max discarded %.3e  cg %lld\n", s, e,
                     res.max_disc, res.cg_iters);
+        if (c.opt.verbose >= 2)
+            fprintf(stderr, "[mpspt]   host ms: rhs %.1f plan %.1f solve %.1f split %.1f env %.1f | sigma dev ms %.1f (64: %.1f)\n",
+                    sw.t_rhs, sw.t_plan, sw.t_solve, sw.t_split, sw.t_env, res.sigma_ms, res.sigma64_ms);
         if (s > 0 && std::fabs(e - prev) < c.opt.e_tol) break;
         prev = e;
     }

@@ -347,7 +347,7 @@ __global__ void k_cg_update(double* x, double* r, double* z, const double* __res
 }
 
 __global__ void k_cg_dir(double* p, const double* __restrict__ z, size_t n, const CgState* S) {
-    if (S->done == 1) return;
+    if (S->done) return;
     const double be = S->beta;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         p[i] = z[i] + be * p[i];
@@ -390,12 +390,14 @@ inline int ew_grid(size_t n) {
 long long launch_count() { return g_launches.load(); }
 void count_launch() { counted(); }
 
-void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st) {
-    if (ntask > 0) { counted(); k_gemm<double, GemmTask, GemmOp, float><<<ntask, NT, 0, st>>>(tasks, ops, nullptr); }
+void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
+                           const int* skip) {
+    if (ntask > 0) { counted(); k_gemm<double, GemmTask, GemmOp, float><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
 }
 
-void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st) {
-    if (ntask > 0) { counted(); k_gemm<double, GemmTask, GemmOp><<<ntask, NT, 0, st>>>(tasks, ops, nullptr); }
+void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
+                     const int* skip) {
+    if (ntask > 0) { counted(); k_gemm<double, GemmTask, GemmOp><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
 }
 void launch_gemm_f32(const GemmTaskF* tasks, int ntask, const GemmOpF* ops, cudaStream_t st) {
     if (ntask > 0) { counted(); k_gemm<float, GemmTaskF, GemmOpF><<<ntask, NT, 0, st>>>(tasks, ops, nullptr); }

@@ -94,11 +94,14 @@ void count_launch();
 // task format).  *err is set to 1 if a bounded mbarrier wait gave up.
 int tc_tile_m();
 int tc_tile_n();
-void launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmOp* ops, int* err, cudaStream_t st);
+void launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmOp* ops, int* err, cudaStream_t st,
+                    const int* skip = nullptr);
 // Float32-arithmetic variant of the float64 grouped GEMM (float64 in/out).
-void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st);
+void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
+                           const int* skip = nullptr);
 
-void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st);
+void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
+                     const int* skip = nullptr);
 void launch_gemm_f32(const GemmTaskF* tasks, int ntask, const GemmOpF* ops, cudaStream_t st);
 void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaStream_t st);
 void launch_eig(const EigTask* tasks, int ntask, cudaStream_t st);

@@ -97,12 +97,15 @@ __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo
 }
 
 __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__ tasks,
-                                                    const GemmOp* __restrict__ ops, int* err) {
+                                                    const GemmOp* __restrict__ ops, int* err,
+                                                    const int* __restrict__ skip) {
+    if (skip && *skip) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t bars[2];
     __shared__ uint32_t tmem_base_sh;
+    __shared__ int wait_ok;
     const GemmTask t = tasks[blockIdx.x];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mrem = min(BM, t.m - t.r0);
@@ -132,7 +135,11 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
         const bool ta = op.trans & 1, tb = op.trans & 2;
         for (int k0 = 0; k0 < op.k; k0 += BK) {
             const int buf = stage & 1;
-            if (stage >= 2 && !mbar_wait(&bars[buf], ((stage - 2) >> 1) & 1)) { ok = false; break; }
+            if (stage >= 2) {   // stage buffer free once the MMAs of stage-2 completed
+                if (tid == 0) wait_ok = mbar_wait(&bars[buf], ((stage - 2) >> 1) & 1) ? 1 : 0;
+                __syncthreads();
+                if (!wait_ok) { ok = false; break; }
+            }
             unsigned char* Ahi = smem + buf * STAGE_BYTES;
             unsigned char* Alo = Ahi + A_BYTES;
             unsigned char* Bhi = Alo + A_BYTES;
@@ -177,11 +184,18 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
         }
     }
     const bool any = stage > 0;
-    if (any && ok && !mbar_wait(&bars[(stage - 1) & 1], ((stage - 1) >> 1) & 1)) ok = false;
+    if (any && ok) {
+        if (tid == 0) wait_ok = mbar_wait(&bars[(stage - 1) & 1], ((stage - 1) >> 1) & 1) ? 1 : 0;
+        __syncthreads();
+        ok = wait_ok != 0;
+    }
     if (!ok) {
-        if (tid == 0) atomicExch(err, 1);
-        // give in-flight MMAs a bounded chance to drain before releasing TMEM
-        if (any) mbar_wait(&bars[(stage - 1) & 1], ((stage - 1) >> 1) & 1);
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // give in-flight MMAs a bounded chance to drain before releasing TMEM
+            if (any) mbar_wait(&bars[(stage - 1) & 1], ((stage - 1) >> 1) & 1);
+        }
+        __syncthreads();
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     // epilogue: warp w owns accumulator rows 32w .. 32w+31 (TMEM lanes)
@@ -225,7 +239,8 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
 int tc_tile_m() { return BM; }
 int tc_tile_n() { return BN; }
 
-void launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmOp* ops, int* err, cudaStream_t st) {
+void launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmOp* ops, int* err, cudaStream_t st,
+                    const int* skip) {
     if (ntask <= 0) return;
     static bool attr = false;
     if (!attr) {
@@ -233,7 +248,7 @@ void launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmOp* ops, int* er
         attr = true;
     }
     count_launch();
-    k_gemm_tc<<<ntask, NTH, SMEM_BYTES, st>>>(tasks, ops, err);
+    k_gemm_tc<<<ntask, NTH, SMEM_BYTES, st>>>(tasks, ops, err, skip);
 }
 
 }  // namespace mpspt

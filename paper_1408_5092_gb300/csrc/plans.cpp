@@ -37,9 +37,9 @@ void GemmPlan::upload(cudaStream_t st) {
 }
 
 void GemmPlan::run(cudaStream_t st) const {
-    if (kind == GEMM_TC) launch_gemm_tc(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), err, st);
-    else if (kind == GEMM_F32) launch_gemm_f64in_f32(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), st);
-    else launch_gemm_f64(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), st);
+    if (kind == GEMM_TC) launch_gemm_tc(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), err, st, skip);
+    else if (kind == GEMM_F32) launch_gemm_f64in_f32(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), st, skip);
+    else launch_gemm_f64(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), st, skip);
 }
 
 void Omega::build(const MPO& W, int i) {

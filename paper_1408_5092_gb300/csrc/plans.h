@@ -13,6 +13,7 @@ struct GemmPlan {
     int tm = GEMM_TM, tn = GEMM_TN;   // output tile (TC kernel: 128 x 64)
     int kind = GEMM_F64;
     int* err = nullptr;               // TC kernel error flag (device)
+    const int* skip = nullptr;        // device flag: launch becomes a no-op when set
     void set_kind(int k, int* e) {
         kind = k;
         err = e;
@@ -49,6 +50,7 @@ struct TwoSitePlan {
     DBuf T;
     size_t tsize = 0;
     void set_kind(int k, int* e) { g1.set_kind(k, e); g2.set_kind(k, e); }
+    void set_skip(const int* s) { g1.skip = s; g2.skip = s; }
     void build(const Omega& om, const TwoT& bra, const TwoT& ket, const Bond& braL,
                const Bond& ketL, const Bond& braR, const Bond& ketR, const EnvT& L,
                const EnvT& R, const std::vector<QN>& dqR, const double* x, double* out,
