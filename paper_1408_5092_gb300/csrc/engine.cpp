@@ -584,10 +584,16 @@ struct Sweeper {
         if (c.opt.prec == MPSPT_MIXED_BF16) lo_kind = GEMM_TC;
         else if (c.opt.prec == MPSPT_FP32) lo_kind = GEMM_F32;
         sig_lo.set_kind(lo_kind, c.tcerr.as<int>());
+        sig.set_kind(GEMM_F64, nullptr);
+        rhs.set_kind(GEMM_F64, nullptr);
         MPSPT_CUDA(cudaEventCreate(&ev0));
         MPSPT_CUDA(cudaEventCreate(&ev1));
+        for (auto& e : evs) MPSPT_CUDA(cudaEventCreate(&e));
     }
-    ~Sweeper() { cudaEventDestroy(ev0); cudaEventDestroy(ev1); }
+    ~Sweeper() {
+        cudaEventDestroy(ev0); cudaEventDestroy(ev1);
+        for (auto& e : evs) cudaEventDestroy(e);
+    }
 
     void boundary_envs() {
         const int k = P.k;
@@ -852,28 +858,44 @@ struct Sweeper {
         return 0.0;
     }
 
+    // every sigma launch pair is bracketed by its own events (ring of 64
+    // pairs); elapsed times are collected at the next host sync
+    static constexpr int NEV = 64;
+    cudaEvent_t evs[2 * NEV];
+    bool ev_is64[NEV];
+    int nev = 0;
+    void ev_begin() {
+        if (nev == NEV) add_time();
+        MPSPT_CUDA(cudaEventRecord(evs[2 * nev], c.st));
+    }
+    void ev_end(bool is64) {
+        MPSPT_CUDA(cudaEventRecord(evs[2 * nev + 1], c.st));
+        ev_is64[nev++] = is64;
+    }
     void sigma64() {
-        MPSPT_CUDA(cudaEventRecord(ev0, c.st));
+        ev_begin();
         sig.run(c.st);
-        MPSPT_CUDA(cudaEventRecord(ev1, c.st));
+        ev_end(true);
         res->sigma64_calls++;
         res->sigma64_flops += sig.flops();
-        pending64 = true;
     }
     void sigma_lo() {
-        MPSPT_CUDA(cudaEventRecord(ev0, c.st));
+        ev_begin();
         sig_lo.run(c.st);
-        MPSPT_CUDA(cudaEventRecord(ev1, c.st));
+        ev_end(false);
         res->sigma_calls++;
         res->sigma_flops += sig_lo.flops();
-        pending64 = false;
     }
-    bool pending64 = false;
     void add_time() {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ev0, ev1) != cudaSuccess) return;
-        if (pending64) res->sigma64_ms += ms;
-        else res->sigma_ms += ms;
+        if (nev == 0) return;
+        MPSPT_CUDA(cudaEventSynchronize(evs[2 * nev - 1]));
+        for (int q = 0; q < nev; ++q) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, evs[2 * q], evs[2 * q + 1]) != cudaSuccess) continue;
+            if (ev_is64[q]) res->sigma64_ms += ms;
+            else res->sigma_ms += ms;
+        }
+        nev = 0;
     }
     void sync_state() {
         MPSPT_CUDA(cudaMemcpyAsync(c.cg_host, c.cg.as<CgState>(), sizeof(CgState), cudaMemcpyDeviceToHost, c.st));

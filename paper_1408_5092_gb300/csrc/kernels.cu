@@ -17,32 +17,33 @@ constexpr int TK = 16;
 constexpr int NT = 256;
 
 // Grouped GEMM: one CTA per output tile, looping over the tile's K-list.
-// 16x16 threads, each owns rows ty+16i, cols tx+16j (i, j < 4).
-// T: storage type of A, B, C; U: arithmetic type.
-template <class T, class Task, class Op, class U = T>
+// 16x16 threads; thread (tx, ty) owns rows ty + 16 i (i < TM/16) and
+// cols tx + 16 j (j < TN/16).  T: storage type, U: arithmetic type.
+template <int TM, int TN, class T, class Task, class Op, class U = T>
 __global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks,
                                              const Op* __restrict__ ops,
                                              const int* __restrict__ skip) {
     if (skip && *skip) return;
+    constexpr int RI = TM / 16, RJ = TN / 16;
     const Task t = tasks[blockIdx.x];
-    __shared__ U As[TK][GEMM_TM + 1];
-    __shared__ U Bs[TK][GEMM_TN + 1];
+    __shared__ U As[TK][TM + 1];
+    __shared__ U Bs[TK][TN + 1];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    U acc[4][4];
+    U acc[RI][RJ];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = U(0);
-    const int mrem = min(GEMM_TM, t.m - t.r0);
-    const int nrem = min(GEMM_TN, t.n - t.c0);
+        for (int j = 0; j < RJ; ++j) acc[i][j] = U(0);
+    const int mrem = min(TM, t.m - t.r0);
+    const int nrem = min(TN, t.n - t.c0);
     for (int o = t.op0; o < t.op1; ++o) {
         const Op op = ops[o];
         const bool ta = op.trans & 1, tb = op.trans & 2;
         for (int k0 = 0; k0 < op.k; k0 += TK) {
             const int krem = min(TK, op.k - k0);
-            for (int e = threadIdx.x; e < GEMM_TM * TK; e += NT) {
+            for (int e = threadIdx.x; e < TM * TK; e += NT) {
                 int i, kk;
-                if (ta) { i = e % GEMM_TM; kk = e / GEMM_TM; }
+                if (ta) { i = e % TM; kk = e / TM; }
                 else { kk = e % TK; i = e / TK; }
                 T v = T(0);
                 if (i < mrem && kk < krem) {
@@ -52,10 +53,10 @@ __global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks,
                 }
                 As[kk][i] = (U)v;
             }
-            for (int e = threadIdx.x; e < GEMM_TN * TK; e += NT) {
+            for (int e = threadIdx.x; e < TN * TK; e += NT) {
                 int j, kk;
                 if (tb) { kk = e % TK; j = e / TK; }
-                else { j = e % GEMM_TN; kk = e / GEMM_TN; }
+                else { j = e % TN; kk = e / TN; }
                 T v = T(0);
                 if (j < nrem && kk < krem) {
                     const int col = t.c0 + j, kg = k0 + kk;
@@ -66,30 +67,51 @@ __global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks,
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < TK; ++kk) {
-                U a[4], b[4];
+                U a[RI], b[RJ];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+                for (int i = 0; i < RI; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+                for (int j = 0; j < RJ; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < RI; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                    for (int j = 0; j < RJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
             }
             __syncthreads();
         }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RI; ++i) {
         const int r = ty + 16 * i;
         if (r >= mrem) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < RJ; ++j) {
             const int c = tx + 16 * j;
             if (c >= nrem) continue;
-            T* dst = t.C + (size_t)(t.r0 + r) * t.ldc + (t.c0 + c);
+            const int gr = t.r0 + r, gc = t.c0 + c;
+            T* dst;
+            if (t.cmap == nullptr) dst = t.C + (size_t)gr * t.ldc + gc;
+            else if (t.cmap_rows) dst = t.C + t.cmap[2 * gr] + (size_t)gc * t.cmap[2 * gr + 1];
+            else dst = t.C + t.cmap[2 * gc] + (size_t)gr * t.cmap[2 * gc + 1];
             *dst = t.accumulate ? *dst + (T)acc[i][j] : (T)acc[i][j];
         }
+    }
+}
+
+// dst = sum coef * src over the task's source list (memory-bound).
+__global__ void k_mix(const MixTask* __restrict__ tasks, const MixSrc* __restrict__ srcs,
+                      const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const MixTask t = tasks[blockIdx.x];
+    const int n = t.rows * t.cols;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int i = e / t.cols, j = e % t.cols;
+        double s = 0.0;
+        for (int q = t.s0; q < t.s1; ++q) {
+            const MixSrc m = srcs[q];
+            s += m.coef * m.src[(size_t)i * m.lds + j];
+        }
+        t.dst[(size_t)i * t.ldd + j] = s;
     }
 }
 
@@ -392,15 +414,23 @@ void count_launch() { counted(); }
 
 void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                            const int* skip) {
-    if (ntask > 0) { counted(); k_gemm<double, GemmTask, GemmOp, float><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
+    if (ntask > 0) { counted(); k_gemm<64, 64, double, GemmTask, GemmOp, float><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
+}
+void launch_gemm_f64_skinny(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
+                            const int* skip) {
+    if (ntask > 0) { counted(); k_gemm<16, 128, double, GemmTask, GemmOp><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
+}
+void launch_gemm_f64in_f32_skinny(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
+                                  const int* skip) {
+    if (ntask > 0) { counted(); k_gemm<16, 128, double, GemmTask, GemmOp, float><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
+}
+void launch_mix(const MixTask* tasks, int ntask, const MixSrc* srcs, cudaStream_t st, const int* skip) {
+    if (ntask > 0) { counted(); k_mix<<<ntask, 128, 0, st>>>(tasks, srcs, skip); }
 }
 
 void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                      const int* skip) {
-    if (ntask > 0) { counted(); k_gemm<double, GemmTask, GemmOp><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
-}
-void launch_gemm_f32(const GemmTaskF* tasks, int ntask, const GemmOpF* ops, cudaStream_t st) {
-    if (ntask > 0) { counted(); k_gemm<float, GemmTaskF, GemmOpF><<<ntask, NT, 0, st>>>(tasks, ops, nullptr); }
+    if (ntask > 0) { counted(); k_gemm<64, 64, double, GemmTask, GemmOp><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
 }
 void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaStream_t st) {
     if (ntask > 0) { counted(); k_diag<<<ntask, 256, 0, st>>>(tasks, terms); }

@@ -16,34 +16,36 @@ struct GemmOp {
 };
 
 // One output tile (rows [r0, r0+TM) x cols [c0, c0+TN) of an m x n block C).
+// With cmap set, element (i, j) of the block is stored at
+//   C + cmap[2j] + i * cmap[2j+1]          (cmap_rows == 0, per-column map)
+//   C + cmap[2i] + j * cmap[2i+1]          (cmap_rows == 1, per-row map)
+// which scatters a panel GEMM straight into a block-sparse layout.
 struct GemmTask {
     double* C;
+    const int* cmap;
     int ldc, m, n;
     int r0, c0;
     int op0, op1;      // range of GemmOp
     int accumulate;    // 1: C += sum, 0: C = sum
-    int pad;
-};
-
-// Float32 variant (same layout, float pointers).
-struct GemmOpF {
-    const float* A;
-    const float* B;
-    int lda, ldb, k, trans;
-    float alpha;
-    int pad;
-};
-struct GemmTaskF {
-    float* C;
-    int ldc, m, n;
-    int r0, c0;
-    int op0, op1;
-    int accumulate;
-    int pad;
+    int cmap_rows;
 };
 
 constexpr int GEMM_TM = 64;
 constexpr int GEMM_TN = 64;
+
+// dst block (rows x cols, leading dim ldd) = sum_k coef_k * src_k (leading dim lds_k)
+struct MixSrc {
+    const double* src;
+    int lds;
+    int pad;
+    double coef;
+};
+struct MixTask {
+    double* dst;
+    int rows, cols, ldd;
+    int s0, s1;
+    int pad;
+};
 
 // Jacobi diagonal of A_loc: out[l, r] += sum coef * L[l*(ldL+1)] * R[r*(ldR+1)]
 struct DiagTerm {
@@ -102,7 +104,13 @@ void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, 
 
 void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                      const int* skip = nullptr);
-void launch_gemm_f32(const GemmTaskF* tasks, int ntask, const GemmOpF* ops, cudaStream_t st);
+// Skinny-tile (16 x 128) float64 variant for panels with few rows.
+void launch_gemm_f64_skinny(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
+                            const int* skip = nullptr);
+void launch_gemm_f64in_f32_skinny(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
+                                  const int* skip = nullptr);
+void launch_mix(const MixTask* tasks, int ntask, const MixSrc* srcs, cudaStream_t st,
+                const int* skip = nullptr);
 void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaStream_t st);
 void launch_eig(const EigTask* tasks, int ntask, cudaStream_t st);
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);

@@ -221,7 +221,11 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
             for (int q = 0; q < 16; ++q) {
                 const int col = c0 + q;
                 if (col < nrem) {
-                    double* dst = t.C + (size_t)(t.r0 + row) * t.ldc + (t.c0 + col);
+                    const int gr = t.r0 + row, gc = t.c0 + col;
+                    double* dst;
+                    if (t.cmap == nullptr) dst = t.C + (size_t)gr * t.ldc + gc;
+                    else if (t.cmap_rows) dst = t.C + t.cmap[2 * gr] + (size_t)gc * t.cmap[2 * gr + 1];
+                    else dst = t.C + t.cmap[2 * gc] + (size_t)gr * t.cmap[2 * gc + 1];
                     const double val = (double)__uint_as_float(v[q]);
                     *dst = t.accumulate ? *dst + val : val;
                 }

@@ -7,21 +7,40 @@
 
 namespace mpspt {
 
-void GemmPlan::block(double* C, int ldc, int m, int n, int accumulate, int op0) {
+void GemmPlan::block(double* C, int ldc, int m, int n, int accumulate, int op0, long long cmap_off,
+                     int cmap_rows) {
     if (m <= 0 || n <= 0) return;
     const int op1 = (int)ops.size();
     for (int o = op0; o < op1; ++o) flops += 2.0 * m * n * ops[o].k;
     for (int r0 = 0; r0 < m; r0 += tm)
-        for (int c0 = 0; c0 < n; c0 += tn)
-            tasks.push_back({C, ldc, m, n, r0, c0, op0, op1, accumulate, 0});
+        for (int c0 = 0; c0 < n; c0 += tn) {
+            tasks.push_back({C, nullptr, ldc, m, n, r0, c0, op0, op1, accumulate, cmap_rows});
+            task_cmap.push_back(cmap_off);
+        }
 }
 
 void GemmPlan::upload(cudaStream_t st) {
+    if (!cmaps.empty()) mpspt::upload(dcmaps, cmaps, st);
+    const int* cbase = dcmaps.as<int>();
+    for (size_t i = 0; i < tasks.size(); ++i)
+        tasks[i].cmap = task_cmap[i] >= 0 ? cbase + task_cmap[i] : nullptr;
     if (checks_enabled()) {
-        for (const auto& t : tasks) {
-            check_range(t.C, ((size_t)(t.m - 1) * t.ldc + t.n) * sizeof(double), "gemm C");
-            for (int o = t.op0; o < t.op1; ++o) {
-                const GemmOp& op = ops[o];
+        for (size_t i = 0; i < tasks.size(); ++i) {
+            const auto& t = tasks[i];
+            if (t.cmap == nullptr) {
+                check_range(t.C, ((size_t)(t.m - 1) * t.ldc + t.n) * sizeof(double), "gemm C");
+                if (t.ldc < t.n) throw Error(MPSPT_ERR_INVALID, "gemm ldc");
+            } else {
+                const long long o = task_cmap[i];
+                const int nmap = t.cmap_rows ? t.m : t.n, other = t.cmap_rows ? t.n : t.m;
+                require((size_t)(o + 2 * (long long)nmap) <= cmaps.size(), "gemm cmap range");
+                for (int q = 0; q < nmap; ++q) {
+                    const int base = cmaps[o + 2 * q], ld = cmaps[o + 2 * q + 1];
+                    check_range(t.C + base, ((size_t)(other - 1) * ld + 1) * sizeof(double), "gemm cmap dst");
+                }
+            }
+            for (int q = t.op0; q < t.op1; ++q) {
+                const GemmOp& op = ops[q];
                 const size_t ea = (op.trans & 1) ? (size_t)(op.k - 1) * op.lda + t.m : (size_t)(t.m - 1) * op.lda + op.k;
                 const size_t eb = (op.trans & 2) ? (size_t)(t.n - 1) * op.ldb + op.k : (size_t)(op.k - 1) * op.ldb + t.n;
                 check_range(op.A, ea * sizeof(double), "gemm A");
@@ -29,7 +48,6 @@ void GemmPlan::upload(cudaStream_t st) {
                 if ((op.trans & 1) ? op.lda < t.m : op.lda < op.k) throw Error(MPSPT_ERR_INVALID, "gemm lda");
                 if ((op.trans & 2) ? op.ldb < op.k : op.ldb < t.n) throw Error(MPSPT_ERR_INVALID, "gemm ldb");
             }
-            if (t.ldc < t.n) throw Error(MPSPT_ERR_INVALID, "gemm ldc");
         }
     }
     mpspt::upload(dtasks, tasks, st);
@@ -37,15 +55,19 @@ void GemmPlan::upload(cudaStream_t st) {
 }
 
 void GemmPlan::run(cudaStream_t st) const {
-    if (kind == GEMM_TC) launch_gemm_tc(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), err, st, skip);
-    else if (kind == GEMM_F32) launch_gemm_f64in_f32(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), st, skip);
-    else launch_gemm_f64(dtasks.as<GemmTask>(), (int)tasks.size(), dops.as<GemmOp>(), st, skip);
+    const int nt = (int)tasks.size();
+    if (nt == 0) return;
+    const GemmTask* t = dtasks.as<GemmTask>();
+    const GemmOp* o = dops.as<GemmOp>();
+    if (kind == GEMM_TC) launch_gemm_tc(t, nt, o, err, st, skip);
+    else if (kind == GEMM_F32) (skinny ? launch_gemm_f64in_f32_skinny : launch_gemm_f64in_f32)(t, nt, o, st, skip);
+    else (skinny ? launch_gemm_f64_skinny : launch_gemm_f64)(t, nt, o, st, skip);
 }
 
 void Omega::build(const MPO& W, int i) {
     std::map<int, std::vector<const MpoEntry*>> by_b;
     for (const auto& e : W.W[i + 1]) by_b[e.a].push_back(&e);
-    std::map<std::tuple<int, int, int, int>, double> acc;
+    std::map<std::tuple<int, int, int, int>, double> acc;   // (a, out, c, in)
     for (const auto& e1 : W.W[i]) {
         auto it = by_b.find(e1.b);
         if (it == by_b.end()) continue;
@@ -61,23 +83,23 @@ void Omega::build(const MPO& W, int i) {
                         for (int t2 = 0; t2 < 4; ++t2) {
                             const double v2 = o2[s2 * 4 + t2];
                             if (v2 == 0.0) continue;
-                            acc[{s1 * 4 + s2, e1.a, e2->b, t1 * 4 + t2}] += cc * v1 * v2;
+                            acc[{e1.a, s1 * 4 + s2, e2->b, t1 * 4 + t2}] += cc * v1 * v2;
                         }
                 }
         }
     }
+    Da = W.dim[i];
     e.clear();
-    first.assign(17, 0);
     for (auto& kv : acc) {
         if (kv.second == 0.0) continue;
-        e.push_back({std::get<1>(kv.first), std::get<2>(kv.first), std::get<0>(kv.first),
+        e.push_back({std::get<0>(kv.first), std::get<2>(kv.first), std::get<1>(kv.first),
                      std::get<3>(kv.first), kv.second});
     }
-    // entries are sorted by out already (map order); build the index
-    int k = 0;
-    for (int o = 0; o <= 16; ++o) {
-        while (k < (int)e.size() && e[k].out < o) ++k;
-        first[o] = k;
+    first.assign((size_t)Da * 16 + 1, 0);
+    size_t k = 0;
+    for (int key = 0; key <= Da * 16; ++key) {
+        while (k < e.size() && e[k].a * 16 + e[k].out < key) ++k;
+        first[key] = (int)k;
     }
 }
 
@@ -85,70 +107,188 @@ void TwoSitePlan::build(const Omega& om, const TwoT& bra, const TwoT& ket, const
                         const Bond& ketL, const Bond& braR, const Bond& ketR, const EnvT& L,
                         const EnvT& R, const std::vector<QN>& dqR, const double* x, double* out,
                         cudaStream_t st) {
-    (void)dqR;
-    g1.clear();
-    g2.clear();
+    (void)dqR; (void)ketL;
+    g1.clear(); g2.clear(); g2s.clear();
+    mtasks.clear(); msrc.clear();
     const int np = (int)ket.panels.size();
     const int nc = (int)(R.idx.size() / (size_t)std::max(1, R.nsk));
-    // T panels: one per (c, ket panel) with an R_c block on the panel's sector
-    std::vector<long long> toff((size_t)nc * np, -1);
-    std::vector<int> tcols((size_t)nc * np, 0);
-    std::vector<int> panel_of(ket.blk.size());
-    for (int p = 0; p < np; ++p)
-        for (int b = ket.panels[p].b0; b < ket.panels[p].b1; ++b) panel_of[b] = p;
-    tsize = 0;
-    for (int c = 0; c < nc; ++c)
-        for (int p = 0; p < np; ++p) {
-            int rb = R.find(c, ket.panels[p].sr);
+    const int na = om.Da;
+    // ---- Rpack per ket right sector: blocks R_c(sb_c, sk) stacked by c
+    std::vector<long long> rp_off(ketR.nsec(), -1);
+    std::vector<int> rp_rows(ketR.nsec(), 0);
+    std::vector<int> rcol((size_t)nc * ketR.nsec(), -1);   // row offset of c inside Rpack(sk)
+    size_t rps = 0;
+    std::vector<CopyTask> pk_tasks;
+    for (const auto& P : ket.panels) {
+        const int sk = P.sr;
+        int rows = 0;
+        for (int c = 0; c < nc; ++c) {
+            int rb = R.find(c, sk);
             if (rb < 0) continue;
-            int cols = braR.sec[R.blk[rb].sb].dim;
-            toff[(size_t)c * np + p] = (long long)tsize;
-            tcols[(size_t)c * np + p] = cols;
-            tsize += (size_t)ket.panels[p].rows * cols;
+            rcol[(size_t)c * ketR.nsec() + sk] = rows;
+            rows += braR.sec[R.blk[rb].sb].dim;
         }
+        rp_rows[sk] = rows;
+        rp_off[sk] = (long long)rps;
+        rps += (size_t)rows * ketR.sec[sk].dim;
+    }
+    // ---- Lpack per bra left sector: blocks L_a(sl, sk_a) side by side
+    std::vector<int> lp_cols(braL.nsec(), 0);
+    std::vector<long long> lp_off(braL.nsec(), -1);
+    std::vector<int> lcol((size_t)na * braL.nsec(), -1);
+    std::vector<int> l_blk((size_t)na * braL.nsec(), -1);
+    for (int b = 0; b < (int)L.blk.size(); ++b) l_blk[(size_t)L.blk[b].a * braL.nsec() + L.blk[b].sb] = b;
+    size_t lps = 0;
+    for (int sl = 0; sl < braL.nsec(); ++sl) {
+        int cols = 0;
+        for (int a = 0; a < na; ++a) {
+            int lb = l_blk[(size_t)a * braL.nsec() + sl];
+            if (lb < 0) continue;
+            lcol[(size_t)a * braL.nsec() + sl] = cols;
+            cols += ketL.sec[L.blk[lb].sk].dim;
+        }
+        lp_cols[sl] = cols;
+        lp_off[sl] = (long long)lps;
+        lps += (size_t)braL.sec[sl].dim * cols;
+    }
+    Rp.ensure((rps + 1) * sizeof(double), st);
+    Lp.ensure((lps + 1) * sizeof(double), st);
+    double* Rpp = Rp.as<double>();
+    double* Lpp = Lp.as<double>();
+    for (const auto& P : ket.panels) {
+        const int sk = P.sr, dk = ketR.sec[sk].dim;
+        for (int c = 0; c < nc; ++c) {
+            int rb = R.find(c, sk);
+            if (rb < 0) continue;
+            const int db = braR.sec[R.blk[rb].sb].dim;
+            pk_tasks.push_back({R.ptr(R.blk[rb]), Rpp + rp_off[sk] + (size_t)rcol[(size_t)c * ketR.nsec() + sk] * dk,
+                                nullptr, db, dk, dk, dk, 0, 0});
+        }
+    }
+    for (int sl = 0; sl < braL.nsec(); ++sl)
+        for (int a = 0; a < na; ++a) {
+            int lb = l_blk[(size_t)a * braL.nsec() + sl];
+            if (lb < 0) continue;
+            const int dl = braL.sec[sl].dim, dk = ketL.sec[L.blk[lb].sk].dim;
+            pk_tasks.push_back({L.ptr(L.blk[lb]), Lpp + lp_off[sl] + lcol[(size_t)a * braL.nsec() + sl],
+                                nullptr, dl, dk, dk, lp_cols[sl], 0, 0});
+        }
+    if (checks_enabled())
+        for (const auto& t : pk_tasks) {
+            check_range(t.src, ((size_t)(t.rows - 1) * t.lds + t.cols_n) * sizeof(double), "pack src");
+            check_range(t.dst, ((size_t)(t.rows - 1) * t.ldd + t.cols_n) * sizeof(double), "pack dst");
+        }
+    mpspt::upload(pk, pk_tasks, st);
+    launch_copy(pk.as<CopyTask>(), (int)pk_tasks.size(), st);
+    // ---- T panels
+    std::vector<long long> toff(np, -1);
+    std::vector<int> panel_of(ket.blk.size());
+    tsize = 0;
+    for (int p = 0; p < np; ++p) {
+        const auto& P = ket.panels[p];
+        for (int b = P.b0; b < P.b1; ++b) panel_of[b] = p;
+        if (rp_rows[P.sr] == 0) continue;
+        toff[p] = (long long)tsize;
+        tsize += (size_t)P.rows * rp_rows[P.sr];
+    }
     T.ensure((tsize + 1) * sizeof(double), st);
     double* Tp = T.as<double>();
-    for (int c = 0; c < nc; ++c)
-        for (int p = 0; p < np; ++p) {
-            long long o = toff[(size_t)c * np + p];
-            if (o < 0) continue;
-            const auto& P = ket.panels[p];
-            int rb = R.find(c, P.sr);
-            int k = ketR.sec[P.sr].dim;
-            int m0 = g1.mark();
-            g1.op(x + P.off, k, R.ptr(R.blk[rb]), k, k, 2, 1.0);
-            g1.block(Tp + o, tcols[(size_t)c * np + p], P.rows, tcols[(size_t)c * np + p], 0, m0);
-        }
-    // L_a block landing on each bra sector (q_bra = q_ket + dq_a: at most one)
-    const int nsb = braL.nsec();
-    const int na = (int)(L.idx.size() / (size_t)std::max(1, L.nsk));
-    std::vector<int> l_by_sb((size_t)na * nsb, -1);
-    for (int b = 0; b < (int)L.blk.size(); ++b) l_by_sb[(size_t)L.blk[b].a * nsb + L.blk[b].sb] = b;
-    // output blocks: out = sum L_a [Omega_ac] T_c
-    for (const auto& bb : bra.blk) {
-        const int o16 = bb.s1 * 4 + bb.s2;
-        int m0 = g2.mark();
-        for (int q = om.first[o16]; q < om.first[o16 + 1]; ++q) {
-            const Omega::E& E = om.e[q];
-            const int t1 = E.in / 4, t2 = E.in % 4;
-            const int lb = l_by_sb[(size_t)E.a * nsb + bb.sl];
-            if (lb < 0) continue;
-            const int sk = L.blk[lb].sk;
-            const int kb = ket.find(sk, t1, t2);
-            if (kb < 0) continue;
-            const int p = panel_of[kb];
-            const long long o = toff[(size_t)E.c * np + p];
-            if (o < 0) continue;
-            const int cols = tcols[(size_t)E.c * np + p];
-            if (cols != bb.cols) continue;
-            const auto& K = ket.blk[kb];
-            const size_t row_in_panel = (K.off - ket.panels[p].off) / (size_t)K.cols;
-            g2.op(L.ptr(L.blk[lb]), K.rows, Tp + o + row_in_panel * cols, cols, K.rows, 0, E.v);
-        }
-        g2.block(out + bb.off, bb.cols, bb.rows, bb.cols, 0, m0);
+    for (int p = 0; p < np; ++p) {
+        if (toff[p] < 0) continue;
+        const auto& P = ket.panels[p];
+        const int dk = ketR.sec[P.sr].dim, nr = rp_rows[P.sr];
+        int m0 = g1.mark();
+        g1.op(x + P.off, dk, Rpp + rp_off[P.sr], dk, dk, 2, 1.0);
+        g1.block(Tp + toff[p], nr, P.rows, nr, 0, m0);
     }
+    // ---- bra left panels, V stacks and mix tasks
+    std::vector<std::vector<int>> left_blocks(braL.nsec());
+    for (int b = 0; b < (int)bra.blk.size(); ++b) left_blocks[bra.blk[b].sl].push_back(b);
+    std::vector<long long> voff(braL.nsec(), -1);
+    std::vector<int> wd(braL.nsec(), 0);
+    size_t vs = 0;
+    for (int sl = 0; sl < braL.nsec(); ++sl) {
+        int w = 0;
+        for (int b : left_blocks[sl]) w += bra.blk[b].cols;
+        wd[sl] = w;
+        if (w == 0 || lp_cols[sl] == 0) continue;
+        voff[sl] = (long long)vs;
+        vs += (size_t)lp_cols[sl] * w;
+    }
+    V.ensure((vs + 1) * sizeof(double), st);
+    double* Vp = V.as<double>();
+    for (int sl = 0; sl < braL.nsec(); ++sl) {
+        if (voff[sl] < 0) continue;
+        const int W = wd[sl];
+        // column map of the bra left panel -> two-site layout
+        std::vector<int> cm;
+        int wcol = 0;
+        for (int bi : left_blocks[sl]) {
+            const auto& B = bra.blk[bi];
+            for (int r = 0; r < B.cols; ++r) { cm.push_back((int)(B.off + r)); cm.push_back(B.cols); }
+            for (int a = 0; a < na; ++a) {
+                const int lc = lcol[(size_t)a * braL.nsec() + sl];
+                if (lc < 0) continue;
+                const int lb = l_blk[(size_t)a * braL.nsec() + sl];
+                const int sk = L.blk[lb].sk, dk = ketL.sec[sk].dim;
+                MixTask mt{Vp + voff[sl] + (size_t)lc * W + wcol, dk, B.cols, W, (int)msrc.size(), 0, 0};
+                const int o16 = B.s1 * 4 + B.s2;
+                for (int q = om.begin(a, o16); q < om.end(a, o16); ++q) {
+                    const Omega::E& E = om.e[q];
+                    const int kb = ket.find(sk, E.in / 4, E.in % 4);
+                    if (kb < 0) continue;
+                    const int p = panel_of[kb];
+                    if (toff[p] < 0) continue;
+                    const int srk = ket.panels[p].sr;
+                    const int rc = rcol[(size_t)E.c * ketR.nsec() + srk];
+                    if (rc < 0) continue;
+                    const int rb = R.find(E.c, srk);
+                    if (R.blk[rb].sb != B.sr) continue;
+                    const auto& K = ket.blk[kb];
+                    const size_t rip = (K.off - ket.panels[p].off) / (size_t)K.cols;
+                    const int nr = rp_rows[srk];
+                    msrc.push_back({Tp + toff[p] + rip * nr + rc, nr, 0, E.v});
+                }
+                mt.s1 = (int)msrc.size();
+                mtasks.push_back(mt);
+            }
+            wcol += B.cols;
+        }
+        // g2: out(sl, :) = Lpack(sl) V_stack(sl); TC computes the transpose (rows = panel cols)
+        const int dl = braL.sec[sl].dim, K = lp_cols[sl];
+        if (kind == GEMM_TC) {
+            const long long co = g2.add_cmap(cm);
+            int m0 = g2.mark();
+            g2.op(Vp + voff[sl], W, Lpp + lp_off[sl], K, K, 1 | 2, 1.0);
+            g2.block(out, 0, W, dl, 0, m0, co, 1);
+        } else {
+            GemmPlan& g = (dl <= 16) ? g2s : g2;
+            const long long co = g.add_cmap(cm);
+            int m0 = g.mark();
+            g.op(Lpp + lp_off[sl], K, Vp + voff[sl], W, K, 0, 1.0);
+            g.block(out, 0, dl, W, 0, m0, co, 0);
+        }
+    }
+    // bra blocks whose left panel has no operator: zero them through the mix path
+    for (int sl = 0; sl < braL.nsec(); ++sl) {
+        if (voff[sl] >= 0) continue;
+        for (int bi : left_blocks[sl]) {
+            const auto& B = bra.blk[bi];
+            mtasks.push_back({out + B.off, B.rows, B.cols, B.cols, (int)msrc.size(), (int)msrc.size(), 0});
+        }
+    }
+    if (checks_enabled()) {
+        for (const auto& t : mtasks) {
+            check_range(t.dst, ((size_t)(t.rows - 1) * t.ldd + t.cols) * sizeof(double), "mix dst");
+            for (int q = t.s0; q < t.s1; ++q)
+                check_range(msrc[q].src, ((size_t)(t.rows - 1) * msrc[q].lds + t.cols) * sizeof(double), "mix src");
+        }
+    }
+    mpspt::upload(dmt, mtasks, st);
+    mpspt::upload(dms, msrc, st);
     g1.upload(st);
     g2.upload(st);
+    g2s.upload(st);
 }
 
 void DiagPlan::build(const Omega& om, const TwoT& x, const Bond& Lb, const Bond& Rb,
@@ -160,13 +300,17 @@ void DiagPlan::build(const Omega& om, const TwoT& x, const Bond& Lb, const Bond&
     for (const auto& b : x.blk) {
         const int o16 = b.s1 * 4 + b.s2;
         int t0 = (int)terms.size();
-        for (int q = om.first[o16]; q < om.first[o16 + 1]; ++q) {
-            const Omega::E& E = om.e[q];
-            if (E.in != o16) continue;
-            if (!(dqL[E.a] == QN(0, 0)) || !(dqR[E.c] == QN(0, 0))) continue;
-            int lb = Le.find(E.a, b.sl), rb = Re.find(E.c, b.sr);
-            if (lb < 0 || rb < 0) continue;
-            terms.push_back({Le.ptr(Le.blk[lb]), Re.ptr(Re.blk[rb]), b.rows, b.cols, E.v});
+        for (int a = 0; a < om.Da; ++a) {
+            if (!(dqL[a] == QN(0, 0))) continue;
+            const int lb = Le.find(a, b.sl);
+            if (lb < 0) continue;
+            for (int q = om.begin(a, o16); q < om.end(a, o16); ++q) {
+                const Omega::E& E = om.e[q];
+                if (E.in != o16 || !(dqR[E.c] == QN(0, 0))) continue;
+                const int rb = Re.find(E.c, b.sr);
+                if (rb < 0) continue;
+                terms.push_back({Le.ptr(Le.blk[lb]), Re.ptr(Re.blk[rb]), b.rows, b.cols, E.v});
+            }
         }
         tasks.push_back({out + b.off, b.rows, b.cols, t0, (int)terms.size()});
     }

@@ -10,27 +10,40 @@ namespace mpspt {
 enum GemmKind { GEMM_F64 = 0, GEMM_F32 = 1, GEMM_TC = 2 };
 
 struct GemmPlan {
-    int tm = GEMM_TM, tn = GEMM_TN;   // output tile (TC kernel: 128 x 64)
+    int tm = GEMM_TM, tn = GEMM_TN;   // output tile (TC kernel: 128 x 64; skinny: 16 x 128)
     int kind = GEMM_F64;
+    bool skinny = false;
     int* err = nullptr;               // TC kernel error flag (device)
     const int* skip = nullptr;        // device flag: launch becomes a no-op when set
-    void set_kind(int k, int* e) {
+    void set_kind(int k, int* e, bool skinny_ = false) {
         kind = k;
         err = e;
-        if (k == GEMM_TC) { tm = tc_tile_m(); tn = tc_tile_n(); } else { tm = GEMM_TM; tn = GEMM_TN; }
+        skinny = skinny_ && k != GEMM_TC;
+        if (k == GEMM_TC) { tm = tc_tile_m(); tn = tc_tile_n(); }
+        else if (skinny) { tm = 16; tn = 128; }
+        else { tm = GEMM_TM; tn = GEMM_TN; }
     }
     std::vector<GemmTask> tasks;
     std::vector<GemmOp> ops;
+    std::vector<int> cmaps;           // host copy of all column / row maps
+    std::vector<long long> task_cmap; // per task: offset into cmaps or -1
     double flops = 0.0;   // algorithmic: sum over ops of 2 m n k (each product once)
-    DBuf dtasks, dops;
-    void clear() { tasks.clear(); ops.clear(); flops = 0.0; }
+    DBuf dtasks, dops, dcmaps;
+    void clear() { tasks.clear(); ops.clear(); cmaps.clear(); task_cmap.clear(); flops = 0.0; }
     int mark() const { return (int)ops.size(); }
     void op(const double* A, int lda, const double* B, int ldb, int k, int trans, double alpha) {
         if (k <= 0) return;
         ops.push_back({A, B, lda, ldb, k, trans, alpha});
     }
-    // close the output block C (m x n) whose K-list is ops[op0, end)
-    void block(double* C, int ldc, int m, int n, int accumulate, int op0);
+    long long add_cmap(const std::vector<int>& m) {
+        long long o = (long long)cmaps.size();
+        cmaps.insert(cmaps.end(), m.begin(), m.end());
+        return o;
+    }
+    // close the output block C (m x n) whose K-list is ops[op0, end); with
+    // cmap_off >= 0 the element addresses come from the map (see GemmTask)
+    void block(double* C, int ldc, int m, int n, int accumulate, int op0, long long cmap_off = -1,
+               int cmap_rows = 0);
     void upload(cudaStream_t st);
     void run(cudaStream_t st) const;
 };
@@ -38,25 +51,49 @@ struct GemmPlan {
 // Two-site operator sum_{a,c} L_a (Omega_ac) R_c with Omega_ac = sum_b W1_ab (x) W2_bc.
 struct Omega {
     struct E { int a, c, out, in; double v; };   // out/in = s1*4 + s2
-    std::vector<E> e;                              // sorted by (out, a, c, in)
-    std::vector<int> first;                        // first entry per out (17 entries)
+    std::vector<E> e;                              // sorted by (a, out, c, in)
+    std::vector<int> first;                        // first entry per (a*16 + out), size Da*16+1
+    int Da = 0;
     void build(const MPO& W, int i);
+    int begin(int a, int out) const { return first[(size_t)a * 16 + out]; }
+    int end(int a, int out) const { return first[(size_t)a * 16 + out + 1]; }
 };
 
 // sigma-type application: out(bra layout) = sum L_a Omega_ac R_c x(ket layout).
-// T holds x R_c^T for every c (scratch sized by the plan).
+// Per bond step the environments are packed per sector (Rpack: all R_c
+// blocks on one ket right sector stacked; Lpack: all L_a blocks on one bra
+// left sector side by side).  Then per application:
+//   g1:  T_p = x_panel(p) Rpack^T           one GEMM per ket right sector
+//   mix: V_stack(sl) = sum Omega coef T      memory-bound block sums
+//   g2:  out(sl, :) = Lpack(sl) V_stack(sl)  one long-K GEMM per bra left
+//        sector, scattered into the two-site layout by a column map
 struct TwoSitePlan {
-    GemmPlan g1, g2;
-    DBuf T;
+    GemmPlan g1, g2, g2s;            // g2: wide rows, g2s: few rows (skinny tiles)
+    std::vector<MixTask> mtasks;
+    std::vector<MixSrc> msrc;
+    DBuf dmt, dms;
+    DBuf T, V, Lp, Rp, pk;
     size_t tsize = 0;
-    void set_kind(int k, int* e) { g1.set_kind(k, e); g2.set_kind(k, e); }
-    void set_skip(const int* s) { g1.skip = s; g2.skip = s; }
+    int kind = GEMM_F64;
+    const int* skip = nullptr;
+    void set_kind(int k, int* e) {
+        kind = k;
+        g1.set_kind(k, e);
+        g2.set_kind(k, e);
+        g2s.set_kind(k, e, true);
+    }
+    void set_skip(const int* s) { skip = s; g1.skip = s; g2.skip = s; g2s.skip = s; }
     void build(const Omega& om, const TwoT& bra, const TwoT& ket, const Bond& braL,
                const Bond& ketL, const Bond& braR, const Bond& ketR, const EnvT& L,
                const EnvT& R, const std::vector<QN>& dqR, const double* x, double* out,
                cudaStream_t st);
-    void run(cudaStream_t st) const { g1.run(st); g2.run(st); }
-    double flops() const { return g1.flops + g2.flops; }
+    void run(cudaStream_t st) const {
+        g1.run(st);
+        launch_mix(dmt.as<MixTask>(), (int)mtasks.size(), dms.as<MixSrc>(), st, skip);
+        g2.run(st);
+        g2s.run(st);
+    }
+    double flops() const { return g1.flops + g2.flops + g2s.flops; }
 };
 
 // Jacobi diagonal of sum L_a Omega_ac R_c on the bra layout.
