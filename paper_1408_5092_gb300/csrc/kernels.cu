@@ -141,25 +141,42 @@ __global__ void k_copy(const CopyTask* __restrict__ tasks) {
     }
 }
 
-// Cyclic two-sided Jacobi with the round-robin parallel ordering: in each of
-// the m-1 rounds of a sweep, m/2 disjoint (p, q) rotations are applied at
-// once (rows, then columns).  Works in global memory (L2-resident blocks).
+// Cyclic two-sided Jacobi with the round-robin parallel ordering.  In each
+// of the m-1 rounds of a sweep the m/2 disjoint pairs (p_k, q_k) get their
+// rotation R_k; the whole matrix is then updated in one pass, block by
+// block: the 2x2 block of pairs (k, l) becomes R_k^T A_kl R_l (blocks are
+// independent, so the update is in place), and V's columns of pair l are
+// rotated by R_l.  Matrices live in shared memory when they fit, else in
+// global memory (L2-resident).  A pair is skipped when its off-diagonal
+// element is negligible against its diagonal (threshold Jacobi).
 constexpr int EIG_MAXN = 2048;
+constexpr int EIG_SMEM_N = 112;   // 2 * 112^2 doubles = 200 KB
+
+__device__ __forceinline__ void rr_pair(int k, int r, int m, int& pa, int& pb) {
+    pa = (k == 0) ? 0 : ((k - 1 + r) % (m - 1)) + 1;
+    pb = ((m - 1 - k - 1 + r) % (m - 1)) + 1;
+}
+
 __global__ void __launch_bounds__(512) k_eig(const EigTask* __restrict__ tasks) {
+    extern __shared__ double esm[];
     const EigTask t = tasks[blockIdx.x];
     const int n = t.n;
-    double* A = t.A;
-    double* V = t.V;
+    const bool in_smem = n <= EIG_SMEM_N;
+    double* A = in_smem ? esm : t.A;
+    double* V = in_smem ? esm + n * n : t.V;
     __shared__ int Pp[EIG_MAXN / 2], Qq[EIG_MAXN / 2];
     __shared__ double Cc[EIG_MAXN / 2], Ss[EIG_MAXN / 2];
     __shared__ double red[2][32];
     __shared__ int stop;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e / n == e % n) ? 1.0 : 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        if (in_smem) A[e] = t.A[e];
+        V[e] = (e / n == e % n) ? 1.0 : 0.0;
+    }
+    __syncthreads();
     if (n > 1) {
         const int m = n + (n & 1);
         const int half = m / 2;
-        for (int sweep = 0; sweep < 30; ++sweep) {
-            // convergence: off-diagonal Frobenius norm relative to the whole
+        for (int sweep = 0; sweep < 40; ++sweep) {
             double off = 0.0, all = 0.0;
             for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
                 const double v = A[e];
@@ -181,52 +198,63 @@ __global__ void __launch_bounds__(512) k_eig(const EigTask* __restrict__ tasks) 
             if (stop) break;
             for (int r = 0; r < m - 1; ++r) {
                 for (int k = threadIdx.x; k < half; k += blockDim.x) {
-                    const int pa = (k == 0) ? 0 : ((k - 1 + r) % (m - 1)) + 1;
-                    const int pb = ((m - 1 - k - 1 + r) % (m - 1)) + 1;
+                    int pa, pb;
+                    rr_pair(k, r, m, pa, pb);
                     int p = min(pa, pb), q = max(pa, pb);
                     double c = 1.0, s = 0.0;
                     if (q < n) {
                         const double apq = A[(size_t)p * n + q];
-                        if (apq != 0.0) {
-                            const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                        if (fabs(apq) > 1e-18 * sqrt(fabs(app * aqq)) && apq != 0.0) {
                             const double th = (aqq - app) / (2.0 * apq);
                             const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
                             c = 1.0 / sqrt(tt * tt + 1.0);
                             s = tt * c;
                         }
                     } else {
-                        q = p;  // dummy player: no rotation
+                        q = -1;  // dummy player: no rotation, single index p
                     }
                     Pp[k] = p; Qq[k] = q; Cc[k] = c; Ss[k] = s;
                 }
                 __syncthreads();
-                for (int e = threadIdx.x; e < half * n; e += blockDim.x) {
-                    const int k = e / n, j = e % n;
-                    const int p = Pp[k], q = Qq[k];
-                    if (p == q || Ss[k] == 0.0) continue;
-                    const double c = Cc[k], s = Ss[k];
-                    const double apj = A[(size_t)p * n + j], aqj = A[(size_t)q * n + j];
-                    A[(size_t)p * n + j] = c * apj - s * aqj;
-                    A[(size_t)q * n + j] = s * apj + c * aqj;
+                // A <- J^T A J block by block; V <- V J
+                for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
+                    const int k = e / half, l = e % half;
+                    const int p = Pp[k], q = Qq[k], u = Pp[l], v = Qq[l];
+                    const double ck = Cc[k], sk = Ss[k], cl = Cc[l], sl = Ss[l];
+                    if (sk == 0.0 && sl == 0.0) continue;
+                    // rows p (and q), columns u (and v); rotation: new_p = c*old_p - s*old_q,
+                    // new_q = s*old_p + c*old_q, applied on both sides
+                    const bool hq = q >= 0, hv = v >= 0;
+                    double a_pu = A[(size_t)p * n + u];
+                    double a_pv = hv ? A[(size_t)p * n + v] : 0.0;
+                    double a_qu = hq ? A[(size_t)q * n + u] : 0.0;
+                    double a_qv = (hq && hv) ? A[(size_t)q * n + v] : 0.0;
+                    // left: rows
+                    const double r_pu = ck * a_pu - sk * a_qu, r_qu = sk * a_pu + ck * a_qu;
+                    const double r_pv = ck * a_pv - sk * a_qv, r_qv = sk * a_pv + ck * a_qv;
+                    // right: columns
+                    A[(size_t)p * n + u] = cl * r_pu - sl * r_pv;
+                    if (hv) A[(size_t)p * n + v] = sl * r_pu + cl * r_pv;
+                    if (hq) A[(size_t)q * n + u] = cl * r_qu - sl * r_qv;
+                    if (hq && hv) A[(size_t)q * n + v] = sl * r_qu + cl * r_qv;
                 }
-                __syncthreads();
-                for (int e = threadIdx.x; e < half * n; e += blockDim.x) {
-                    const int k = e % half, i = e / half;
-                    const int p = Pp[k], q = Qq[k];
-                    if (p == q || Ss[k] == 0.0) continue;
-                    const double c = Cc[k], s = Ss[k];
-                    const double aip = A[(size_t)i * n + p], aiq = A[(size_t)i * n + q];
-                    A[(size_t)i * n + p] = c * aip - s * aiq;
-                    A[(size_t)i * n + q] = s * aip + c * aiq;
-                    const double vip = V[(size_t)i * n + p], viq = V[(size_t)i * n + q];
-                    V[(size_t)i * n + p] = c * vip - s * viq;
-                    V[(size_t)i * n + q] = s * vip + c * viq;
+                for (int e = threadIdx.x; e < n * half; e += blockDim.x) {
+                    const int i = e / half, l = e % half;
+                    const int u = Pp[l], v = Qq[l];
+                    const double cl = Cc[l], sl = Ss[l];
+                    if (sl == 0.0 || v < 0) continue;
+                    const double viu = V[(size_t)i * n + u], viv = V[(size_t)i * n + v];
+                    V[(size_t)i * n + u] = cl * viu - sl * viv;
+                    V[(size_t)i * n + v] = sl * viu + cl * viv;
                 }
                 __syncthreads();
             }
         }
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) t.w[i] = A[(size_t)i * n + i];
+    if (in_smem)
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) { t.V[e] = V[e]; t.A[e] = A[e]; }
 }
 
 // ----------------------------------------------------------------- vectors
@@ -436,7 +464,15 @@ void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaSt
     if (ntask > 0) { counted(); k_diag<<<ntask, 256, 0, st>>>(tasks, terms); }
 }
 void launch_eig(const EigTask* tasks, int ntask, cudaStream_t st) {
-    if (ntask > 0) { counted(); k_eig<<<ntask, 512, 0, st>>>(tasks); }
+    if (ntask <= 0) return;
+    static bool attr = false;
+    const int smem = 2 * EIG_SMEM_N * EIG_SMEM_N * (int)sizeof(double);
+    if (!attr) {
+        cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    counted();
+    k_eig<<<ntask, 512, smem, st>>>(tasks);
 }
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st) {
     if (ntask > 0) { counted(); k_copy<<<ntask, 256, 0, st>>>(tasks); }

@@ -46,8 +46,16 @@ def test_medium_local_operators(medium, h0):
         got_s = L.mpspt_local_apply(ctx, h0, psi, i, L.MPSPT_LOCAL_SIGMA, x, x.shape)
         got_g = L.mpspt_local_apply(ctx, h0, psi, i, L.MPSPT_LOCAL_RHS, None, x.shape)
         got_d = L.mpspt_local_apply(ctx, h0, psi, i, L.MPSPT_LOCAL_DIAG, None, x.shape)
-        for got, ref in ((got_s, ref_s), (got_g, ref_g), (got_d, ref_d)):
-            assert np.abs(got - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max()), i
+        # a-priori float64 bound: rounding <= eps * K * (same contraction on |.|)
+        absW = lambda W: {k: np.abs(v) for k, v in W.items()}
+        bnd_s = two_site_apply(np.abs(sw.LA[i]), absW(sw.WA.W[i]), absW(sw.WA.W[i + 1]), np.abs(sw.RA[i + 2]),
+                               np.abs(x), sw.WA.dims[i + 1]) * mask
+        bnd_g = two_site_apply(np.abs(sw.LV[i]), absW(sw.WV.W[i]), absW(sw.WV.W[i + 1]), np.abs(sw.RV[i + 2]),
+                               np.abs(p0), sw.WV.dims[i + 1]) * mask
+        bnd_d = two_site_diag(np.abs(sw.LA[i]), absW(sw.WA.W[i]), absW(sw.WA.W[i + 1]), np.abs(sw.RA[i + 2]),
+                              x.shape, sw.WA.dims[i + 1]) * mask
+        for got, ref, bnd in ((got_s, ref_s, bnd_s), (got_g, ref_g, bnd_g), (got_d, ref_d, bnd_d)):
+            assert np.all(np.abs(got - ref) <= 1e-12 * bnd + 1e-300), i
         done += 1
         if i < 20:
             sw._update_left(i)
