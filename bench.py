@@ -173,24 +173,35 @@ def run_gpu(args):
     o.stream = stream.cuda_stream
     o.prec = L.PREC[args.prec]
     o.e_tol = args.e_tol
+    o.max_sweeps = 64
     ctx = L.mpspt_create(o)
     L.mpspt_set_integrals(ctx, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
     L.mpspt_set_reference(ctx, ci)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def one():
+    def one(c=None):
         flush.zero_()
         torch.cuda.synchronize()
-        e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, args.h0, args.M, want_psi1=False)
+        e2, psi, rep = L.mpspt_minimize_hylleraas(c or ctx, args.h0, args.M, want_psi1=False)
         return e2, rep
 
-    e2_ref = None
-    for w in range(args.warmup):
-        e2, rep = one()
-        if e2_ref is None:
-            e2_ref = e2
-    if e2_ref is None:
-        e2_ref = one()[0]
+    # warm-up 1: the plain float64 sweep converged tightly; it fixes E2_ref
+    # (the float64 E2 at this M) and gives the float64 time-to-E2
+    o64 = L.mpspt_default_options()
+    o64.device = local
+    o64.stream = stream.cuda_stream
+    o64.prec = L.MPSPT_FP64
+    o64.e_tol = args.ref_e_tol
+    o64.max_sweeps = 64
+    ctx64 = L.mpspt_create(o64)
+    L.mpspt_set_integrals(ctx64, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
+    L.mpspt_set_reference(ctx64, ci)
+    e2_ref, rep64 = one(ctx64)
+    L.mpspt_destroy(ctx64)
+    hist64 = [rep64.e2_per_sweep[s] for s in range(rep64.n_sweeps)]
+    t64, s64 = _time_to_e2(rep64, e2_ref)
+    for w in range(max(0, args.warmup - 1)):
+        one()
     sampler, cpath = _clock_sampler() if rank == 0 else (None, None)
     if dist:
         dist.barrier()
@@ -215,7 +226,7 @@ def run_gpu(args):
         dist.barrier()
     # end to end through the public API with host buffers
     e2e_times = []
-    for s in range(args.steps):
+    for s in range(args.e2e_steps):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         ctx2 = L.mpspt_create(o)
@@ -260,6 +271,10 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "E2": statistics.median(e2s), "E2_ref": e2_ref,
         "sweeps": [r.n_sweeps for r in reps],
+        "fp64": {"time_to_e2_s": t64, "sweeps_to_e2": (s64 + 1) if s64 is not None else None,
+                 "sweeps": rep64.n_sweeps, "sigma_tflops": (rep64.sigma_flops / (rep64.sigma_ms * 1e-3) / 1e12)
+                 if rep64.sigma_ms > 0 else None, "e2_history": hist64},
+        "speedup_vs_fp64": (t64 / value) if (t64 and value) else None,
         "sigma_tflops": achieved,
         "roofline": {"bound": "fp64_alu" if args.prec == "fp64" else "tensor", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
@@ -293,9 +308,11 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="medium")
     ap.add_argument("--h0", default="dyall", choices=["dyall", "fock"])
-    ap.add_argument("--M", type=int, default=64)
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "mixed"])
-    ap.add_argument("--e_tol", type=float, default=1e-8)
+    ap.add_argument("--M", type=int, default=256)
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--e_tol", type=float, default=1e-7)
+    ap.add_argument("--ref_e_tol", type=float, default=1e-9)
+    ap.add_argument("--e2e_steps", type=int, default=1)
     ap.add_argument("--ref_budget", type=float, default=15.0)
     ap.add_argument("--ref_sweeps", type=int, default=12)
     ap.add_argument("--no_cpu_baseline", action="store_true")

@@ -133,6 +133,19 @@ mpspt_status mpspt_energies(mpspt_ctx* ctx, mpspt_h0 h0, double* e0, double* e1,
 mpspt_status mpspt_minimize_hylleraas(mpspt_ctx* ctx, mpspt_h0 h0, int M, double* e2,
                                       mpspt_mps** psi1, mpspt_report* rep);
 
+/* Partitioned E2 (the paper's parallelism over virtual-orbital pairs, not
+ * implemented there): H0 conserves the occupation of every semicanonical
+ * virtual orbital, so the first-order problem splits exactly into
+ * partitions P = (a, b), a <= b (0-based virtual indices): one electron in a
+ * and one in b (a < b), or one or two electrons in a (a = b).  Each is an
+ * MPS-PT problem on the chain (active orbitals, a[, b]) minimised with its
+ * own bond dimension M_part[i]; E2 = sum_P E2_P in the given pair order
+ * (float64).  Partitions run concurrently on n_streams CUDA streams (0 =
+ * default 8).  pair_ab: 2*n_part ints; e2_part (nullable) receives E2_P. */
+mpspt_status mpspt_minimize_partitioned(mpspt_ctx* ctx, mpspt_h0 h0, int n_part,
+                                        const int* pair_ab, const int* M_part, int n_streams,
+                                        double* e2_total, double* e2_part, mpspt_report* rep);
+
 /* Eq. 5: E3 = <Psi1|V|Psi1> - E1 <Psi1|Psi1> with V = H - H0 (full
  * Hamiltonian MPO restricted to X), by one transfer sweep. */
 mpspt_status mpspt_third_order(mpspt_ctx* ctx, mpspt_h0 h0, const mpspt_mps* psi1,

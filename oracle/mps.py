@@ -408,7 +408,8 @@ class HylleraasSweep:
     """Two-site MPS-PT2 sweep on the full chain (active sites, then virtual)."""
 
     def __init__(self, prob, M, seed=1408, tol_cg=1e-10, tol_e=1e-10,
-                 max_sweeps=30, cg_maxit=1000, mpo_A=None, mpo_V=None, verbose=False):
+                 max_sweeps=30, cg_maxit=1000, mpo_A=None, mpo_V=None, verbose=False,
+                 allowed=None):
         from .mpo import build_mpo
         self.prob = prob
         self.M = M
@@ -419,7 +420,8 @@ class HylleraasSweep:
         self.cg_maxit = cg_maxit
         self.verbose = verbose
         N = prob.n_elec
-        self.allowed = {prob.k_act: {N - 1, N - 2}}
+        # bond filters: N_left allowed on given cuts (default: first-order space X)
+        self.allowed = allowed if allowed is not None else {prob.k_act: {N - 1, N - 2}}
         self.WA = mpo_A or build_mpo(prob.h0_terms(), self.k, k_split=prob.k_act)
         self.WV = mpo_V or build_mpo(prob.rhs_terms(), self.k, k_split=prob.k_act)
         self.psi0 = reference_mps(prob.ci, prob.k_act, prob.k_virt)

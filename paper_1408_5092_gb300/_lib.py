@@ -71,6 +71,8 @@ def load():
             "mpspt_minimize_hylleraas": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(vp),
                                                         ctypes.POINTER(mpspt_report)]),
             "mpspt_third_order": (ctypes.c_int, [vp, ctypes.c_int, vp, dp]),
+            "mpspt_minimize_partitioned": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, ip, ctypes.c_int, dp, dp,
+                                                          ctypes.POINTER(mpspt_report)]),
             "mpspt_mps_free": (None, [vp]),
             "mpspt_mps_import": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(vp)]),
             "mpspt_mps_shape": (ctypes.c_int, [vp, ip, ip]),
@@ -150,6 +152,20 @@ def mpspt_minimize_hylleraas(ctx, h0, M, want_psi1=True):
     _check(load().mpspt_minimize_hylleraas(ctx, H0.get(h0, h0), M, ctypes.byref(e2),
                                            ctypes.byref(psi) if want_psi1 else None, ctypes.byref(rep)))
     return e2.value, (psi if want_psi1 else None), rep
+
+
+def mpspt_minimize_partitioned(ctx, h0, pairs, Ms, n_streams=0):
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    Ms = np.ascontiguousarray(np.asarray(Ms, dtype=np.int32).reshape(-1))
+    n = len(Ms)
+    e2 = ctypes.c_double()
+    ep = np.zeros(n)
+    rep = mpspt_report()
+    ipp = ctypes.POINTER(ctypes.c_int)
+    _check(load().mpspt_minimize_partitioned(ctx, H0.get(h0, h0), n, pairs.ctypes.data_as(ipp),
+                                             Ms.ctypes.data_as(ipp), n_streams, ctypes.byref(e2), _dp(ep),
+                                             ctypes.byref(rep)))
+    return e2.value, ep, rep
 
 
 def mpspt_third_order(ctx, h0, psi1):

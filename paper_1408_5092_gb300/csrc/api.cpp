@@ -139,6 +139,45 @@ mpspt_status mpspt_minimize_hylleraas(mpspt_ctx* ctx, mpspt_h0 h0, int M, double
     });
 }
 
+namespace {
+void fill_report(mpspt_report* rep, const mpspt::SweepResult& r) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->n_sweeps = (int)r.e2_sweep.size();
+    for (int s = 0; s < rep->n_sweeps && s < 64; ++s) rep->e2_per_sweep[s] = r.e2_sweep[s];
+    rep->max_discarded_weight = r.max_disc;
+    rep->cg_iters = r.cg_iters;
+    rep->sigma_calls = r.sigma_calls;
+    rep->sigma_flops = r.sigma_flops;
+    rep->sigma_ms = r.sigma_ms;
+    rep->wall_ms = r.wall_ms;
+    rep->max_bond_dim = r.max_bond;
+    for (int s = 0; s < rep->n_sweeps && s < 64 && s < (int)r.sweep_ms.size(); ++s) rep->sweep_ms[s] = r.sweep_ms[s];
+    rep->kernel_launches = r.launches;
+    rep->sigma64_calls = r.sigma64_calls;
+    rep->sigma64_flops = r.sigma64_flops;
+    rep->sigma64_ms = r.sigma64_ms;
+}
+}  // namespace
+
+mpspt_status mpspt_minimize_partitioned(mpspt_ctx* ctx, mpspt_h0 h0, int n_part, const int* pair_ab,
+                                        const int* M_part, int n_streams, double* e2_total, double* e2_part,
+                                        mpspt_report* rep) {
+    if (!ctx || !e2_total || n_part < 1 || !pair_ab || !M_part) return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] {
+        auto& c = *ctx->c;
+        MPSPT_CUDA(cudaSetDevice(c.opt.device));
+        std::vector<std::pair<int, int>> pairs(n_part);
+        std::vector<int> Ms(M_part, M_part + n_part);
+        for (int i = 0; i < n_part; ++i) pairs[i] = {pair_ab[2 * i], pair_ab[2 * i + 1]};
+        std::vector<double> ep;
+        mpspt::SweepResult r;
+        const double tot = mpspt::minimize_partitioned(c, h0, pairs, Ms, n_streams > 0 ? n_streams : 8, ep, r);
+        if (rep) fill_report(rep, r);
+        if (e2_part) for (int i = 0; i < n_part; ++i) e2_part[i] = ep[i];
+        *e2_total = tot;
+    });
+}
+
 mpspt_status mpspt_third_order(mpspt_ctx* ctx, mpspt_h0 h0, const mpspt_mps* psi1, double* e3) {
     if (!ctx || !psi1 || !e3) return MPSPT_ERR_INVALID;
     return guard(ctx, [&] {

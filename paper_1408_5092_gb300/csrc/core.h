@@ -125,8 +125,8 @@ class DBuf {
     DBuf& operator=(DBuf&& o) noexcept {
         if (this != &o) {
             release();
-            p_ = o.p_; n_ = o.n_; st_ = o.st_;
-            o.p_ = nullptr; o.n_ = 0;
+            p_ = o.p_; n_ = o.n_; st_ = o.st_; owned_ = o.owned_;
+            o.p_ = nullptr; o.n_ = 0; o.owned_ = true;
         }
         return *this;
     }
@@ -143,9 +143,17 @@ class DBuf {
         if (bytes > n_) alloc(bytes + bytes / 4, st);
     }
     void release() {
-        if (p_) { Registry::get().remove(p_); cudaFreeAsync(p_, st_); }
+        if (p_ && owned_) { Registry::get().remove(p_); cudaFreeAsync(p_, st_); }
         p_ = nullptr;
         n_ = 0;
+        owned_ = true;
+    }
+    // non-owning view of memory owned by another buffer
+    void make_view(void* p, size_t bytes) {
+        release();
+        p_ = p;
+        n_ = bytes;
+        owned_ = false;
     }
     template <class T> T* as() const { return static_cast<T*>(p_); }
     void* get() const { return p_; }
@@ -155,6 +163,7 @@ class DBuf {
     void* p_ = nullptr;
     size_t n_ = 0;
     cudaStream_t st_ = 0;
+    bool owned_ = true;
 };
 
 template <class T>

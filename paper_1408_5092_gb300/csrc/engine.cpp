@@ -2,7 +2,9 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -12,9 +14,33 @@
 namespace mpspt {
 
 // ------------------------------------------------------------------ context
+Lane::Lane(cudaStream_t s, bool create) : st(s), own_stream(create) {
+    if (create) MPSPT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    red.alloc(4 * 1024 * sizeof(double), st);
+    cnt.alloc(64, st);
+    MPSPT_CUDA(cudaMemsetAsync(cnt.get(), 0, 64, st));
+    cg.alloc(sizeof(CgState), st);
+    scal.alloc(16 * sizeof(double), st);
+    tcerr.alloc(sizeof(int) * 4, st);
+    MPSPT_CUDA(cudaMemsetAsync(tcerr.get(), 0, sizeof(int) * 4, st));
+    MPSPT_CUDA(cudaMallocHost(&cg_host, sizeof(CgState)));
+    MPSPT_CUDA(cudaMallocHost(&scal_host, 16 * sizeof(double)));
+    MPSPT_CUDA(cudaStreamSynchronize(st));
+}
+
+Lane::~Lane() {
+    cudaStreamSynchronize(st);
+    red.release(); cnt.release(); cg.release(); scal.release(); tcerr.release();
+    cudaStreamSynchronize(st);
+    if (cg_host) cudaFreeHost(cg_host);
+    if (scal_host) cudaFreeHost(scal_host);
+    if (own_stream) cudaStreamDestroy(st);
+}
+
 Ctx::Ctx(const mpspt_options& o) : opt(o) {
     MPSPT_CUDA(cudaSetDevice(o.device));
     st = static_cast<cudaStream_t>(o.stream);
+    lane0.reset(new Lane(st));
     red.alloc(4 * 1024 * sizeof(double), st);
     cnt.alloc(64, st);
     MPSPT_CUDA(cudaMemsetAsync(cnt.get(), 0, 64, st));
@@ -556,8 +582,9 @@ void check_copies(const std::vector<CopyTask>& ct, const std::vector<int>& colv,
 
 struct Sweeper {
     Ctx& c;
-    const Problem& P;
-    int h0, M;
+    Lane& ln;
+    const Chain& ch;
+    int M;
     const MPO& WA;
     const MPO& WV;
     MpsD& psi;
@@ -576,32 +603,34 @@ struct Sweeper {
     SweepResult* res = nullptr;
     cudaEvent_t ev0, ev1;
 
-    Sweeper(Ctx& c_, int h0_, int M_, MpsD& psi_)
-        : c(c_), P(c_.P), h0(h0_), M(M_), WA(c_.A_mpo(h0_)), WV(c_.V_mpo()), psi(psi_), psi0(c_.psi0) {
-        filt = cut_filters(P);
-        const int k = P.k;
+    Sweeper(Ctx& c_, Lane& ln_, const Chain& ch_, int M_, MpsD& psi_)
+        : c(c_), ln(ln_), ch(ch_), M(M_), WA(*ch_.WA), WV(*ch_.WV), psi(psi_), psi0(ch_.psi0) {
+        filt = ch.filt;
+        const int k = ch.nsite;
         LA.resize(k + 1); LV.resize(k + 1); RA.resize(k + 1); RV.resize(k + 1);
         if (c.opt.prec == MPSPT_MIXED_BF16) lo_kind = GEMM_TC;
         else if (c.opt.prec == MPSPT_FP32) lo_kind = GEMM_F32;
-        sig_lo.set_kind(lo_kind, c.tcerr.as<int>());
+        sig_lo.set_kind(lo_kind, ln.tcerr.as<int>());
         sig.set_kind(GEMM_F64, nullptr);
         rhs.set_kind(GEMM_F64, nullptr);
         MPSPT_CUDA(cudaEventCreate(&ev0));
         MPSPT_CUDA(cudaEventCreate(&ev1));
         for (auto& e : evs) MPSPT_CUDA(cudaEventCreate(&e));
+        for (auto& e : sev) MPSPT_CUDA(cudaEventCreate(&e));
     }
     ~Sweeper() {
         cudaEventDestroy(ev0); cudaEventDestroy(ev1);
         for (auto& e : evs) cudaEventDestroy(e);
+        for (auto& e : sev) cudaEventDestroy(e);
     }
 
     void boundary_envs() {
-        const int k = P.k;
+        const int k = ch.nsite;
         auto one = [&](EnvT& E, const std::vector<QN>& dq, const Bond& b, const Bond& k0) {
-            E.build(dq, b, k0, c.st);
+            E.build(dq, b, k0, ln.st);
             const double v = 1.0;
-            MPSPT_CUDA(cudaMemcpyAsync(E.d.get(), &v, sizeof(double), cudaMemcpyHostToDevice, c.st));
-            MPSPT_CUDA(cudaStreamSynchronize(c.st));
+            MPSPT_CUDA(cudaMemcpyAsync(E.d.get(), &v, sizeof(double), cudaMemcpyHostToDevice, ln.st));
+            MPSPT_CUDA(cudaStreamSynchronize(ln.st));
         };
         one(LA[0], WA.dq[0], psi.bond[0], psi.bond[0]);
         one(LV[0], WV.dq[0], psi.bond[0], psi0.bond[0]);
@@ -610,25 +639,25 @@ struct Sweeper {
     }
 
     void update_left(int i) {   // L[i+1] from L[i] and site i
-        LA[i + 1].build(WA.dq[i + 1], psi.bond[i + 1], psi.bond[i + 1], c.st);
+        LA[i + 1].build(WA.dq[i + 1], psi.bond[i + 1], psi.bond[i + 1], ln.st);
         envp.build_left(WA, i, LA[i], psi.A[i], psi.A[i], psi.bond[i], psi.bond[i], psi.bond[i + 1],
-                        psi.bond[i + 1], LA[i + 1], c.st);
-        envp.run(c.st);
-        LV[i + 1].build(WV.dq[i + 1], psi.bond[i + 1], psi0.bond[i + 1], c.st);
+                        psi.bond[i + 1], LA[i + 1], ln.st);
+        envp.run(ln.st);
+        LV[i + 1].build(WV.dq[i + 1], psi.bond[i + 1], psi0.bond[i + 1], ln.st);
         envp.build_left(WV, i, LV[i], psi.A[i], psi0.A[i], psi.bond[i], psi0.bond[i], psi.bond[i + 1],
-                        psi0.bond[i + 1], LV[i + 1], c.st);
-        envp.run(c.st);
+                        psi0.bond[i + 1], LV[i + 1], ln.st);
+        envp.run(ln.st);
     }
 
     void update_right(int i) {  // R[i] from R[i+1] and site i
-        RA[i].build(WA.dq[i], psi.bond[i], psi.bond[i], c.st);
+        RA[i].build(WA.dq[i], psi.bond[i], psi.bond[i], ln.st);
         envp.build_right(WA, i, RA[i + 1], psi.A[i], psi.A[i], psi.bond[i], psi.bond[i], psi.bond[i + 1],
-                         psi.bond[i + 1], RA[i], c.st);
-        envp.run(c.st);
-        RV[i].build(WV.dq[i], psi.bond[i], psi0.bond[i], c.st);
+                         psi.bond[i + 1], RA[i], ln.st);
+        envp.run(ln.st);
+        RV[i].build(WV.dq[i], psi.bond[i], psi0.bond[i], ln.st);
         envp.build_right(WV, i, RV[i + 1], psi.A[i], psi0.A[i], psi.bond[i], psi0.bond[i], psi.bond[i + 1],
-                         psi0.bond[i + 1], RV[i], c.st);
-        envp.run(c.st);
+                         psi0.bond[i + 1], RV[i], ln.st);
+        envp.run(ln.st);
     }
 
     // x (device, X layout) -> new A_i, A_{i+1}, bond i+1.  dir 0: left-to-right.
@@ -656,11 +685,11 @@ struct Sweeper {
             rs += (size_t)kv.second.dim * kv.second.dim;
             cl.push_back(kv.second);
         }
-        rho.ensure((rs + 1) * sizeof(double), c.st);
-        V.ensure((rs + 1) * sizeof(double), c.st);
+        rho.ensure((rs + 1) * sizeof(double), ln.st);
+        V.ensure((rs + 1) * sizeof(double), ln.st);
         size_t wsz = 0;
         for (auto& cp : cl) wsz += cp.dim;
-        wv.ensure((wsz + 1) * sizeof(double), c.st);
+        wv.ensure((wsz + 1) * sizeof(double), ln.st);
         double* rhop = rho.as<double>();
         // rho blocks
         gr.clear();
@@ -693,8 +722,10 @@ struct Sweeper {
                     gr.block(rhop + cp.rho_off + (size_t)m1.roff * cp.dim + m2.roff, cp.dim, m1.dim, m2.dim, 0, m0);
                 }
         }
-        gr.upload(c.st);
-        gr.run(c.st);
+        gr.upload(ln.st);
+        if (c.opt.verbose >= 3) MPSPT_CUDA(cudaEventRecord(sev[0], ln.st));
+        gr.run(ln.st);
+        if (c.opt.verbose >= 3) MPSPT_CUDA(cudaEventRecord(sev[1], ln.st));
         // eigen-decomposition per composite sector
         std::vector<EigTask> et;
         size_t wo = 0;
@@ -710,11 +741,17 @@ struct Sweeper {
             check_range(t.V, (size_t)t.n * t.n * sizeof(double), "eig V");
             check_range(t.w, (size_t)t.n * sizeof(double), "eig w");
         }
-        upload(etasks, et, c.st);
-        launch_eig(etasks.as<EigTask>(), (int)et.size(), c.st);
+        upload(etasks, et, ln.st);
+        launch_eig(etasks.as<EigTask>(), (int)et.size(), ln.st);
+        if (c.opt.verbose >= 3) {
+            MPSPT_CUDA(cudaEventRecord(sev[2], ln.st));
+            double n3 = 0; int nmax = 0;
+            for (const auto& t : et) { n3 += (double)t.n * t.n * t.n; nmax = std::max(nmax, t.n); }
+            eig_n3 += n3; eig_nmax = std::max(eig_nmax, nmax); eig_calls += (int)et.size();
+        }
         std::vector<double> wh(wsz);
-        if (wsz) MPSPT_CUDA(cudaMemcpyAsync(wh.data(), wv.get(), wsz * sizeof(double), cudaMemcpyDeviceToHost, c.st));
-        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        if (wsz) MPSPT_CUDA(cudaMemcpyAsync(wh.data(), wv.get(), wsz * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
+        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
         // selection: keep the Mkeep largest (ties at the cut dropped as a group)
         struct Cand { double lam; int ci; int rank; int col; };
         std::vector<Cand> cand;
@@ -763,16 +800,16 @@ struct Sweeper {
         std::vector<int> colv;
         std::vector<size_t> coff(cl.size(), 0);
         for (size_t ci = 0; ci < cl.size(); ++ci) { coff[ci] = colv.size(); colv.insert(colv.end(), kcols[ci].begin(), kcols[ci].end()); }
-        upload(cols, colv, c.st);
+        upload(cols, colv, ln.st);
         const int* colp = cols.as<int>();
         psi.bond[i + 1] = nb;
         SiteT An, Bn;
-        An.build(bL, nb, c.st);
-        Bn.build(nb, bR, c.st);
+        An.build(bL, nb, ln.st);
+        Bn.build(nb, bR, ln.st);
         std::vector<CopyTask> ct;
         gc.clear();
         if (dir == 0) {
-            if (An.n) MPSPT_CUDA(cudaMemsetAsync(An.d.get(), 0, An.n * sizeof(double), c.st));
+            if (An.n) MPSPT_CUDA(cudaMemsetAsync(An.d.get(), 0, An.n * sizeof(double), ln.st));
             for (const auto& b : An.blk) {
                 const int ci = std::find_if(cl.begin(), cl.end(), [&](const Comp& cp) { return cp.q == nb.sec[b.sr].q; }) - cl.begin();
                 const Comp& cp = cl[ci];
@@ -782,8 +819,8 @@ struct Sweeper {
                                       colp + coff[ci], mm.dim, nb.sec[b.sr].dim, cp.dim, nb.sec[b.sr].dim, 0, 0});
             }
             check_copies(ct, colv, colp);
-            upload(ctasks, ct, c.st);
-            launch_copy(ctasks.as<CopyTask>(), (int)ct.size(), c.st);
+            upload(ctasks, ct, ln.st);
+            launch_copy(ctasks.as<CopyTask>(), (int)ct.size(), ln.st);
             // carry: B(Q, s2, sr) = sum_(sl,s1) A(sl,s1,Q)^T x(sl,s1,s2)
             for (const auto& b : Bn.blk) {
                 int m0 = gc.mark();
@@ -800,7 +837,7 @@ struct Sweeper {
                 gc.block(Bn.ptr(b), bR.sec[b.sr].dim, kq, bR.sec[b.sr].dim, 0, m0);
             }
         } else {
-            if (Bn.n) MPSPT_CUDA(cudaMemsetAsync(Bn.d.get(), 0, Bn.n * sizeof(double), c.st));
+            if (Bn.n) MPSPT_CUDA(cudaMemsetAsync(Bn.d.get(), 0, Bn.n * sizeof(double), ln.st));
             for (const auto& b : Bn.blk) {
                 const int ci = std::find_if(cl.begin(), cl.end(), [&](const Comp& cp) { return cp.q == nb.sec[b.sl].q; }) - cl.begin();
                 const Comp& cp = cl[ci];
@@ -810,8 +847,8 @@ struct Sweeper {
                                       colp + coff[ci], nb.sec[b.sl].dim, mm.dim, cp.dim, mm.dim, 1, 0});
             }
             check_copies(ct, colv, colp);
-            upload(ctasks, ct, c.st);
-            launch_copy(ctasks.as<CopyTask>(), (int)ct.size(), c.st);
+            upload(ctasks, ct, ln.st);
+            launch_copy(ctasks.as<CopyTask>(), (int)ct.size(), ln.st);
             // carry: A(sl, s1, Q) = sum_(s2,sr) x(sl,s1,s2,sr) B(Q,s2,sr)^T
             for (const auto& b : An.blk) {
                 int m0 = gc.mark();
@@ -828,11 +865,20 @@ struct Sweeper {
                 gc.block(An.ptr(b), kq, bL.sec[b.sl].dim, kq, 0, m0);
             }
         }
-        gc.upload(c.st);
-        gc.run(c.st);
+        gc.upload(ln.st);
+        gc.run(ln.st);
+        if (c.opt.verbose >= 3) {
+            MPSPT_CUDA(cudaEventRecord(sev[3], ln.st));
+            MPSPT_CUDA(cudaEventSynchronize(sev[3]));
+            float a = 0, b = 0, d = 0;
+            cudaEventElapsedTime(&a, sev[0], sev[1]);
+            cudaEventElapsedTime(&b, sev[1], sev[2]);
+            cudaEventElapsedTime(&d, sev[2], sev[3]);
+            t_rho += a; t_eig += b; t_post += d;
+        }
         psi.A[i] = std::move(An);
         psi.A[i + 1] = std::move(Bn);
-        MPSPT_CUDA(cudaStreamSynchronize(c.st));   // plans above reference host vectors
+        MPSPT_CUDA(cudaStreamSynchronize(ln.st));   // plans above reference host vectors
         return tr > 0 ? std::max(0.0, (tr - kept_w) / tr) : 0.0;
     }
 
@@ -840,21 +886,21 @@ struct Sweeper {
     void product(GemmPlan& g, const MpsD& m, int i, const TwoT& Xl, double* xd) {
         g.clear();
         plan_product(g, Xl, xd, m.bond[i + 1], m.A[i], m.A[i + 1], m.bond[i]);
-        g.upload(c.st);
-        g.run(c.st);
+        g.upload(ln.st);
+        g.run(ln.st);
     }
 
     void right_canonicalize() {
-        for (int i = P.k - 2; i >= 0; --i) {
+        for (int i = ch.nsite - 2; i >= 0; --i) {
             X.build(psi.bond[i], psi.bond[i + 2], filt[i + 1]);
-            w.ensure(X.n, 1, c.st);
+            w.ensure(X.n, 1, ln.st);
             product(prod, psi, i, X, w.x.as<double>());
             split(i, 1, 1 << 30, X, w.x.as<double>());
         }
     }
 
     double dot(const double* a, const double* b, size_t n, int slot) {
-        vec_dot(a, b, n, c.scal.as<double>() + slot, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
+        vec_dot(a, b, n, ln.scal.as<double>() + slot, ln.red.as<double>(), ln.cnt.as<unsigned>(), ln.st);
         return 0.0;
     }
 
@@ -866,22 +912,22 @@ struct Sweeper {
     int nev = 0;
     void ev_begin() {
         if (nev == NEV) add_time();
-        MPSPT_CUDA(cudaEventRecord(evs[2 * nev], c.st));
+        MPSPT_CUDA(cudaEventRecord(evs[2 * nev], ln.st));
     }
     void ev_end(bool is64) {
-        MPSPT_CUDA(cudaEventRecord(evs[2 * nev + 1], c.st));
+        MPSPT_CUDA(cudaEventRecord(evs[2 * nev + 1], ln.st));
         ev_is64[nev++] = is64;
     }
     void sigma64() {
         ev_begin();
-        sig.run(c.st);
+        sig.run(ln.st);
         ev_end(true);
         res->sigma64_calls++;
         res->sigma64_flops += sig.flops();
     }
     void sigma_lo() {
         ev_begin();
-        sig_lo.run(c.st);
+        sig_lo.run(ln.st);
         ev_end(false);
         res->sigma_calls++;
         res->sigma_flops += sig_lo.flops();
@@ -898,15 +944,15 @@ struct Sweeper {
         nev = 0;
     }
     void sync_state() {
-        MPSPT_CUDA(cudaMemcpyAsync(c.cg_host, c.cg.as<CgState>(), sizeof(CgState), cudaMemcpyDeviceToHost, c.st));
-        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        MPSPT_CUDA(cudaMemcpyAsync(ln.cg_host, ln.cg.as<CgState>(), sizeof(CgState), cudaMemcpyDeviceToHost, ln.st));
+        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
         add_time();
     }
     void check_tc() {
         if (lo_kind != GEMM_TC) return;
         int e = 0;
-        MPSPT_CUDA(cudaMemcpyAsync(&e, c.tcerr.get(), sizeof(int), cudaMemcpyDeviceToHost, c.st));
-        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        MPSPT_CUDA(cudaMemcpyAsync(&e, ln.tcerr.get(), sizeof(int), cudaMemcpyDeviceToHost, ln.st));
+        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
         require(e == 0, "tensor-core GEMM: bounded mbarrier wait gave up", MPSPT_ERR_TIMEOUT);
     }
 
@@ -915,41 +961,41 @@ struct Sweeper {
         double* x = w.x.as<double>();
         dot(x, w.Ap.as<double>(), n, 0);
         dot(x, w.g.as<double>(), n, 1);
-        MPSPT_CUDA(cudaMemcpyAsync(c.scal_host, c.scal.get(), 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
-        MPSPT_CUDA(cudaStreamSynchronize(c.st));
-        return c.scal_host[0] + 2.0 * c.scal_host[1];
+        MPSPT_CUDA(cudaMemcpyAsync(ln.scal_host, ln.scal.get(), 2 * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
+        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        return ln.scal_host[0] + 2.0 * ln.scal_host[1];
     }
 
     // Plain float64 Jacobi-PCG on A x = b from the warm start x.
     double solve_plain(size_t n) {
         double* x = w.x.as<double>();
-        CgState* S = c.cg.as<CgState>();
-        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+        CgState* S = ln.cg.as<CgState>();
+        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
         sigma64();
         cg_init(w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.b.as<double>(), w.Ap.as<double>(),
-                w.minv.as<double>(), n, S, c.opt.cg_tol, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
+                w.minv.as<double>(), n, S, c.opt.cg_tol, ln.red.as<double>(), ln.cnt.as<unsigned>(), ln.st);
         sync_state();
         int launched = 0;
         sig.set_skip(&S->done);
-        while (!c.cg_host->done && launched < c.opt.cg_max_iter) {
+        while (!ln.cg_host->done && launched < c.opt.cg_max_iter) {
             const int chunk = std::min(c.opt.cg_max_iter - launched, launched < 8 ? 4 : 8);
             for (int q = 0; q < chunk; ++q) {
                 sigma64();
                 cg_step(x, w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.Ap.as<double>(),
-                        w.minv.as<double>(), n, S, c.red.as<double>(), c.cnt.as<unsigned>(), c.st);
+                        w.minv.as<double>(), n, S, ln.red.as<double>(), ln.cnt.as<unsigned>(), ln.st);
             }
             launched += chunk;
             sync_state();
         }
         sig.set_skip(nullptr);
-        require(!c.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
+        require(!ln.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
                 MPSPT_ERR_NOT_SPD);
-        res->cg_iters += c.cg_host->iters;
-        res->sigma64_calls -= launched - c.cg_host->iters;   // skipped launches did no work
-        res->sigma64_flops -= (launched - c.cg_host->iters) * sig.flops();
-        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+        res->cg_iters += ln.cg_host->iters;
+        res->sigma64_calls -= launched - ln.cg_host->iters;   // skipped launches did no work
+        res->sigma64_flops -= (launched - ln.cg_host->iters) * sig.flops();
+        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
         sigma64();
-        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
         add_time();
         return hylleraas(n);
     }
@@ -959,48 +1005,48 @@ struct Sweeper {
     // residual meets cg_tol.  The last float64 A x gives the Hylleraas value.
     double solve_refined(size_t n) {
         double* x = w.x.as<double>();
-        CgState* S = c.cg.as<CgState>();
+        CgState* S = ln.cg.as<CgState>();
         const int max_outer = 12;
         const double tol_in = 1e-4;
         dot(w.b.as<double>(), w.b.as<double>(), n, 2);
         for (int outer = 0;; ++outer) {
-            MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+            MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
             sigma64();
-            MPSPT_CUDA(cudaMemcpyAsync(w.r.get(), w.b.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
-            vec_axpy(w.r.as<double>(), w.Ap.as<double>(), -1.0, n, c.st);
+            MPSPT_CUDA(cudaMemcpyAsync(w.r.get(), w.b.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
+            vec_axpy(w.r.as<double>(), w.Ap.as<double>(), -1.0, n, ln.st);
             dot(w.r.as<double>(), w.r.as<double>(), n, 3);
-            MPSPT_CUDA(cudaMemcpyAsync(c.scal_host, c.scal.get(), 4 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
-            MPSPT_CUDA(cudaStreamSynchronize(c.st));
+            MPSPT_CUDA(cudaMemcpyAsync(ln.scal_host, ln.scal.get(), 4 * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
+            MPSPT_CUDA(cudaStreamSynchronize(ln.st));
             add_time();
-            const double bb = c.scal_host[2], rr = c.scal_host[3];
+            const double bb = ln.scal_host[2], rr = ln.scal_host[3];
             if (rr <= c.opt.cg_tol * c.opt.cg_tol * bb || bb == 0.0 || outer == max_outer) break;
             // inner solve from d = 0 (the Ap buffer is reused by the inner operator)
-            MPSPT_CUDA(cudaMemsetAsync(w.d.get(), 0, n * sizeof(double), c.st));
+            MPSPT_CUDA(cudaMemsetAsync(w.d.get(), 0, n * sizeof(double), ln.st));
             cg_init(w.ri.as<double>(), w.z.as<double>(), w.p.as<double>(), w.r.as<double>(),
-                    w.zero.as<double>(), w.minv.as<double>(), n, S, tol_in, c.red.as<double>(),
-                    c.cnt.as<unsigned>(), c.st);
-            MPSPT_CUDA(cudaMemcpyAsync(c.cg_host, S, sizeof(CgState), cudaMemcpyDeviceToHost, c.st));
-            MPSPT_CUDA(cudaStreamSynchronize(c.st));
+                    w.zero.as<double>(), w.minv.as<double>(), n, S, tol_in, ln.red.as<double>(),
+                    ln.cnt.as<unsigned>(), ln.st);
+            MPSPT_CUDA(cudaMemcpyAsync(ln.cg_host, S, sizeof(CgState), cudaMemcpyDeviceToHost, ln.st));
+            MPSPT_CUDA(cudaStreamSynchronize(ln.st));
             int launched = 0;
             sig_lo.set_skip(&S->done);
-            while (!c.cg_host->done && launched < c.opt.cg_max_iter) {
+            while (!ln.cg_host->done && launched < c.opt.cg_max_iter) {
                 const int chunk = std::min(c.opt.cg_max_iter - launched, launched < 8 ? 4 : 8);
                 for (int q = 0; q < chunk; ++q) {
                     sigma_lo();
                     cg_step(w.d.as<double>(), w.ri.as<double>(), w.z.as<double>(), w.p.as<double>(),
-                            w.Ap.as<double>(), w.minv.as<double>(), n, S, c.red.as<double>(),
-                            c.cnt.as<unsigned>(), c.st);
+                            w.Ap.as<double>(), w.minv.as<double>(), n, S, ln.red.as<double>(),
+                            ln.cnt.as<unsigned>(), ln.st);
                 }
                 launched += chunk;
                 sync_state();
             }
             sig_lo.set_skip(nullptr);
-            require(!c.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
+            require(!ln.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
                     MPSPT_ERR_NOT_SPD);
-            res->cg_iters += c.cg_host->iters;
-            res->sigma_calls -= launched - c.cg_host->iters;
-            res->sigma_flops -= (launched - c.cg_host->iters) * sig_lo.flops();
-            vec_axpy(x, w.d.as<double>(), 1.0, n, c.st);
+            res->cg_iters += ln.cg_host->iters;
+            res->sigma_calls -= launched - ln.cg_host->iters;
+            res->sigma_flops -= (launched - ln.cg_host->iters) * sig_lo.flops();
+            vec_axpy(x, w.d.as<double>(), 1.0, n, ln.st);
         }
         return hylleraas(n);   // w.Ap holds the float64 A x of the final x
     }
@@ -1008,6 +1054,9 @@ struct Sweeper {
     // one bond step; returns h_loc
     // host-side phase timers (printed with verbose >= 2)
     double t_plan = 0, t_rhs = 0, t_solve = 0, t_split = 0, t_env = 0;
+    double t_rho = 0, t_eig = 0, t_post = 0, eig_n3 = 0;   // device ms (verbose >= 3)
+    int eig_nmax = 0, eig_calls = 0;
+    cudaEvent_t sev[4];
     using clk = std::chrono::steady_clock;
     static double since(clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); }
 
@@ -1017,26 +1066,26 @@ struct Sweeper {
         X.build(bL, bR, filt[i + 1]);
         X0.build(psi0.bond[i], psi0.bond[i + 2], {});
         const size_t n = X.n;
-        w.ensure(n, X0.n, c.st);
+        w.ensure(n, X0.n, ln.st);
         double* x = w.x.as<double>();
         product(prod, psi, i, X, x);
         product(prod0, psi0, i, X0, w.x0.as<double>());
         omA.build(WA, i);
         omV.build(WV, i);
         rhs.build(omV, X, X0, bL, psi0.bond[i], bR, psi0.bond[i + 2], LV[i], RV[i + 2], WV.dq[i + 2],
-                  w.x0.as<double>(), w.g.as<double>(), c.st);
-        rhs.run(c.st);
-        if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(c.st)); t_rhs += since(t0); t0 = clk::now(); }
+                  w.x0.as<double>(), w.g.as<double>(), ln.st);
+        rhs.run(ln.st);
+        if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_rhs += since(t0); t0 = clk::now(); }
         sig.build(omA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
-                  w.Ap.as<double>(), c.st);
-        dia.build(omA, X, bL, bR, LA[i], RA[i + 2], WA.dq[i], WA.dq[i + 2], w.minv.as<double>(), c.st);
-        dia.run(c.st);
-        make_minv(w.minv.as<double>(), w.minv.as<double>(), n, c.st);
-        vec_scale_mask(w.b.as<double>(), w.g.as<double>(), -1.0, n, c.st);
+                  w.Ap.as<double>(), ln.st);
+        dia.build(omA, X, bL, bR, LA[i], RA[i + 2], WA.dq[i], WA.dq[i + 2], w.minv.as<double>(), ln.st);
+        dia.run(ln.st);
+        make_minv(w.minv.as<double>(), w.minv.as<double>(), n, ln.st);
+        vec_scale_mask(w.b.as<double>(), w.g.as<double>(), -1.0, n, ln.st);
         if (lo_kind != GEMM_F64)
             sig_lo.build(omA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
-                         w.Ap.as<double>(), c.st);
-        if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(c.st)); t_plan += since(t0); t0 = clk::now(); }
+                         w.Ap.as<double>(), ln.st);
+        if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_plan += since(t0); t0 = clk::now(); }
         const double h = (lo_kind == GEMM_F64) ? solve_plain(n) : solve_refined(n);
         check_tc();
         if (c.opt.verbose >= 2) { t_solve += since(t0); t0 = clk::now(); }
@@ -1046,17 +1095,17 @@ struct Sweeper {
         if (c.opt.verbose >= 2) { t_split += since(t0); t0 = clk::now(); }
         if (dir == 0) update_left(i);
         else update_right(i + 1);
-        if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(c.st)); t_env += since(t0); }
+        if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_env += since(t0); }
         return h;
     }
 };
 
 }  // namespace
 
-std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
+std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res, Lane* lane) {
+    Lane& ln = lane ? *lane : *c.lane0;
     require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
     require(M >= 1, "bond dimension M must be >= 1");
-    require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
     require(c.opt.prec == MPSPT_FP64 || c.opt.prec == MPSPT_FP32 || c.opt.prec == MPSPT_MIXED_BF16,
             "unknown precision mode");
     const auto t0 = std::chrono::steady_clock::now();
@@ -1065,14 +1114,14 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
     cudaEvent_t e_start;
     std::vector<cudaEvent_t> e_sweep;
     MPSPT_CUDA(cudaEventCreate(&e_start));
-    MPSPT_CUDA(cudaEventRecord(e_start, c.st));
-    const Problem& P = c.P;
+    MPSPT_CUDA(cudaEventRecord(e_start, ln.st));
+    const int nsite = ch.nsite;
     // initial Psi1
     MpsHost ih;
-    ih.nsite = P.k;
-    ih.bond = initial_bonds(P.k, QN(P.nel, 0), cut_filters(P), M);
-    ih.T.resize(P.k);
-    for (int s = 0; s < P.k; ++s) {
+    ih.nsite = nsite;
+    ih.bond = initial_bonds(nsite, ch.target, ch.filt, M);
+    ih.T.resize(nsite);
+    for (int s = 0; s < nsite; ++s) {
         const Bond &L = ih.bond[s], &R = ih.bond[s + 1];
         ih.T[s].assign((size_t)L.total * 4 * R.total, 0.0);
         for (const auto& sl : L.sec)
@@ -1086,23 +1135,23 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
                             init_value(c.opt.seed, s, t, sl.off + a, rs.off + b);
             }
     }
-    std::unique_ptr<MpsD> psi = mps_upload(ih, c.st);
-    Sweeper sw(c, h0, M, *psi);
+    std::unique_ptr<MpsD> psi = mps_upload(ih, ln.st);
+    Sweeper sw(c, ln, ch, M, *psi);
     sw.res = &res;
     sw.right_canonicalize();
     sw.boundary_envs();
-    for (int i = P.k - 1; i >= 1; --i) sw.update_right(i);
+    for (int i = nsite - 1; i >= 1; --i) sw.update_right(i);
     double prev = 0.0;
     const int maxs = std::min(64, std::max(1, c.opt.max_sweeps));
     for (int s = 0; s < maxs; ++s) {
         res.max_disc = 0.0;
         double e = 0.0;
-        for (int i = 0; i <= P.k - 2; ++i) e = sw.step(i, 0);
-        for (int i = P.k - 2; i >= 0; --i) e = sw.step(i, 1);
+        for (int i = 0; i <= nsite - 2; ++i) e = sw.step(i, 0);
+        for (int i = nsite - 2; i >= 0; --i) e = sw.step(i, 1);
         res.e2_sweep.push_back(e);
         cudaEvent_t ev;
         MPSPT_CUDA(cudaEventCreate(&ev));
-        MPSPT_CUDA(cudaEventRecord(ev, c.st));
+        MPSPT_CUDA(cudaEventRecord(ev, ln.st));
         e_sweep.push_back(ev);
         if (c.opt.verbose)
             fprintf(stderr, "[mpspt] sweep %d  E2 = %.12f  max discarded %.3e  cg %lld\n", s, e,
@@ -1110,6 +1159,9 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
         if (c.opt.verbose >= 2)
             fprintf(stderr, "[mpspt]   host ms: rhs %.1f plan %.1f solve %.1f split %.1f env %.1f | sigma dev ms %.1f (64: %.1f)\n",
                     sw.t_rhs, sw.t_plan, sw.t_solve, sw.t_split, sw.t_env, res.sigma_ms, res.sigma64_ms);
+        if (c.opt.verbose >= 3)
+            fprintf(stderr, "[mpspt]   split dev ms: rho %.1f eig %.1f post %.1f | eig tasks %d nmax %d sum n^3 %.3g\n",
+                    sw.t_rho, sw.t_eig, sw.t_post, sw.eig_calls, sw.eig_nmax, sw.eig_n3);
         if (s > 0 && std::fabs(e - prev) < c.opt.e_tol) break;
         prev = e;
     }
@@ -1118,7 +1170,7 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
     if (c.opt.prec == MPSPT_FP64) {   // all applications are float64: report them as sigma
         res.sigma_calls = res.sigma64_calls; res.sigma_flops = res.sigma64_flops; res.sigma_ms = res.sigma64_ms;
     }
-    MPSPT_CUDA(cudaStreamSynchronize(c.st));
+    MPSPT_CUDA(cudaStreamSynchronize(ln.st));
     for (cudaEvent_t ev : e_sweep) {
         float ms = 0.f;
         MPSPT_CUDA(cudaEventElapsedTime(&ms, e_start, ev));
@@ -1128,6 +1180,173 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
     cudaEventDestroy(e_start);
     res.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return psi;
+}
+
+std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res) {
+    require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
+    require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
+    Chain ch = full_chain(c, h0);
+    return minimize(c, ch, M, res);
+}
+
+namespace {
+// Views of the context's reference MPS: site map s -> full-chain site.
+void view_psi0(const Ctx& c, const std::vector<int>& sites, MpsD& out) {
+    out.nsite = (int)sites.size();
+    out.bond.clear();
+    out.A.clear();
+    out.A.resize(sites.size());
+    out.bond.push_back(c.psi0.bond[sites[0]]);
+    for (size_t s = 0; s < sites.size(); ++s) {
+        const SiteT& src = c.psi0.A[sites[s]];
+        SiteT& dst = out.A[s];
+        dst.blk = src.blk;
+        dst.idx = src.idx;
+        dst.n = src.n;
+        dst.d.make_view(src.d.get(), src.n * sizeof(double));
+        out.bond.push_back(c.psi0.bond[sites[s] + 1]);
+    }
+}
+}  // namespace
+
+Chain full_chain(Ctx& c, int h0) {
+    Chain ch;
+    const Problem& P = c.P;
+    ch.nsite = P.k;
+    ch.ka = P.ka;
+    ch.target = QN(P.nel, 0);
+    ch.filt = cut_filters(P);
+    ch.WA = &c.A_mpo(h0);
+    ch.WV = &c.V_mpo();
+    std::vector<int> sites(P.k);
+    for (int s = 0; s < P.k; ++s) sites[s] = s;
+    ch.orbs = sites;
+    view_psi0(c, sites, ch.psi0);
+    return ch;
+}
+
+Chain partition_chain(Ctx& c, int h0, int a, int b, PartOps& ops) {
+    const Problem& P = c.P;
+    require(a >= 0 && b >= a && b < P.kv, "partition pair out of range (need 0 <= a <= b < k_virt)");
+    Chain ch;
+    const int ka = P.ka, N = P.nel;
+    std::vector<int> orbs;
+    for (int t = 0; t < ka; ++t) orbs.push_back(t);
+    orbs.push_back(ka + a);
+    if (b != a) orbs.push_back(ka + b);
+    const int ks = (int)orbs.size();
+    ch.nsite = ks;
+    ch.ka = ka;
+    ch.target = QN(N, 0);
+    ch.orbs = orbs;
+    ch.filt.assign(ks + 1, {});
+    if (a == b) ch.filt[ka] = {N - 1, N - 2};
+    else { ch.filt[ka] = {N - 2}; ch.filt[ka + 1] = {N - 1}; }
+    // integrals restricted to the chain's orbitals, in chain order
+    const int k = P.k;
+    std::vector<double> h((size_t)ks * ks), f((size_t)ks * ks), eps(ks), eri((size_t)ks * ks * ks * ks);
+    for (int p = 0; p < ks; ++p) {
+        eps[p] = P.eps[orbs[p]];
+        for (int q = 0; q < ks; ++q) {
+            h[(size_t)p * ks + q] = P.h[(size_t)orbs[p] * k + orbs[q]];
+            f[(size_t)p * ks + q] = P.f[(size_t)orbs[p] * k + orbs[q]];
+            for (int r = 0; r < ks; ++r)
+                for (int s2 = 0; s2 < ks; ++s2)
+                    eri[(((size_t)p * ks + q) * ks + r) * ks + s2] =
+                        P.eri[(((size_t)orbs[p] * k + orbs[q]) * k + orbs[r]) * k + orbs[s2]];
+        }
+    }
+    std::vector<Term> tA, tV;
+    if (h0 == MPSPT_H0_DYALL) {
+        add_one_body(tA, h, ks, 0, ka, 0, ka);
+        add_two_body(tA, eri, ks, 0, ka, 0, ka, -1);
+    } else {
+        add_one_body(tA, f, ks, 0, ka, 0, ka);
+    }
+    add_number(tA, eps, ka, ks);
+    tA.push_back(Term{-c.e0(h0), 0, {}});
+    add_one_body(tV, h, ks, ka, ks, 0, ka);
+    add_two_body(tV, eri, ks, 0, ks, 0, ka, ka);
+    ops.A = build_mpo(tA, ks, ka);
+    ops.V = build_mpo(tV, ks, ka);
+    ch.WA = &ops.A;
+    ch.WV = &ops.V;
+    std::vector<int> sites;
+    for (int t = 0; t < ka; ++t) sites.push_back(t);
+    for (int s = ka; s < ks; ++s) sites.push_back(ka);   // empty virtual site of the reference
+    view_psi0(c, sites, ch.psi0);
+    return ch;
+}
+
+double minimize_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int>>& pairs,
+                            const std::vector<int>& Ms, int n_lanes, std::vector<double>& e2_part,
+                            SweepResult& res) {
+    require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
+    require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
+    require(pairs.size() == Ms.size(), "one bond dimension per partition");
+    for (size_t i = 0; i < pairs.size(); ++i) {
+        require(pairs[i].first >= 0 && pairs[i].first <= pairs[i].second && pairs[i].second < c.P.kv,
+                "partition pair out of range (need 0 <= a <= b < k_virt)");
+        require(Ms[i] >= 1, "bond dimension must be >= 1");
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = launch_count();
+    const int n = (int)pairs.size();
+    e2_part.assign(n, 0.0);
+    // longest first: cost grows like M^3
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return Ms[x] > Ms[y]; });
+    n_lanes = std::max(1, std::min(n_lanes, n));
+    std::vector<std::unique_ptr<Lane>> lanes;
+    for (int l = 0; l < n_lanes; ++l) lanes.emplace_back(new Lane(nullptr, true));
+    std::atomic<int> next{0};
+    std::vector<SweepResult> rs(n);
+    std::vector<std::pair<mpspt_status, std::string>> errs(n_lanes, {MPSPT_OK, ""});
+    auto work = [&](int l) {
+        try {
+            MPSPT_CUDA(cudaSetDevice(c.opt.device));
+            for (int j; (j = next.fetch_add(1)) < n;) {
+                const int idx = order[j];
+                PartOps ops;
+                Chain ch = partition_chain(c, h0, pairs[idx].first, pairs[idx].second, ops);
+                minimize(c, ch, Ms[idx], rs[idx], lanes[l].get());
+                e2_part[idx] = rs[idx].e2;
+            }
+        } catch (const Error& e) {
+            errs[l] = {e.status, e.what()};
+            next.store(n);
+        } catch (const std::exception& e) {
+            errs[l] = {MPSPT_ERR_INVALID, e.what()};
+            next.store(n);
+        }
+    };
+    std::vector<std::thread> th;
+    for (int l = 1; l < n_lanes; ++l) th.emplace_back(work, l);
+    work(0);
+    for (auto& t : th) t.join();
+    for (auto& e : errs)
+        if (e.first != MPSPT_OK) throw Error(e.first, e.second);
+    double tot = 0.0;
+    for (int i = 0; i < n; ++i) tot += e2_part[i];   // fixed (pair) order
+    res = SweepResult();
+    res.e2 = tot;
+    for (const auto& r : rs) {
+        res.cg_iters += r.cg_iters;
+        res.sigma_calls += r.sigma_calls;
+        res.sigma_flops += r.sigma_flops;
+        res.sigma_ms += r.sigma_ms;
+        res.sigma64_calls += r.sigma64_calls;
+        res.sigma64_flops += r.sigma64_flops;
+        res.sigma64_ms += r.sigma64_ms;
+        res.max_disc = std::max(res.max_disc, r.max_disc);
+        res.max_bond = std::max(res.max_bond, r.max_bond);
+        if (r.e2_sweep.size() > res.e2_sweep.size()) res.e2_sweep.resize(r.e2_sweep.size(), 0.0);
+    }
+    res.launches = launch_count() - l0;
+    res.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    res.sweep_ms.assign(res.e2_sweep.size(), res.wall_ms);
+    return tot;
 }
 
 double expectation(Ctx& c, const MPO& W, const MpsD& bra, const MpsD& ket) {
@@ -1165,7 +1384,9 @@ void local_apply(Ctx& c, int h0, const MpsD& psi1_in, int i, int op, const doubl
     require(i >= 0 && i + 1 < c.P.k, "bond index out of range");
     MpsD& psi1 = const_cast<MpsD&>(psi1_in);
     SweepResult res;
-    Sweeper sw(c, h0, 1 << 30, psi1);
+    require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
+    Chain ch = full_chain(c, h0);
+    Sweeper sw(c, *c.lane0, ch, 1 << 30, psi1);
     sw.res = &res;
     sw.boundary_envs();
     for (int s = 0; s < i; ++s) sw.update_left(s);

@@ -36,6 +36,18 @@ struct Problem {
     std::vector<double> ci;
 };
 
+// Per-stream resources of one concurrent solve: stream, reduction scratch,
+// CG scalars and their pinned host mirrors, tensor-core error flag.
+struct Lane {
+    cudaStream_t st = 0;
+    bool own_stream = false;
+    DBuf red, cnt, cg, scal, tcerr;
+    CgState* cg_host = nullptr;
+    double* scal_host = nullptr;
+    explicit Lane(cudaStream_t s, bool create = false);
+    ~Lane();
+};
+
 struct Ctx {
     mpspt_options opt;
     cudaStream_t st = 0;
@@ -50,6 +62,7 @@ struct Ctx {
     DBuf scal;
     DBuf tcerr;                           // tensor-core kernel error flag
     std::string last_error;
+    std::unique_ptr<Lane> lane0;          // resources on the context stream
 
     explicit Ctx(const mpspt_options& o);
     ~Ctx();
@@ -77,6 +90,29 @@ struct SweepResult {
     double sigma64_flops = 0.0, sigma64_ms = 0.0;
 };
 
+// One MPS-PT problem on a chain of sites: the full space (active + all
+// virtual orbitals) or one virtual-pair partition (active + a [+ b]).
+struct Chain {
+    int nsite = 0, ka = 0;
+    QN target;
+    std::vector<std::vector<int>> filt;   // allowed N_left per cut (empty = any)
+    const MPO* WA = nullptr;              // H0 - E0 on the chain
+    const MPO* WV = nullptr;              // RHS operator on the chain
+    MpsD psi0;                            // reference on the chain (views)
+    std::vector<int> orbs;                // full-space orbital of each site
+};
+struct PartOps {
+    MPO A, V;
+};
+Chain full_chain(Ctx& c, int h0);
+Chain partition_chain(Ctx& c, int h0, int a, int b, PartOps& ops);
+
+std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res, Lane* lane = nullptr);
+// Independent virtual-pair partitions, run concurrently on n_lanes streams;
+// e2_part[i] receives E2 of pair i, the return value their sum in pair order.
+double minimize_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int>>& pairs,
+                            const std::vector<int>& Ms, int n_lanes, std::vector<double>& e2_part,
+                            SweepResult& res);
 std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res);
 double expectation(Ctx& c, const MPO& W, const MpsD& bra, const MpsD& ket);
 double third_order(Ctx& c, int h0, const MpsD& psi1);
