@@ -101,27 +101,65 @@ def _time_to_e2(rep, e2_ref, tol=1e-6):
     return rep.sweep_ms[first] / 1e3, first
 
 
-def _oracle_sample(name, h0, M, budget_s):
-    """Oracle (CPU) on the first bond steps of the first sweep; returns
-    (seconds per bond step, steps sampled, total bond steps per sweep)."""
-    from oracle.mps import HylleraasSweep
+def _oracle_sample(name, h0, M, cg_per_step, bonds_active, bonds_virtual):
+    """Bounded oracle (CPU) sample of the same workload.
+
+    The oracle's own sweep would spend minutes just building environments at
+    this size, so the sample times its kernels once each on tensors with the
+    workload's shapes (bond dimensions from the initial-state rule, the real
+    MPOs): sigma at an active-region bond and at a virtual-region bond, and
+    the once-per-step work (RHS, Jacobi diagonal, truncation, two environment
+    updates) at the virtual-region bond.  Seconds per bond step are then
+    (cg + 2) x sigma + once-per-step work; the active-region once-per-step
+    work (larger RHS) is not included, so the estimate is a lower bound."""
+    import numpy as np
+    from oracle.mps import (HylleraasSweep, env_left, random_mps, reference_mps, truncate,
+                            two_site_apply, two_site_diag, two_site_mask)
+    from oracle.mpo import build_mpo
     from oracle.operators import Problem
     h, L, c, ci = _inputs(name)
     p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
+    WA = build_mpo(p.h0_terms(), p.k, k_split=p.k_act)
+    WV = build_mpo(p.rhs_terms(), p.k, k_split=p.k_act)
+    N = p.n_elec
+    allowed = {p.k_act: {N - 1, N - 2}}
+    psi = random_mps(p.k, (N, 0), allowed, M, 1408)
+    psi0 = reference_mps(p.ci, p.k_act, p.k_virt)
+    rng = np.random.default_rng(0)
+
+    def t_sigma(i):
+        Dl, Dr = len(psi.q[i]), len(psi.q[i + 2])
+        La = rng.normal(size=(WA.dims[i], Dl, Dl))
+        Ra = rng.normal(size=(WA.dims[i + 2], Dr, Dr))
+        mask = two_site_mask(psi.q[i], psi.q[i + 2], allowed.get(i + 1))
+        x = rng.normal(size=mask.shape) * mask
+        t0 = time.perf_counter()
+        two_site_apply(La, WA.W[i], WA.W[i + 1], Ra, x, WA.dims[i + 1])
+        return time.perf_counter() - t0, (La, Ra, x, mask, Dl, Dr)
+
+    ia = max(1, p.k_act // 2)
+    iv = p.k_act + (p.k_virt // 2)
+    ts_a, _ = t_sigma(ia)
+    ts_v, (La, Ra, x, mask, Dl, Dr) = t_sigma(iv)
+    i = iv
+    D0l, D0r = len(psi0.q[i]), len(psi0.q[i + 2])
+    Lv = rng.normal(size=(WV.dims[i], Dl, D0l))
+    Rv = rng.normal(size=(WV.dims[i + 2], Dr, D0r))
+    p0 = np.einsum("lsm,mtr->lstr", psi0.A[i], psi0.A[i + 1])
     t0 = time.perf_counter()
-    sw = HylleraasSweep(p, M)
-    t_init = time.perf_counter() - t0
-    per_sweep = 2 * (p.k - 1)
-    t1 = time.perf_counter()
-    n = 0
-    order = [(i, "LR") for i in range(p.k - 1)] + [(i, "RL") for i in range(p.k - 2, -1, -1)]
-    for i, d in order:
-        sw.step(i, d)
-        n += 1
-        if time.perf_counter() - t1 > budget_s:
-            break
-    dt = time.perf_counter() - t1
-    return dt / n, n, per_sweep, t_init
+    two_site_apply(Lv, WV.W[i], WV.W[i + 1], Rv, p0, WV.dims[i + 1])
+    two_site_diag(La, WA.W[i], WA.W[i + 1], Ra, x.shape, WA.dims[i + 1])
+    Al, Ar, lab, w = truncate(x, psi.q[i], psi.q[i + 2], M, "LR", allowed.get(i + 1))
+    env_left(La, Al, WA.W[i], Al, WA.dims[i + 1])
+    env_left(Lv, Al, WV.W[i], psi0.A[i], WV.dims[i + 1])
+    t_once = time.perf_counter() - t0
+    per_a = (cg_per_step + 2) * ts_a + t_once
+    per_v = (cg_per_step + 2) * ts_v + t_once
+    sample = (f"oracle kernels timed once each on random tensors of the workload's shapes (M={M}): "
+              f"sigma {ts_a:.3f}s at active bond {ia}, {ts_v:.3f}s at virtual bond {iv}; "
+              f"once-per-step work {t_once:.3f}s at bond {iv}; x {cg_per_step:.1f} CG iterations per step "
+              f"over {bonds_active} active and {bonds_virtual} virtual bond steps (lower bound)")
+    return per_a * bonds_active + per_v * bonds_virtual, sample
 
 
 def run_reference(args):
@@ -129,19 +167,18 @@ def run_reference(args):
     if rank != 0:
         return
     cores = len(os.sched_getaffinity(0))
-    steps = []
+    c = {"medium": (8, 24)}.get(args.config, (8, 24))
+    bonds = 2 * (c[0] + c[1] - 1) * args.ref_sweeps
+    frac_a = c[0] / (c[0] + c[1] - 1)
+    vals = []
+    sample = ""
     for _ in range(args.warmup + args.steps):
-        steps.append(_oracle_sample(args.config, args.h0, args.M, args.ref_budget))
-    timed = steps[args.warmup:]
-    sec_per_bond = statistics.median(s[0] for s in timed)
-    n, per_sweep, t_init = timed[0][1], timed[0][2], timed[0][3]
-    # extrapolate to the sweeps the GPU float64 path needs (recorded in the sample note)
-    sweeps = args.ref_sweeps
-    value = t_init + sec_per_bond * per_sweep * sweeps
-    sample = (f"oracle first {n} of {per_sweep} bond steps of sweep 1 at M={args.M} ({args.h0} H0), "
-              f"median of {args.steps}; extrapolated to {sweeps} sweeps x {per_sweep} bond steps + set-up")
+        v, sample = _oracle_sample(args.config, args.h0, args.M, args.ref_cg, bonds * frac_a, bonds * (1 - frac_a))
+        vals.append(v)
+    value = statistics.median(vals[args.warmup:])
+    sample += f"; {args.ref_sweeps} sweeps assumed"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_bond * n * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"{args.config}: 8e/8o + 24 virtual, M={args.M}, {args.h0} H0",
@@ -286,13 +323,14 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        spb, n, per_sweep, t_init = _oracle_sample(args.config, args.h0, args.M, args.ref_budget)
-        sweeps = int(statistics.median(r.n_sweeps for r in reps))
-        val = t_init + spb * per_sweep * sweeps
-        line["cpu_baseline"] = {
-            "value": val, "unit": "s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": (f"oracle first {n} of {per_sweep} bond steps of sweep 1, extrapolated to the "
-                       f"{sweeps} sweeps the GPU run took, plus set-up")}
+        # the oracle needs as many bond steps as the float64 GPU run took to reach E2
+        ka, kv = c["k_act"], k - c["k_act"]
+        nb = 2 * (k - 1) * ((s64 + 1) if s64 is not None else rep64.n_sweeps)
+        cg_ps = rep64.cg_iters / max(1, 2 * (k - 1) * rep64.n_sweeps)
+        frac_a = ka / (k - 1)
+        val, sample = _oracle_sample(args.config, args.h0, args.M, cg_ps, nb * frac_a, nb * (1 - frac_a))
+        line["cpu_baseline"] = {"value": val, "unit": "s", "cores": len(os.sched_getaffinity(0)),
+                                "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
     L.mpspt_destroy(ctx)
@@ -313,8 +351,8 @@ def main():
     ap.add_argument("--e_tol", type=float, default=1e-7)
     ap.add_argument("--ref_e_tol", type=float, default=1e-9)
     ap.add_argument("--e2e_steps", type=int, default=1)
-    ap.add_argument("--ref_budget", type=float, default=15.0)
-    ap.add_argument("--ref_sweeps", type=int, default=12)
+    ap.add_argument("--ref_sweeps", type=int, default=10)
+    ap.add_argument("--ref_cg", type=float, default=6.0)
     ap.add_argument("--no_cpu_baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

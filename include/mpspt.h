@@ -93,6 +93,8 @@ typedef struct {
     double sigma64_flops;        /*   refinement and the Hylleraas value when    */
     double sigma64_ms;           /*   prec != FP64 (sigma_* then count the       */
                                  /*   inner low-precision applications)          */
+    long long learned_used;      /* local solves started from the learned guess  */
+    long long learned_rejected;  /* ... where the warm start had lower residual  */
 } mpspt_report;
 
 /* Fills *opt with defaults: device 0, default stream, FP64, 30 sweeps,
@@ -177,6 +179,59 @@ mpspt_status mpspt_mps_export(const mpspt_mps* mps, int* bond_qn, double* const*
 typedef enum { MPSPT_LOCAL_SIGMA = 0, MPSPT_LOCAL_RHS = 1, MPSPT_LOCAL_DIAG = 2 } mpspt_local_op;
 mpspt_status mpspt_local_apply(mpspt_ctx* ctx, mpspt_h0 h0, const mpspt_mps* psi1, int i,
                                mpspt_local_op op, const double* x, double* out);
+
+/* ---- Learned block preconditioner ------------------------------------
+ * A 3-layer perceptron (width `width`, bfloat16 weights with float32 master
+ * copies, float32 accumulation, ReLU) maps 16 features of each QN block of
+ * a local problem (statistics of the H0 - E0 diagonal, of g and of the warm
+ * start, the block's quantum numbers and sizes) to two coefficients
+ * (gamma_B, delta_B) of the block's initial guess
+ *     x0_B = gamma_B * x_warm,B + delta_B * (D^-1 b)_B     (b = -g).
+ * Jacobi-preconditioned CG remains the solver; in the sweep the learned
+ * guess replaces the warm start only when its float64 residual is smaller,
+ * and CG runs to the same tolerance, so E2 is unchanged.  Training pairs
+ * come from plain solves (mpspt_harvest): the least-squares (gamma, delta)
+ * of the converged solution per block.  Parameter layout: W_l row-major
+ * (out x in), b_l (out); l = 1: in = 16, l = 3: out = 2.  All arrays are
+ * host float32; the network lives on `device`. */
+typedef struct mpspt_mlp mpspt_mlp;
+mpspt_status mpspt_mlp_create(int device, int width, unsigned long long seed, mpspt_mlp** out);
+void mpspt_mlp_free(mpspt_mlp* net);
+mpspt_status mpspt_mlp_set_params(mpspt_mlp* net, const float* W1, const float* b1, const float* W2,
+                                  const float* b2, const float* W3, const float* b3);
+mpspt_status mpspt_mlp_get_params(const mpspt_mlp* net, float* W1, float* b1, float* W2, float* b2,
+                                  float* W3, float* b3);
+/* y (batch x 2) = network(x (batch x 16)). */
+mpspt_status mpspt_mlp_forward(mpspt_mlp* net, int batch, const float* x, float* y);
+/* Mean-squared-error loss 1/(2 batch) sum |y - t|^2 and its gradients with
+ * respect to the master parameters (the bfloat16 rounding passed straight
+ * through).  Any gradient pointer may be NULL. */
+mpspt_status mpspt_mlp_gradient(mpspt_mlp* net, int batch, const float* x, const float* t, float* loss,
+                                float* gW1, float* gb1, float* gW2, float* gb2, float* gW3, float* gb3);
+/* Adam (beta 0.9 / 0.999) over n samples in order, minibatches of `batch`,
+ * `epochs` passes; *loss = mean loss of the last epoch. */
+mpspt_status mpspt_mlp_train(mpspt_mlp* net, int n, const float* x, const float* t, int epochs, int batch,
+                             float lr, float* loss);
+/* Runs the plain sweep (as mpspt_minimize_hylleraas) and records up to
+ * max_samples training pairs: x (max x 16) features, t (max x 2) targets. */
+mpspt_status mpspt_harvest(mpspt_ctx* ctx, mpspt_h0 h0, int M, int max_samples, float* x, float* t,
+                           int* n_samples);
+/* Attach a network to the context; used when options.use_learned is set.
+ * The context does not own it (NULL detaches). */
+mpspt_status mpspt_set_preconditioner(mpspt_ctx* ctx, const mpspt_mlp* net);
+
+/* The float64 eigensolver of the truncation step (row "a8": density-matrix
+ * sectors rho_q = X_q X_q^T, paper text on the renormalisation step) on
+ * caller data: batched cyclic Jacobi with round-robin parallel rotations.
+ * Device pointers; the batch's matrices are stored back to back: matrix i
+ * has size n[i] (host array, 1 <= n[i] <= 2048) and starts at offset
+ * sum_{j<i} n[j]^2 of A (row-major, symmetric, not modified) and of V
+ * (eigenvectors as columns), and at sum_{j<i} n[j] of w (eigenvalues, in
+ * the column order of V, unsorted).  Work is ordered on `stream`
+ * (cudaStream_t, 0 = default); the call allocates a work copy of A with
+ * cudaMallocAsync on that stream and returns without synchronising. */
+mpspt_status mpspt_eigh_batched(int device, void* stream, int batch, const int* n, const double* A,
+                                double* V, double* w);
 
 const char* mpspt_status_string(mpspt_status s);
 

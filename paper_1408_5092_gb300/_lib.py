@@ -42,7 +42,8 @@ class mpspt_report(ctypes.Structure):
                 ("sigma_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
                 ("max_bond_dim", ctypes.c_int), ("sweep_ms", ctypes.c_double * 64),
                 ("kernel_launches", ctypes.c_longlong), ("sigma64_calls", ctypes.c_longlong),
-                ("sigma64_flops", ctypes.c_double), ("sigma64_ms", ctypes.c_double)]
+                ("sigma64_flops", ctypes.c_double), ("sigma64_ms", ctypes.c_double),
+                ("learned_used", ctypes.c_longlong), ("learned_rejected", ctypes.c_longlong)]
 
 
 class MpsptError(RuntimeError):
@@ -61,6 +62,7 @@ def load():
             raise RuntimeError(f"{LIB_PATH} is missing: run paper_1408_5092_gb300.build.build()")
         lib = ctypes.CDLL(LIB_PATH)
         vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        fp = ctypes.POINTER(ctypes.c_float)
         sig = {
             "mpspt_default_options": (None, [ctypes.POINTER(mpspt_options)]),
             "mpspt_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(mpspt_options)]),
@@ -79,6 +81,16 @@ def load():
             "mpspt_mps_export": (ctypes.c_int, [vp, ip, ctypes.POINTER(dp)]),
             "mpspt_local_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, dp, dp]),
             "mpspt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "mpspt_eigh_batched": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_int, ip, vp, vp, vp]),
+            "mpspt_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(vp)]),
+            "mpspt_mlp_free": (None, [vp]),
+            "mpspt_mlp_set_params": (ctypes.c_int, [vp] + [fp] * 6),
+            "mpspt_mlp_get_params": (ctypes.c_int, [vp] + [fp] * 6),
+            "mpspt_mlp_forward": (ctypes.c_int, [vp, ctypes.c_int, fp, fp]),
+            "mpspt_mlp_gradient": (ctypes.c_int, [vp, ctypes.c_int, fp, fp, fp] + [fp] * 6),
+            "mpspt_mlp_train": (ctypes.c_int, [vp, ctypes.c_int, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_float, fp]),
+            "mpspt_harvest": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, ip]),
+            "mpspt_set_preconditioner": (ctypes.c_int, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -217,6 +229,82 @@ def mpspt_local_apply(ctx, h0, psi1, i, op, x=None, shape=None):
         xp = _dp(xa)
     _check(load().mpspt_local_apply(ctx, H0.get(h0, h0), psi1, i, op, xp, _dp(out)))
     return out
+
+
+def mpspt_eigh_batched(device, stream, n, A_ptr, V_ptr, w_ptr):
+    """Device pointers (ints, e.g. torch tensor .data_ptr()); n: host sizes."""
+    n = np.ascontiguousarray(np.asarray(n, dtype=np.int32))
+    _check(load().mpspt_eigh_batched(device, stream, len(n), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     A_ptr, V_ptr, w_ptr))
+
+
+MLP_NF = 16
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fpp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def mpspt_mlp_create(device=0, width=256, seed=5092):
+    h = ctypes.c_void_p()
+    _check(load().mpspt_mlp_create(device, width, seed, ctypes.byref(h)))
+    return h
+
+
+def mpspt_mlp_free(net):
+    load().mpspt_mlp_free(net)
+
+
+def mpspt_mlp_set_params(net, p):
+    arrs = [_f32(p[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+    _check(load().mpspt_mlp_set_params(net, *[_fpp(a) for a in arrs]))
+
+
+def mpspt_mlp_get_params(net, width=256):
+    shapes = {"W1": (width, MLP_NF), "b1": (width,), "W2": (width, width), "b2": (width,), "W3": (2, width), "b3": (2,)}
+    out = {k: np.zeros(v, dtype=np.float32) for k, v in shapes.items()}
+    _check(load().mpspt_mlp_get_params(net, *[_fpp(out[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]))
+    return out
+
+
+def mpspt_mlp_forward(net, x):
+    x = _f32(x)
+    y = np.zeros((x.shape[0], 2), dtype=np.float32)
+    _check(load().mpspt_mlp_forward(net, x.shape[0], _fpp(x), _fpp(y)))
+    return y
+
+
+def mpspt_mlp_gradient(net, x, t, width=256):
+    x, t = _f32(x), _f32(t)
+    loss = ctypes.c_float()
+    shapes = {"W1": (width, MLP_NF), "b1": (width,), "W2": (width, width), "b2": (width,), "W3": (2, width), "b3": (2,)}
+    g = {k: np.zeros(v, dtype=np.float32) for k, v in shapes.items()}
+    _check(load().mpspt_mlp_gradient(net, x.shape[0], _fpp(x), _fpp(t), ctypes.byref(loss),
+                                     *[_fpp(g[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]))
+    return loss.value, g
+
+
+def mpspt_mlp_train(net, x, t, epochs=10, batch=256, lr=1e-3):
+    x, t = _f32(x), _f32(t)
+    loss = ctypes.c_float()
+    _check(load().mpspt_mlp_train(net, x.shape[0], _fpp(x), _fpp(t), epochs, batch, lr, ctypes.byref(loss)))
+    return loss.value
+
+
+def mpspt_harvest(ctx, h0, M, max_samples):
+    x = np.zeros((max_samples, MLP_NF), dtype=np.float32)
+    t = np.zeros((max_samples, 2), dtype=np.float32)
+    n = ctypes.c_int()
+    _check(load().mpspt_harvest(ctx, H0.get(h0, h0), M, max_samples, _fpp(x), _fpp(t), ctypes.byref(n)))
+    return x[: n.value].copy(), t[: n.value].copy()
+
+
+def mpspt_set_preconditioner(ctx, net):
+    _check(load().mpspt_set_preconditioner(ctx, net))
 
 
 def mpspt_status_string(st):

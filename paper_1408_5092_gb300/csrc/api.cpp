@@ -8,6 +8,11 @@ struct mpspt_ctx {
     std::unique_ptr<mpspt::Ctx> c;
 };
 
+struct mpspt_mlp {
+    std::unique_ptr<mpspt::Mlp> m;
+    int device = 0;
+};
+
 struct mpspt_mps {
     std::unique_ptr<mpspt::MpsD> m;
     cudaStream_t st = 0;
@@ -127,6 +132,8 @@ mpspt_status mpspt_minimize_hylleraas(mpspt_ctx* ctx, mpspt_h0 h0, int M, double
             rep->sigma64_calls = r.sigma64_calls;
             rep->sigma64_flops = r.sigma64_flops;
             rep->sigma64_ms = r.sigma64_ms;
+            rep->learned_used = r.learned_used;
+            rep->learned_rejected = r.learned_rejected;
         }
         *e2 = r.e2;
         if (psi1) {
@@ -156,6 +163,8 @@ void fill_report(mpspt_report* rep, const mpspt::SweepResult& r) {
     rep->sigma64_calls = r.sigma64_calls;
     rep->sigma64_flops = r.sigma64_flops;
     rep->sigma64_ms = r.sigma64_ms;
+    rep->learned_used = r.learned_used;
+    rep->learned_rejected = r.learned_rejected;
 }
 }  // namespace
 
@@ -268,6 +277,154 @@ mpspt_status mpspt_local_apply(mpspt_ctx* ctx, mpspt_h0 h0, const mpspt_mps* psi
         mpspt::require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
         mpspt::local_apply(c, h0, *psi1->m, i, op, x, out);
     });
+}
+
+mpspt_status mpspt_eigh_batched(int device, void* stream, int batch, const int* n, const double* A,
+                                double* V, double* w) {
+    if (batch < 1 || !n || !A || !V || !w) return MPSPT_ERR_INVALID;
+    return guard(nullptr, [&] {
+        MPSPT_CUDA(cudaSetDevice(device));
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        size_t tot = 0, totw = 0;
+        for (int i = 0; i < batch; ++i) {
+            mpspt::require(n[i] >= 1 && n[i] <= 2048, "matrix size must be in [1, 2048]");
+            tot += (size_t)n[i] * n[i];
+            totw += (size_t)n[i];
+        }
+        mpspt::DBuf work(tot * sizeof(double), st), dt;
+        MPSPT_CUDA(cudaMemcpyAsync(work.get(), A, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        std::vector<mpspt::EigTask> tasks(batch);
+        size_t o = 0, ow = 0;
+        for (int i = 0; i < batch; ++i) {
+            tasks[i] = {work.as<double>() + o, V + o, w + ow, n[i], 0};
+            o += (size_t)n[i] * n[i];
+            ow += (size_t)n[i];
+        }
+        mpspt::upload(dt, tasks, st);
+        mpspt::launch_eig(dt.as<mpspt::EigTask>(), batch, st);
+        MPSPT_CUDA(cudaGetLastError());
+    });
+}
+
+mpspt_status mpspt_mlp_create(int device, int width, unsigned long long seed, mpspt_mlp** out) {
+    if (!out || width < 1) return MPSPT_ERR_INVALID;
+    return guard(nullptr, [&] {
+        MPSPT_CUDA(cudaSetDevice(device));
+        auto* h = new mpspt_mlp;
+        h->device = device;
+        try {
+            h->m.reset(new mpspt::Mlp(mpspt::MLP_NF, width, 2, seed, 0));
+        } catch (...) {
+            delete h;
+            throw;
+        }
+        *out = h;
+    });
+}
+
+void mpspt_mlp_free(mpspt_mlp* net) {
+    if (!net) return;
+    cudaSetDevice(net->device);
+    delete net;
+}
+
+mpspt_status mpspt_mlp_set_params(mpspt_mlp* net, const float* W1, const float* b1, const float* W2,
+                                  const float* b2, const float* W3, const float* b3) {
+    if (!net || !W1 || !b1 || !W2 || !b2 || !W3 || !b3) return MPSPT_ERR_INVALID;
+    return guard(nullptr, [&] {
+        MPSPT_CUDA(cudaSetDevice(net->device));
+        const float* W[3] = {W1, W2, W3};
+        const float* b[3] = {b1, b2, b3};
+        net->m->set_params(W, b);
+    });
+}
+
+mpspt_status mpspt_mlp_get_params(const mpspt_mlp* net, float* W1, float* b1, float* W2, float* b2,
+                                  float* W3, float* b3) {
+    if (!net || !W1 || !b1 || !W2 || !b2 || !W3 || !b3) return MPSPT_ERR_INVALID;
+    return guard(nullptr, [&] {
+        MPSPT_CUDA(cudaSetDevice(net->device));
+        float* W[3] = {W1, W2, W3};
+        float* b[3] = {b1, b2, b3};
+        net->m->get_params(W, b);
+    });
+}
+
+mpspt_status mpspt_mlp_forward(mpspt_mlp* net, int batch, const float* x, float* y) {
+    if (!net || batch < 1 || !x || !y) return MPSPT_ERR_INVALID;
+    return guard(nullptr, [&] {
+        MPSPT_CUDA(cudaSetDevice(net->device));
+        auto& m = *net->m;
+        std::vector<float> xs(x, x + (size_t)batch * m.nin);
+        mpspt::DBuf X, Y((size_t)batch * m.nout * sizeof(float) + 16, m.st);
+        mpspt::upload(X, xs, m.st);
+        m.forward(batch, X.as<float>(), Y.as<float>());
+        MPSPT_CUDA(cudaMemcpyAsync(y, Y.get(), (size_t)batch * m.nout * sizeof(float), cudaMemcpyDeviceToHost, m.st));
+        MPSPT_CUDA(cudaStreamSynchronize(m.st));
+    });
+}
+
+mpspt_status mpspt_mlp_gradient(mpspt_mlp* net, int batch, const float* x, const float* t, float* loss,
+                                float* gW1, float* gb1, float* gW2, float* gb2, float* gW3, float* gb3) {
+    if (!net || batch < 1 || !x || !t) return MPSPT_ERR_INVALID;
+    return guard(nullptr, [&] {
+        MPSPT_CUDA(cudaSetDevice(net->device));
+        auto& m = *net->m;
+        std::vector<float> xs(x, x + (size_t)batch * m.nin), ts(t, t + (size_t)batch * m.nout);
+        mpspt::DBuf X, T;
+        mpspt::upload(X, xs, m.st);
+        mpspt::upload(T, ts, m.st);
+        const float l = m.gradient(batch, X.as<float>(), T.as<float>());
+        if (loss) *loss = l;
+        float* gw[3] = {gW1, gW2, gW3};
+        float* gb[3] = {gb1, gb2, gb3};
+        for (int q = 0; q < 3; ++q) {
+            if (gw[q]) MPSPT_CUDA(cudaMemcpyAsync(gw[q], m.gW[q].get(), m.wn(q) * sizeof(float), cudaMemcpyDeviceToHost, m.st));
+            if (gb[q]) MPSPT_CUDA(cudaMemcpyAsync(gb[q], m.gb[q].get(), m.out_of(q) * sizeof(float), cudaMemcpyDeviceToHost, m.st));
+        }
+        MPSPT_CUDA(cudaStreamSynchronize(m.st));
+    });
+}
+
+mpspt_status mpspt_mlp_train(mpspt_mlp* net, int n, const float* x, const float* t, int epochs, int batch,
+                             float lr, float* loss) {
+    if (!net || n < 1 || !x || !t || epochs < 1 || batch < 1 || !(lr > 0)) return MPSPT_ERR_INVALID;
+    return guard(nullptr, [&] {
+        MPSPT_CUDA(cudaSetDevice(net->device));
+        const float l = net->m->train(n, x, t, epochs, batch, lr);
+        if (loss) *loss = l;
+    });
+}
+
+mpspt_status mpspt_harvest(mpspt_ctx* ctx, mpspt_h0 h0, int M, int max_samples, float* x, float* t,
+                           int* n_samples) {
+    if (!ctx || max_samples < 1 || !x || !t || !n_samples) return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] {
+        auto& c = *ctx->c;
+        MPSPT_CUDA(cudaSetDevice(c.opt.device));
+        c.harvesting = true;
+        c.harvest_max = (size_t)max_samples;
+        c.harvest_x.clear();
+        c.harvest_t.clear();
+        mpspt::SweepResult r;
+        try {
+            mpspt::minimize(c, h0, M, r);
+        } catch (...) {
+            c.harvesting = false;
+            throw;
+        }
+        c.harvesting = false;
+        const int ns = (int)(c.harvest_x.size() / mpspt::MLP_NF);
+        std::copy(c.harvest_x.begin(), c.harvest_x.end(), x);
+        std::copy(c.harvest_t.begin(), c.harvest_t.end(), t);
+        *n_samples = ns;
+    });
+}
+
+mpspt_status mpspt_set_preconditioner(mpspt_ctx* ctx, const mpspt_mlp* net) {
+    if (!ctx) return MPSPT_ERR_INVALID;
+    ctx->c->net = net ? net->m.get() : nullptr;
+    return MPSPT_OK;
 }
 
 const char* mpspt_status_string(mpspt_status s) {

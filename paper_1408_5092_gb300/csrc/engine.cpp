@@ -533,13 +533,13 @@ std::vector<Bond> initial_bonds(int nsite, QN target, const std::vector<std::vec
 namespace {
 
 struct Work {
-    DBuf x, g, b, r, z, p, Ap, minv, x0, d, ri, zero;
+    DBuf x, g, b, r, z, p, Ap, minv, x0, d, ri, zero, xw, dg;
     size_t nzero = 0;
     void ensure(size_t n, size_t n0, cudaStream_t st) {
         const size_t by = (n + 1) * sizeof(double);
         x.ensure(by, st); g.ensure(by, st); b.ensure(by, st); r.ensure(by, st); z.ensure(by, st);
         p.ensure(by, st); Ap.ensure(by, st); minv.ensure(by, st);
-        d.ensure(by, st); ri.ensure(by, st);
+        d.ensure(by, st); ri.ensure(by, st); xw.ensure(by, st); dg.ensure(by, st);
         if (zero.bytes() < by || nzero < n) {
             zero.ensure(by, st);
             MPSPT_CUDA(cudaMemsetAsync(zero.get(), 0, zero.bytes(), st));
@@ -1051,6 +1051,92 @@ struct Sweeper {
         return hylleraas(n);   // w.Ap holds the float64 A x of the final x
     }
 
+    // ---- learned preconditioner -------------------------------------------
+    DBuf dblocks, dmeta, dfeat, dcoef, dfit;
+    std::vector<BlockRef> hblocks;
+    std::vector<float> hmeta;
+
+    // block list + QN metadata and the feature vectors of the current step
+    void block_prepare(int i) {
+        const Bond &bL = psi.bond[i], &bR = psi.bond[i + 2];
+        hblocks.clear();
+        hmeta.clear();
+        const int N = ch.target.n;
+        for (const auto& b : X.blk) {
+            hblocks.push_back({b.off, b.rows * b.cols, 0});
+            const QN ql = bL.sec[b.sl].q, qr = bR.sec[b.sr].q;
+            const float m[8] = {(float)(ql.n - N) / 4.f, (float)ql.sz / 4.f, (float)(qr.n - N) / 4.f,
+                                (float)qr.sz / 4.f, (float)b.s1 / 3.f, (float)b.s2 / 3.f,
+                                (float)std::log2((double)b.rows) / 8.f, (float)std::log2((double)b.cols) / 8.f};
+            hmeta.insert(hmeta.end(), m, m + 8);
+        }
+        upload(dblocks, hblocks, ln.st);
+        upload(dmeta, hmeta, ln.st);
+        dfeat.ensure(hblocks.size() * MLP_NF * sizeof(float) + 16, ln.st);
+        block_features(dblocks.as<BlockRef>(), (int)hblocks.size(), w.dg.as<double>(), w.g.as<double>(),
+                       w.x.as<double>(), dmeta.as<float>(), dfeat.as<float>(), ln.st);
+    }
+
+    // residual norm^2 of b - A v (float64 sigma)
+    double resid2(const double* v, size_t n) {
+        MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), v, n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
+        sigma64();
+        MPSPT_CUDA(cudaMemcpyAsync(w.r.get(), w.b.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
+        vec_axpy(w.r.as<double>(), w.Ap.as<double>(), -1.0, n, ln.st);
+        dot(w.r.as<double>(), w.r.as<double>(), n, 4);
+        MPSPT_CUDA(cudaMemcpyAsync(ln.scal_host, ln.scal.get(), 5 * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
+        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        add_time();
+        return ln.scal_host[4];
+    }
+
+    // x <- learned initial guess if its float64 residual beats the warm start
+    void learned_guess(size_t n) {
+        Mlp& net = *const_cast<Mlp*>(c.net);
+        const int nb = (int)hblocks.size();
+        dcoef.ensure((size_t)nb * 2 * sizeof(float) + 16, ln.st);
+        net.forward(nb, dfeat.as<float>(), dcoef.as<float>());
+        block_combine(dblocks.as<BlockRef>(), nb, dcoef.as<float>(), w.x.as<double>(), w.minv.as<double>(),
+                      w.b.as<double>(), w.d.as<double>(), ln.st);
+        const double r_warm = resid2(w.x.as<double>(), n);
+        const double r_learn = resid2(w.d.as<double>(), n);
+        if (r_learn < r_warm) {
+            MPSPT_CUDA(cudaMemcpyAsync(w.x.get(), w.d.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
+            res->learned_used++;
+        } else {
+            res->learned_rejected++;
+        }
+    }
+
+    // training pair per block: features -> least-squares (gamma, delta) of x*
+    void harvest(size_t) {
+        const int nb = (int)hblocks.size();
+        dfit.ensure((size_t)nb * 5 * sizeof(double) + 16, ln.st);
+        block_fit(dblocks.as<BlockRef>(), nb, w.xw.as<double>(), w.minv.as<double>(), w.b.as<double>(),
+                  w.x.as<double>(), dfit.as<double>(), ln.st);
+        std::vector<double> fit((size_t)nb * 5);
+        std::vector<float> feat((size_t)nb * MLP_NF);
+        MPSPT_CUDA(cudaMemcpyAsync(fit.data(), dfit.get(), fit.size() * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
+        MPSPT_CUDA(cudaMemcpyAsync(feat.data(), dfeat.get(), feat.size() * sizeof(float), cudaMemcpyDeviceToHost, ln.st));
+        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        for (int q = 0; q < nb; ++q) {
+            if (c.harvest_x.size() / MLP_NF >= c.harvest_max) return;
+            const double* f = &fit[(size_t)q * 5];
+            const double a = f[0], b_ = f[1], cc = f[2], d = f[3], e = f[4];
+            const double det = a * cc - b_ * b_;
+            double ga, de;
+            if (cc <= 0.0) continue;
+            if (a > 0.0 && det > 1e-10 * a * cc) { ga = (d * cc - e * b_) / det; de = (a * e - b_ * d) / det; }
+            else { ga = 0.0; de = e / cc; }
+            if (!std::isfinite(ga) || !std::isfinite(de)) continue;
+            ga = std::max(-4.0, std::min(4.0, ga));
+            de = std::max(-4.0, std::min(4.0, de));
+            c.harvest_x.insert(c.harvest_x.end(), &feat[(size_t)q * MLP_NF], &feat[(size_t)q * MLP_NF] + MLP_NF);
+            c.harvest_t.push_back((float)ga);
+            c.harvest_t.push_back((float)de);
+        }
+    }
+
     // one bond step; returns h_loc
     // host-side phase timers (printed with verbose >= 2)
     double t_plan = 0, t_rhs = 0, t_solve = 0, t_split = 0, t_env = 0;
@@ -1078,16 +1164,22 @@ struct Sweeper {
         if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_rhs += since(t0); t0 = clk::now(); }
         sig.build(omA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
                   w.Ap.as<double>(), ln.st);
-        dia.build(omA, X, bL, bR, LA[i], RA[i + 2], WA.dq[i], WA.dq[i + 2], w.minv.as<double>(), ln.st);
+        dia.build(omA, X, bL, bR, LA[i], RA[i + 2], WA.dq[i], WA.dq[i + 2], w.dg.as<double>(), ln.st);
         dia.run(ln.st);
-        make_minv(w.minv.as<double>(), w.minv.as<double>(), n, ln.st);
+        make_minv(w.minv.as<double>(), w.dg.as<double>(), n, ln.st);
         vec_scale_mask(w.b.as<double>(), w.g.as<double>(), -1.0, n, ln.st);
+        const bool learn = (c.net != nullptr && c.opt.use_learned) || c.harvesting;
+        if (learn) block_prepare(i);
+        if (c.harvesting)
+            MPSPT_CUDA(cudaMemcpyAsync(w.xw.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
         if (lo_kind != GEMM_F64)
             sig_lo.build(omA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
                          w.Ap.as<double>(), ln.st);
         if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_plan += since(t0); t0 = clk::now(); }
+        if (c.net != nullptr && c.opt.use_learned && !c.harvesting) learned_guess(n);
         const double h = (lo_kind == GEMM_F64) ? solve_plain(n) : solve_refined(n);
         check_tc();
+        if (c.harvesting) harvest(n);
         if (c.opt.verbose >= 2) { t_solve += since(t0); t0 = clk::now(); }
         const double disc = split(i, dir, M, X, x);
         res->max_disc = std::max(res->max_disc, disc);

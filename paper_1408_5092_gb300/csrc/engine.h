@@ -7,6 +7,7 @@
 
 #include "core.h"
 #include "kernels.h"
+#include "learned.h"
 #include "mpo.h"
 #include "plans.h"
 #include "tensors.h"
@@ -63,6 +64,12 @@ struct Ctx {
     DBuf tcerr;                           // tensor-core kernel error flag
     std::string last_error;
     std::unique_ptr<Lane> lane0;          // resources on the context stream
+    const Mlp* net = nullptr;             // learned initial guess (opt.use_learned)
+    // harvesting of training pairs from plain solves (block features -> the
+    // least-squares (gamma, delta) of the converged solution)
+    bool harvesting = false;
+    size_t harvest_max = 0;
+    std::vector<float> harvest_x, harvest_t;
 
     explicit Ctx(const mpspt_options& o);
     ~Ctx();
@@ -86,6 +93,7 @@ struct SweepResult {
     int max_bond = 0;
     std::vector<double> sweep_ms;
     long long launches = 0;
+    long long learned_used = 0, learned_rejected = 0;
     long long sigma64_calls = 0;
     double sigma64_flops = 0.0, sigma64_ms = 0.0;
 };

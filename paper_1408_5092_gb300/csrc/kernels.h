@@ -136,4 +136,26 @@ void cg_step(double* x, double* r, double* z, double* p, const double* Ap, const
              size_t n, CgState* S, double* scratch, unsigned* counter, cudaStream_t st);
 void make_minv(double* minv, const double* diag, size_t n, cudaStream_t st);
 
+// ---- learned preconditioner (kernels_mlp.cu)
+struct BlockRef {      // one QN block of a two-site vector
+    size_t off;
+    int len;
+    int pad;
+};
+constexpr int MLP_NF = 16;   // features per block
+void mlp_gemm(int M, int N, int K, const float* A, int lda, bool ta, const float* B, int ldb, bool tb,
+              float* C, int ldc, const float* bias, const float* mask, int epi, cudaStream_t st);
+void mlp_gemm_bf16w(int M, int N, int K, const float* A, int lda, bool ta, const void* B, int ldb, bool tb,
+                    float* C, int ldc, const float* bias, const float* mask, int epi, cudaStream_t st);
+void mlp_colsum(int M, int N, const float* A, float* out, cudaStream_t st);
+void mlp_mse(int B, int N, const float* Y, const float* T, float* dY, float* rowloss, cudaStream_t st);
+void mlp_adam(int n, float* w, const float* g, float* m, float* v, void* wb, float lr, int step, cudaStream_t st);
+void mlp_to_bf16(int n, const float* w, void* wb, cudaStream_t st);
+void block_features(const BlockRef* blocks, int nb, const double* diag, const double* g, const double* xw,
+                    const float* meta, float* feats, cudaStream_t st);
+void block_combine(const BlockRef* blocks, int nb, const float* coef, const double* xw, const double* minv,
+                   const double* bvec, double* x0, cudaStream_t st);
+void block_fit(const BlockRef* blocks, int nb, const double* xw, const double* minv, const double* bvec,
+               const double* x, double* out, cudaStream_t st);
+
 }  // namespace mpspt
