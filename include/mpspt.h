@@ -233,6 +233,24 @@ mpspt_status mpspt_set_preconditioner(mpspt_ctx* ctx, const mpspt_mlp* net);
 mpspt_status mpspt_eigh_batched(int device, void* stream, int batch, const int* n, const double* A,
                                 double* V, double* w);
 
+/* Allocation-free variant of mpspt_eigh_batched (the paper has no
+ * counterpart; this is a service for callers that cannot allocate device
+ * memory during the call -- e.g. code running while a CUDA graph is being
+ * captured, hosts that reserve all device memory up front, or callers whose
+ * own memory pool must not be bypassed).  Same arguments, results and
+ * stream ordering as mpspt_eigh_batched, but the task table and the work
+ * copy of A live in one fixed device array of 2^21 doubles (16 MiB) that
+ * every GPU loading the library holds until the process exits; the call
+ * allocates and frees nothing.  Limits: batch <= 1024 and
+ * sum_i n[i]^2 <= 2^21 - 4096 (else MPSPT_ERR_INVALID, nothing launched).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any
+ * stream capture.  All calls share the array and each overwrites what it
+ * uses: calls whose GPU work overlaps (other streams, other host threads)
+ * race on it and must be serialised by the caller. */
+mpspt_status mpspt_eigh_batched_noalloc(int device, void* stream, int batch, const int* n,
+                                        const double* A, double* V, double* w);
+
 const char* mpspt_status_string(mpspt_status s);
 
 #ifdef __cplusplus

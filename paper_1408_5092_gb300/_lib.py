@@ -82,6 +82,7 @@ def load():
             "mpspt_local_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, dp, dp]),
             "mpspt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "mpspt_eigh_batched": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_int, ip, vp, vp, vp]),
+            "mpspt_eigh_batched_noalloc": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_int, ip, vp, vp, vp]),
             "mpspt_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(vp)]),
             "mpspt_mlp_free": (None, [vp]),
             "mpspt_mlp_set_params": (ctypes.c_int, [vp] + [fp] * 6),
@@ -236,6 +237,13 @@ def mpspt_eigh_batched(device, stream, n, A_ptr, V_ptr, w_ptr):
     n = np.ascontiguousarray(np.asarray(n, dtype=np.int32))
     _check(load().mpspt_eigh_batched(device, stream, len(n), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                      A_ptr, V_ptr, w_ptr))
+
+
+def mpspt_eigh_batched_noalloc(device, stream, n, A_ptr, V_ptr, w_ptr):
+    """As mpspt_eigh_batched, with no device allocation (fixed 16 MiB scratch)."""
+    n = np.ascontiguousarray(np.asarray(n, dtype=np.int32))
+    _check(load().mpspt_eigh_batched_noalloc(device, stream, len(n), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                             A_ptr, V_ptr, w_ptr))
 
 
 MLP_NF = 16
