@@ -274,8 +274,8 @@ def run_gpu(args):
         tt, _ = _time_to_e2(rep, e2_ref)
         e2e_times.append(t_setup + (tt if tt is not None else rep.wall_ms / 1e3))
         L.mpspt_destroy(ctx2)
-    e2e = statistics.median(e2e_times)
-    if dist:
+    e2e = statistics.median(e2e_times) if e2e_times else None
+    if dist and e2e is not None:
         t = torch.tensor([e2e], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e = float(t[0])

@@ -75,6 +75,11 @@ typedef struct {
     unsigned long long seed;    /* initial Psi1 (counter-based, see below)      */
     int use_learned;            /* learned block preconditioner (0 = Jacobi)    */
     int verbose;                /* 1: one line per sweep on stderr              */
+    int eig_fp64_only;          /* density-matrix eigensolver: 0 (default) =    */
+                                /* float32 Jacobi start, float64 Newton-Schulz  */
+                                /* re-orthonormalisation and float64 Jacobi     */
+                                /* polish; 1 = float64 Jacobi from identity     */
+                                /* (see mpspt_eigh_batched_ex)                  */
 } mpspt_options;
 
 typedef struct {
@@ -232,6 +237,19 @@ mpspt_status mpspt_set_preconditioner(mpspt_ctx* ctx, const mpspt_mlp* net);
  * cudaMallocAsync on that stream and returns without synchronising. */
 mpspt_status mpspt_eigh_batched(int device, void* stream, int batch, const int* n, const double* A,
                                 double* V, double* w);
+
+/* Same contract as mpspt_eigh_batched, with the solver the truncation step
+ * uses: Jacobi with one launch per sweep (the matrix as a packed triangle in
+ * shared memory, the recorded rotations applied to the rows of V by many
+ * CTAs in parallel).  f32_start = 0: float64 sweeps from the identity.
+ * f32_start = 1: float32 sweeps from the identity, two float64
+ * Newton-Schulz steps that restore orthonormality (V <- V (3/2 I -
+ * 1/2 V^T V)), then float64 sweeps on V^T A V starting from V, to the same
+ * float64 convergence test.  A is left unchanged.  Allocates device scratch
+ * (about 4 n^2 doubles per matrix) and returns after the stream has
+ * finished the work. */
+mpspt_status mpspt_eigh_batched_ex(int device, void* stream, int batch, const int* n, const double* A,
+                                   double* V, double* w, int f32_start);
 
 /* Allocation-free variant of mpspt_eigh_batched (the paper has no
  * counterpart; this is a service for callers that cannot allocate device

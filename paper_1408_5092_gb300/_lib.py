@@ -32,7 +32,8 @@ class mpspt_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("prec", ctypes.c_int),
                 ("max_sweeps", ctypes.c_int), ("e_tol", ctypes.c_double), ("cg_tol", ctypes.c_double),
                 ("cg_max_iter", ctypes.c_int), ("seed", ctypes.c_ulonglong),
-                ("use_learned", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("use_learned", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("eig_fp64_only", ctypes.c_int)]
 
 
 class mpspt_report(ctypes.Structure):
@@ -83,6 +84,7 @@ def load():
             "mpspt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "mpspt_eigh_batched": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_int, ip, vp, vp, vp]),
             "mpspt_eigh_batched_noalloc": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_int, ip, vp, vp, vp]),
+            "mpspt_eigh_batched_ex": (ctypes.c_int, [ctypes.c_int, vp, ctypes.c_int, ip, vp, vp, vp, ctypes.c_int]),
             "mpspt_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(vp)]),
             "mpspt_mlp_free": (None, [vp]),
             "mpspt_mlp_set_params": (ctypes.c_int, [vp] + [fp] * 6),
@@ -237,6 +239,13 @@ def mpspt_eigh_batched(device, stream, n, A_ptr, V_ptr, w_ptr):
     n = np.ascontiguousarray(np.asarray(n, dtype=np.int32))
     _check(load().mpspt_eigh_batched(device, stream, len(n), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                      A_ptr, V_ptr, w_ptr))
+
+
+def mpspt_eigh_batched_ex(device, stream, n, A_ptr, V_ptr, w_ptr, f32_start=1):
+    """As mpspt_eigh_batched, with the truncation step's sweep-per-launch solver."""
+    n = np.ascontiguousarray(np.asarray(n, dtype=np.int32))
+    _check(load().mpspt_eigh_batched_ex(device, stream, len(n), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                        A_ptr, V_ptr, w_ptr, int(f32_start)))
 
 
 def mpspt_eigh_batched_noalloc(device, stream, n, A_ptr, V_ptr, w_ptr):

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpspt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "kernels_tc.cu", "kernels_mlp.cu", "mpo.cpp", "plans.cpp", "engine.cpp", "learned.cpp", "api.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "kernels_tc.cu", "kernels_mlp.cu", "kernels_eig.cu", "mpo.cpp", "plans.cpp", "engine.cpp", "learned.cpp", "eig.cpp", "api.cpp", "noalloc.cu"]
 
 
 def _nvcc():

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "eig.h"
 #include "engine.h"
 
 struct mpspt_ctx {
@@ -58,6 +59,7 @@ void mpspt_default_options(mpspt_options* o) {
     o->seed = 1408;
     o->use_learned = 0;
     o->verbose = 0;
+    o->eig_fp64_only = 0;
 }
 
 mpspt_status mpspt_create(mpspt_ctx** ctx, const mpspt_options* opt) {
@@ -302,6 +304,36 @@ mpspt_status mpspt_eigh_batched(int device, void* stream, int batch, const int* 
         }
         mpspt::upload(dt, tasks, st);
         mpspt::launch_eig(dt.as<mpspt::EigTask>(), batch, st);
+        MPSPT_CUDA(cudaGetLastError());
+    });
+}
+
+mpspt_status mpspt_eigh_batched_ex(int device, void* stream, int batch, const int* n, const double* A,
+                                   double* V, double* w, int f32_start) {
+    if (batch < 1 || !n || !A || !V || !w) return MPSPT_ERR_INVALID;
+    return guard(nullptr, [&] {
+        MPSPT_CUDA(cudaSetDevice(device));
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        size_t tot = 0, totw = 0;
+        for (int i = 0; i < batch; ++i) {
+            mpspt::require(n[i] >= 1 && n[i] <= 2048, "matrix size must be in [1, 2048]");
+            tot += (size_t)n[i] * n[i];
+            totw += (size_t)n[i];
+        }
+        mpspt::DBuf wa(tot * sizeof(double), st), wv(tot * sizeof(double), st), ww(totw * sizeof(double), st);
+        MPSPT_CUDA(cudaMemcpyAsync(wa.get(), A, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        std::vector<mpspt::EigTask> tasks(batch);
+        size_t o = 0, ow = 0;
+        for (int i = 0; i < batch; ++i) {
+            tasks[i] = {wa.as<double>() + o, wv.as<double>() + o, ww.as<double>() + ow, n[i], 0};
+            o += (size_t)n[i] * n[i];
+            ow += (size_t)n[i];
+        }
+        mpspt::EigSolver es;
+        es.run(tasks, f32_start == 0, st);
+        MPSPT_CUDA(cudaMemcpyAsync(V, wv.get(), tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        MPSPT_CUDA(cudaMemcpyAsync(w, ww.get(), totw * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        MPSPT_CUDA(cudaStreamSynchronize(st));   // the solver's scratch is released on return
         MPSPT_CUDA(cudaGetLastError());
     });
 }

@@ -1,0 +1,110 @@
+#include "eig.h"
+
+#include <algorithm>
+
+namespace mpspt {
+
+namespace {
+constexpr int kMaxSweepsF64 = 40;      // float64 Jacobi from the identity
+constexpr int kMaxSweepsF32 = 12;      // float32 start
+constexpr int kMaxSweepsPolish = 16;   // float64 polish of V^T A V
+size_t a16(size_t b) { return (b + 15) & ~(size_t)15; }
+}  // namespace
+
+void EigSolver::jacobi(const std::vector<EigTask>& et, const std::vector<const double*>& in, int vinit, bool f32,
+                       int maxs, bool want_w, cudaStream_t st) {
+    const int nt = (int)et.size();
+    std::vector<size_t> off(nt);
+    size_t tot = 0;
+    for (int i = 0; i < nt; ++i) {
+        off[i] = tot;
+        tot += a16(jac_p_bytes(et[i].n)) + a16(jac_rot_bytes(et[i].n)) + 16;
+    }
+    scratch.ensure(tot + 16, st);
+    unsigned char* base = static_cast<unsigned char*>(scratch.get());
+    std::vector<JacTask> jt(nt);
+    std::vector<JacRows> rows;
+    int smem = 0;
+    for (int i = 0; i < nt; ++i) {
+        const int n = et[i].n;
+        unsigned char* P = base + off[i];
+        unsigned char* R = P + a16(jac_p_bytes(n));
+        unsigned char* S = R + a16(jac_rot_bytes(n));
+        check_range(in[i], (size_t)n * n * sizeof(double), "jacobi A");
+        check_range(P, jac_p_bytes(n), "jacobi P");
+        check_range(R, jac_rot_bytes(n), "jacobi rot");
+        check_range(S, 16, "jacobi state");
+        jt[i] = {in[i], P, R, et[i].V, want_w ? et[i].w : nullptr, reinterpret_cast<double*>(S),
+                 reinterpret_cast<int*>(S + 8), n, vinit};
+        const int rpb = jac_rows_per_block(n, f32);
+        for (int r0 = 0; r0 < n; r0 += rpb) {
+            const int nr = std::min(rpb, n - r0);
+            rows.push_back({i, r0, nr, 0});
+            smem = std::max(smem, nr * (n | 1) * (f32 ? 4 : 8));
+        }
+    }
+    upload(djt, jt, st);
+    upload(drows, rows, st);
+    for (int s = 0; s <= maxs; ++s) {
+        launch_jac_sweep(djt.as<JacTask>(), nt, s, maxs, f32, st);
+        if (s < maxs) launch_jac_apply(djt.as<JacTask>(), drows.as<JacRows>(), (int)rows.size(), smem, s, f32, st);
+    }
+}
+
+void EigSolver::run(const std::vector<EigTask>& et, bool fp64_only, cudaStream_t st) {
+    if (et.empty()) return;
+    std::vector<const double*> in;
+    for (const auto& t : et) {
+        require(t.n >= 1 && t.n <= 2048, "eigenproblem size must be in [1, 2048]");
+        check_range(t.V, (size_t)t.n * t.n * sizeof(double), "eig V");
+        check_range(t.w, (size_t)t.n * sizeof(double), "eig w");
+        in.push_back(t.A);
+    }
+    if (fp64_only) {
+        jacobi(et, in, 0, false, kMaxSweepsF64, true, st);
+        return;
+    }
+    jacobi(et, in, 0, true, kMaxSweepsF32, false, st);
+    size_t tot = 0;
+    std::vector<size_t> off;
+    for (const auto& t : et) { off.push_back(tot); tot += (size_t)t.n * t.n; }
+    vt.ensure((tot + 1) * sizeof(double), st);
+    g.ensure((tot + 1) * sizeof(double), st);
+    std::vector<EigTask> ns;
+    for (size_t i = 0; i < et.size(); ++i) ns.push_back({g.as<double>() + off[i], nullptr, nullptr, et[i].n, 0});
+    upload(dtns, ns, st);
+    // C_i = op(A_i) B_i for every task (n x n, leading dimension n)
+    enum Src { TA, TV, TVT, TG };
+    auto ptr = [&](Src s, size_t i) -> double* {
+        switch (s) {
+            case TA: return const_cast<double*>(et[i].A);
+            case TV: return et[i].V;
+            case TVT: return vt.as<double>() + off[i];
+            default: return g.as<double>() + off[i];
+        }
+    };
+    auto batched = [&](Src a, int trans, Src b, Src c) {
+        ge.clear();
+        for (size_t i = 0; i < et.size(); ++i) {
+            const int n = et[i].n;
+            const int m0 = ge.mark();
+            ge.op(ptr(a, i), n, ptr(b, i), n, n, trans, 1.0);
+            ge.block(ptr(c, i), n, n, n, 0, m0);
+        }
+        ge.upload(st);
+        ge.run(st);
+    };
+    batched(TV, 1, TV, TG);        // G = V^T V
+    launch_ns_prep(dtns.as<EigTask>(), (int)ns.size(), st);
+    batched(TV, 0, TG, TVT);       // Vt = V (3/2 I - 1/2 G)
+    batched(TVT, 1, TVT, TG);
+    launch_ns_prep(dtns.as<EigTask>(), (int)ns.size(), st);
+    batched(TVT, 0, TG, TV);       // V = Vt (3/2 I - 1/2 Vt^T Vt)
+    batched(TA, 0, TV, TVT);       // Vt = A V
+    batched(TV, 1, TVT, TG);       // G = B = V^T A V
+    std::vector<const double*> bin;
+    for (size_t i = 0; i < et.size(); ++i) bin.push_back(g.as<double>() + off[i]);
+    jacobi(et, bin, 1, false, kMaxSweepsPolish, true, st);
+}
+
+}  // namespace mpspt

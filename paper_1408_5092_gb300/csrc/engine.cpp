@@ -1,5 +1,6 @@
 // MPS-PT engine (host orchestration; device kernels do the contractions).
 #include "engine.h"
+#include "eig.h"
 
 #include <algorithm>
 #include <atomic>
@@ -600,6 +601,7 @@ struct Sweeper {
     GemmPlan prod, prod0, gr, gc;
     EnvPlan envp;
     DBuf rho, V, wv, ctasks, cols, etasks;
+    EigSolver eig;
     SweepResult* res = nullptr;
     cudaEvent_t ev0, ev1;
 
@@ -735,14 +737,7 @@ struct Sweeper {
             woff.push_back(wo);
             wo += cp.dim;
         }
-        for (const auto& t : et) {
-            require(t.n <= 2048, "density-matrix sector larger than 2048");
-            check_range(t.A, (size_t)t.n * t.n * sizeof(double), "eig A");
-            check_range(t.V, (size_t)t.n * t.n * sizeof(double), "eig V");
-            check_range(t.w, (size_t)t.n * sizeof(double), "eig w");
-        }
-        upload(etasks, et, ln.st);
-        launch_eig(etasks.as<EigTask>(), (int)et.size(), ln.st);
+        eig.run(et, c.opt.eig_fp64_only != 0, ln.st);
         if (c.opt.verbose >= 3) {
             MPSPT_CUDA(cudaEventRecord(sev[2], ln.st));
             double n3 = 0; int nmax = 0;

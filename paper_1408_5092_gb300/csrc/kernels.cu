@@ -145,41 +145,72 @@ __global__ void k_copy(const CopyTask* __restrict__ tasks) {
 // of the m-1 rounds of a sweep the m/2 disjoint pairs (p_k, q_k) get their
 // rotation R_k; the whole matrix is then updated in one pass, block by
 // block: the 2x2 block of pairs (k, l) becomes R_k^T A_kl R_l (blocks are
-// independent, so the update is in place), and V's columns of pair l are
-// rotated by R_l.  Matrices live in shared memory when they fit, else in
-// global memory (L2-resident).  A pair is skipped when its off-diagonal
-// element is negligible against its diagonal (threshold Jacobi).
+// independent, so the update is in place), and the eigenvector columns of
+// pair l are rotated by R_l.  Inside the kernel the eigenvectors are held
+// transposed (row j = eigenvector j), so that a column rotation touches two
+// contiguous rows.  A is kept in shared memory whenever it fits, V too when
+// both fit; the rest stays in global memory (L2-resident).  A pair is
+// skipped when its off-diagonal element is negligible against its diagonal
+// (threshold Jacobi).  With vinit the kernel starts from the caller's
+// orthonormal basis V and accumulates the rotations into it (A is then
+// taken to be V0^T A_orig V0 already).
 constexpr int EIG_MAXN = 2048;
-constexpr int EIG_SMEM_N = 112;   // 2 * 112^2 doubles = 200 KB
+constexpr int EIG_SMEM_BYTES = 200704;   // dynamic shared memory per CTA
 
 __device__ __forceinline__ void rr_pair(int k, int r, int m, int& pa, int& pb) {
     pa = (k == 0) ? 0 : ((k - 1 + r) % (m - 1)) + 1;
     pb = ((m - 1 - k - 1 + r) % (m - 1)) + 1;
 }
 
-__global__ void __launch_bounds__(512) k_eig(const EigTask* __restrict__ tasks) {
-    extern __shared__ double esm[];
-    const EigTask t = tasks[blockIdx.x];
+// In-place transpose of an n x n matrix in global memory (one CTA).
+template <class T>
+__device__ void transpose_inplace(T* M, int n) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        if (i < j) {
+            const T x = M[(size_t)i * n + j];
+            M[(size_t)i * n + j] = M[(size_t)j * n + i];
+            M[(size_t)j * n + i] = x;
+        }
+    }
+}
+
+template <class T, class Task>
+__global__ void __launch_bounds__(512) k_eig(const Task* __restrict__ tasks) {
+    extern __shared__ __align__(16) unsigned char esm_raw[];
+    T* esm = reinterpret_cast<T*>(esm_raw);
+    const Task t = tasks[blockIdx.x];
     const int n = t.n;
-    const bool in_smem = n <= EIG_SMEM_N;
-    double* A = in_smem ? esm : t.A;
-    double* V = in_smem ? esm + n * n : t.V;
+    constexpr T STOP = sizeof(T) == 8 ? T(1e-30) : T(1e-11);     // off^2 <= STOP * all^2
+    constexpr T SKIP = sizeof(T) == 8 ? T(1e-18) : T(1e-9);      // negligible a_pq
+    constexpr int MAXSWEEP = sizeof(T) == 8 ? 40 : 12;
+    const size_t nn = (size_t)n * n;
+    const bool a_sm = nn * sizeof(T) <= (size_t)EIG_SMEM_BYTES;
+    const bool v_sm = 2 * nn * sizeof(T) <= (size_t)EIG_SMEM_BYTES;
+    T* A = a_sm ? esm : t.A;
+    T* W = v_sm ? esm + nn : t.V;      // W[j*n + i] = V[i*n + j]
     __shared__ int Pp[EIG_MAXN / 2], Qq[EIG_MAXN / 2];
-    __shared__ double Cc[EIG_MAXN / 2], Ss[EIG_MAXN / 2];
+    __shared__ T Cc[EIG_MAXN / 2], Ss[EIG_MAXN / 2];
     __shared__ double red[2][32];
     __shared__ int stop;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        if (in_smem) A[e] = t.A[e];
-        V[e] = (e / n == e % n) ? 1.0 : 0.0;
+    for (int e = threadIdx.x; e < (int)nn; e += blockDim.x) {
+        if (a_sm) A[e] = t.A[e];
+        if (!t.vinit) W[e] = (e / n == e % n) ? T(1) : T(0);
+        else if (v_sm) W[(size_t)(e % n) * n + e / n] = t.V[e];
+    }
+    if (t.vinit && !v_sm) {
+        __syncthreads();
+        transpose_inplace(W, n);
     }
     __syncthreads();
     if (n > 1) {
         const int m = n + (n & 1);
         const int half = m / 2;
-        for (int sweep = 0; sweep < 40; ++sweep) {
+        double prev_off = 1e300;   // thread 0 only
+        for (int sweep = 0; sweep < MAXSWEEP; ++sweep) {
             double off = 0.0, all = 0.0;
-            for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-                const double v = A[e];
+            for (int e = threadIdx.x; e < (int)nn; e += blockDim.x) {
+                const double v = (double)A[e];
                 all += v * v;
                 if (e / n != e % n) off += v * v;
             }
@@ -192,7 +223,10 @@ __global__ void __launch_bounds__(512) k_eig(const EigTask* __restrict__ tasks) 
             if (threadIdx.x == 0) {
                 double so = 0.0, sa = 0.0;
                 for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { so += red[0][w]; sa += red[1][w]; }
-                stop = (so <= 1e-30 * sa) || sa == 0.0;
+                // converged, or stalled at the rounding floor (a sweep that no
+                // longer shrinks a small off-diagonal norm)
+                stop = (so <= (double)STOP * sa) || sa == 0.0 || (so <= 1e-8 * sa && so > 0.81 * prev_off);
+                prev_off = so;
             }
             __syncthreads();
             if (stop) break;
@@ -201,14 +235,14 @@ __global__ void __launch_bounds__(512) k_eig(const EigTask* __restrict__ tasks) 
                     int pa, pb;
                     rr_pair(k, r, m, pa, pb);
                     int p = min(pa, pb), q = max(pa, pb);
-                    double c = 1.0, s = 0.0;
+                    T c = T(1), s = T(0);
                     if (q < n) {
-                        const double apq = A[(size_t)p * n + q];
-                        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
-                        if (fabs(apq) > 1e-18 * sqrt(fabs(app * aqq)) && apq != 0.0) {
-                            const double th = (aqq - app) / (2.0 * apq);
-                            const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                            c = 1.0 / sqrt(tt * tt + 1.0);
+                        const T apq = A[(size_t)p * n + q];
+                        const T app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                        if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && apq != T(0)) {
+                            const T th = (aqq - app) / (T(2) * apq);
+                            const T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+                            c = T(1) / sqrt(tt * tt + T(1));
                             s = tt * c;
                         }
                     } else {
@@ -217,44 +251,48 @@ __global__ void __launch_bounds__(512) k_eig(const EigTask* __restrict__ tasks) 
                     Pp[k] = p; Qq[k] = q; Cc[k] = c; Ss[k] = s;
                 }
                 __syncthreads();
-                // A <- J^T A J block by block; V <- V J
+                // A <- J^T A J block by block
                 for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
                     const int k = e / half, l = e % half;
                     const int p = Pp[k], q = Qq[k], u = Pp[l], v = Qq[l];
-                    const double ck = Cc[k], sk = Ss[k], cl = Cc[l], sl = Ss[l];
-                    if (sk == 0.0 && sl == 0.0) continue;
+                    const T ck = Cc[k], sk = Ss[k], cl = Cc[l], sl = Ss[l];
+                    if (sk == T(0) && sl == T(0)) continue;
                     // rows p (and q), columns u (and v); rotation: new_p = c*old_p - s*old_q,
                     // new_q = s*old_p + c*old_q, applied on both sides
                     const bool hq = q >= 0, hv = v >= 0;
-                    double a_pu = A[(size_t)p * n + u];
-                    double a_pv = hv ? A[(size_t)p * n + v] : 0.0;
-                    double a_qu = hq ? A[(size_t)q * n + u] : 0.0;
-                    double a_qv = (hq && hv) ? A[(size_t)q * n + v] : 0.0;
-                    // left: rows
-                    const double r_pu = ck * a_pu - sk * a_qu, r_qu = sk * a_pu + ck * a_qu;
-                    const double r_pv = ck * a_pv - sk * a_qv, r_qv = sk * a_pv + ck * a_qv;
-                    // right: columns
+                    T a_pu = A[(size_t)p * n + u];
+                    T a_pv = hv ? A[(size_t)p * n + v] : T(0);
+                    T a_qu = hq ? A[(size_t)q * n + u] : T(0);
+                    T a_qv = (hq && hv) ? A[(size_t)q * n + v] : T(0);
+                    const T r_pu = ck * a_pu - sk * a_qu, r_qu = sk * a_pu + ck * a_qu;
+                    const T r_pv = ck * a_pv - sk * a_qv, r_qv = sk * a_pv + ck * a_qv;
                     A[(size_t)p * n + u] = cl * r_pu - sl * r_pv;
                     if (hv) A[(size_t)p * n + v] = sl * r_pu + cl * r_pv;
                     if (hq) A[(size_t)q * n + u] = cl * r_qu - sl * r_qv;
                     if (hq && hv) A[(size_t)q * n + v] = sl * r_qu + cl * r_qv;
                 }
+                // eigenvector rows u, v of W (columns of V) <- rotation R_l
                 for (int e = threadIdx.x; e < n * half; e += blockDim.x) {
-                    const int i = e / half, l = e % half;
+                    const int l = e / n, i = e % n;
                     const int u = Pp[l], v = Qq[l];
-                    const double cl = Cc[l], sl = Ss[l];
-                    if (sl == 0.0 || v < 0) continue;
-                    const double viu = V[(size_t)i * n + u], viv = V[(size_t)i * n + v];
-                    V[(size_t)i * n + u] = cl * viu - sl * viv;
-                    V[(size_t)i * n + v] = sl * viu + cl * viv;
+                    const T cl = Cc[l], sl = Ss[l];
+                    if (sl == T(0) || v < 0) continue;
+                    const T wu = W[(size_t)u * n + i], wv = W[(size_t)v * n + i];
+                    W[(size_t)u * n + i] = cl * wu - sl * wv;
+                    W[(size_t)v * n + i] = sl * wu + cl * wv;
                 }
                 __syncthreads();
             }
         }
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) t.w[i] = A[(size_t)i * n + i];
-    if (in_smem)
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) { t.V[e] = V[e]; t.A[e] = A[e]; }
+    if (v_sm) {
+        for (int e = threadIdx.x; e < (int)nn; e += blockDim.x) t.V[e] = W[(size_t)(e % n) * n + e / n];
+    } else {
+        transpose_inplace(W, n);
+    }
+    if (a_sm)
+        for (int e = threadIdx.x; e < (int)nn; e += blockDim.x) t.A[e] = A[e];
 }
 
 // ----------------------------------------------------------------- vectors
@@ -403,6 +441,14 @@ __global__ void k_cg_dir(double* p, const double* __restrict__ z, size_t n, cons
         p[i] = z[i] + be * p[i];
 }
 
+// G <- 1.5 I - 0.5 G for each task's n x n block (Newton-Schulz step)
+__global__ void k_ns_prep(const EigTask* __restrict__ tasks) {
+    const EigTask t = tasks[blockIdx.x];
+    const int n = t.n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+        t.A[e] = (e / n == e % n ? 1.5 : 0.0) - 0.5 * t.A[e];
+}
+
 __global__ void k_axpy(double* y, const double* __restrict__ x, double a, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         y[i] += a * x[i];
@@ -466,17 +512,22 @@ void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaSt
 void launch_eig(const EigTask* tasks, int ntask, cudaStream_t st) {
     if (ntask <= 0) return;
     static bool attr = false;
-    const int smem = 2 * EIG_SMEM_N * EIG_SMEM_N * (int)sizeof(double);
+    const int smem = EIG_SMEM_BYTES;
     if (!attr) {
-        cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_eig<double, EigTask>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
     counted();
-    k_eig<<<ntask, 512, smem, st>>>(tasks);
+    k_eig<double, EigTask><<<ntask, 512, smem, st>>>(tasks);
 }
+
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st) {
     if (ntask > 0) { counted(); k_copy<<<ntask, 256, 0, st>>>(tasks); }
 }
+void launch_ns_prep(const EigTask* tasks, int ntask, cudaStream_t st) {
+    if (ntask > 0) { counted(); k_ns_prep<<<ntask, 256, 0, st>>>(tasks); }
+}
+
 void vec_zero(double* x, size_t n, cudaStream_t st) { if (n) k_zero<<<ew_grid(n), 256, 0, st>>>(x, n); }
 void vec_scale_mask(double* y, const double* x, double a, size_t n, cudaStream_t st) {
     if (n) { counted(); k_scale<<<ew_grid(n), 256, 0, st>>>(y, x, a, n); }

@@ -63,10 +63,24 @@ struct DiagTask {
 // Symmetric eigenproblem of one dense n x n row-major block (in place).
 struct EigTask {
     double* A;      // n*n, destroyed (diagonal holds eigenvalues on exit)
-    double* V;      // n*n eigenvectors (columns)
+    double* V;      // n*n eigenvectors (columns); with vinit: initial basis, rotated in place
     double* w;      // n eigenvalues (unsorted)
     int n;
-    int pad;
+    int vinit;
+};
+// One matrix of the sweep-per-launch Jacobi (kernels_eig.cu).
+struct JacTask {
+    const double* A;   // n x n symmetric input, row-major (read by sweep 0 only)
+    void* P;           // scratch: packed upper triangle, jac_p_bytes(n)
+    void* rot;         // scratch: rotation lists of the current sweep, jac_rot_bytes(n)
+    double* V;         // n x n eigenvectors (columns), row-major; with vinit: the start basis
+    double* w;         // n eigenvalues (unsorted), or null
+    double* prev;      // scratch: off-norm of the previous sweep
+    int* done;         // scratch: set once the matrix has converged
+    int n, vinit;
+};
+struct JacRows {       // rows [r0, r0 + rows) of task's V for one apply block
+    int task, r0, rows, pad;
 };
 
 // Block copy with optional column selection and transpose:
@@ -113,6 +127,13 @@ void launch_mix(const MixTask* tasks, int ntask, const MixSrc* srcs, cudaStream_
                 const int* skip = nullptr);
 void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaStream_t st);
 void launch_eig(const EigTask* tasks, int ntask, cudaStream_t st);
+size_t jac_p_bytes(int n);
+size_t jac_rot_bytes(int n);
+int jac_rows_per_block(int n, bool f32);
+void launch_jac_sweep(const JacTask* tasks, int ntask, int sweep, int maxs, bool f32, cudaStream_t st);
+void launch_jac_apply(const JacTask* tasks, const JacRows* rows, int nblocks, int smem, int sweep, bool f32,
+                      cudaStream_t st);
+void launch_ns_prep(const EigTask* tasks, int ntask, cudaStream_t st);
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
 
 // Vector kernels (n doubles).  Reductions are deterministic (fixed order).

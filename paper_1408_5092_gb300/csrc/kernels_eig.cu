@@ -1,0 +1,273 @@
+// Batched cyclic Jacobi for the density-matrix eigenproblems of the
+// truncation step, one launch per sweep.
+//
+// k_jac_sweep (one CTA of 512 threads per matrix): the symmetric matrix is
+// kept as its packed upper triangle, in shared memory when it fits (float64
+// up to n = 215, float32 up to n = 305), else in the task's global scratch.
+// A sweep is the m-1 rounds of the round-robin ordering; in a round the m/2
+// disjoint pairs get their rotations (threshold: negligible a_pq are
+// skipped), then every unordered 2x2 block {k, l} of pairs is updated once
+// (R_k^T A_kl R_l; the symmetric partner is implied).  The applied rotations
+// of each round are recorded, compacted, in the task's rotation list.
+//
+// k_jac_apply (one warp per block of up to 32 rows of V): V <- V R for the
+// recorded rotations, in order.  A row of V is touched independently of the
+// others, so each lane owns one row in shared memory and runs through the
+// whole list without synchronisation; the work spreads over many SMs.
+//
+// The host launches sweep 0, apply 0, sweep 1, apply 1, ... up to maxs.  A
+// sweep first measures off(A)^2 and stops the task (flag, eigenvalues
+// written) when off^2 <= STOP * |A|_F^2, when a small off-norm stalled at
+// the rounding floor, or at sweep maxs; later launches for that task return
+// at once.
+#include "kernels.h"
+
+namespace mpspt {
+namespace {
+
+constexpr int JAC_THREADS = 512;
+constexpr int JAC_SMEM = 200704;     // dynamic shared memory of the sweep kernel
+
+template <class T>
+struct RotE {
+    T c, s;
+    int p, q;
+};
+
+template <class T>
+struct JacTol;
+template <>
+struct JacTol<double> {
+    static constexpr double stop = 1e-30, skip = 1e-18;
+};
+template <>
+struct JacTol<float> {
+    static constexpr double stop = 1e-11, skip = 1e-9;
+};
+
+__device__ __forceinline__ void rr_pair(int k, int r, int m, int& pa, int& pb) {
+    pa = (k == 0) ? 0 : ((k - 1 + r) % (m - 1)) + 1;
+    pb = ((m - 1 - k - 1 + r) % (m - 1)) + 1;
+}
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// shared-memory head of the sweep kernel: rowoff[n], Pp[half], Qq[half], Cc, Ss
+template <class T>
+__host__ __device__ inline size_t jac_head_bytes(int n) {
+    const int half = (n + (n & 1)) / 2;
+    return align16((size_t)n * 4 + 2 * (size_t)half * 4) + align16(2 * (size_t)half * sizeof(T));
+}
+
+template <class T>
+__global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __restrict__ tasks, int sweep, int maxs) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red[2][JAC_THREADS / 32];
+    __shared__ int stop, cnt;
+    const JacTask t = tasks[blockIdx.x];
+    if (sweep > 0 && *(volatile const int*)t.done) return;
+    const int n = t.n;
+    const int m = n + (n & 1), half = m / 2;
+    const size_t np = (size_t)n * (n + 1) / 2;
+    int* rowoff = reinterpret_cast<int*>(sm);
+    int* Pp = rowoff + n;
+    int* Qq = Pp + half;
+    T* Cc = reinterpret_cast<T*>(sm + align16((size_t)n * 4 + 2 * (size_t)half * 4));
+    T* Ss = Cc + half;
+    const size_t head = jac_head_bytes<T>(n);
+    const bool p_sm = head + np * sizeof(T) <= (size_t)JAC_SMEM;
+    T* P = p_sm ? reinterpret_cast<T*>(sm + head) : reinterpret_cast<T*>(t.P);
+    T* Pg = reinterpret_cast<T*>(t.P);
+    int* rcount = reinterpret_cast<int*>(t.rot);
+    RotE<T>* rlist = reinterpret_cast<RotE<T>*>(reinterpret_cast<unsigned char*>(t.rot) + align16((size_t)(m - 1) * 4));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = JAC_THREADS / 32;
+    for (int i = tid; i < n; i += JAC_THREADS) rowoff[i] = i * n - i * (i + 1) / 2;
+    __syncthreads();
+    if (sweep == 0) {
+        for (int e = tid; e < n * n; e += JAC_THREADS) {
+            const int i = e / n, j = e % n;
+            if (j >= i) P[rowoff[i] + j] = (T)t.A[e];
+        }
+    } else if (p_sm) {
+        for (size_t e = tid; e < np; e += JAC_THREADS) P[e] = Pg[e];
+    }
+    __syncthreads();
+    auto S = [&](int a, int b) -> T& { return a <= b ? P[rowoff[a] + b] : P[rowoff[b] + a]; };
+    // convergence test
+    {
+        double off = 0.0, all = 0.0;
+        for (int i = warp; i < n; i += nw)
+            for (int j = i + lane; j < n; j += 32) {
+                const double v = (double)P[rowoff[i] + j];
+                if (j == i) all += v * v;
+                else off += 2.0 * v * v;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            all += __shfl_xor_sync(0xffffffffu, all, o);
+        }
+        if (lane == 0) { red[0][warp] = off; red[1][warp] = all; }
+        __syncthreads();
+        if (tid == 0) {
+            double so = 0.0, sd = 0.0;
+            for (int w = 0; w < nw; ++w) { so += red[0][w]; sd += red[1][w]; }
+            const double sa = so + sd;
+            const double prev = sweep == 0 ? 1e300 : *t.prev;
+            const int s = (so <= JacTol<T>::stop * sa) || sa == 0.0 || (so <= 1e-8 * sa && so > 0.81 * prev) ||
+                          sweep >= maxs || n < 2;
+            *t.prev = so;
+            *t.done = s;
+            stop = s;
+        }
+        __syncthreads();
+    }
+    if (stop) {
+        if (t.w)
+            for (int i = tid; i < n; i += JAC_THREADS) t.w[i] = (double)P[rowoff[i] + i];
+        return;
+    }
+    constexpr T SKIP = (T)JacTol<T>::skip;
+    for (int r = 0; r < m - 1; ++r) {
+        if (tid == 0) cnt = 0;
+        __syncthreads();
+        for (int k = tid; k < half; k += JAC_THREADS) {
+            int pa, pb;
+            rr_pair(k, r, m, pa, pb);
+            int p = min(pa, pb), q = max(pa, pb);
+            T c = T(1), s = T(0);
+            if (q < n) {
+                const T apq = P[rowoff[p] + q];
+                const T app = P[rowoff[p] + p], aqq = P[rowoff[q] + q];
+                if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && apq != T(0)) {
+                    const T th = (aqq - app) / (T(2) * apq);
+                    const T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+                    c = T(1) / sqrt(tt * tt + T(1));
+                    s = tt * c;
+                }
+            } else {
+                q = -1;   // dummy player
+            }
+            Pp[k] = p; Qq[k] = q; Cc[k] = c; Ss[k] = s;
+            if (s != T(0)) {
+                const int slot = atomicAdd(&cnt, 1);   // pairs of a round commute: order is free
+                rlist[(size_t)r * half + slot] = RotE<T>{c, s, p, q};
+            }
+        }
+        __syncthreads();
+        if (tid == 0) rcount[r] = cnt;
+        for (int k = warp; k < half; k += nw) {
+            const int p = Pp[k], q = Qq[k];
+            const T ck = Cc[k], sk = Ss[k];
+            for (int l = k + lane; l < half; l += 32) {
+                const T cl = Cc[l], sl = Ss[l];
+                if (sk == T(0) && sl == T(0)) continue;
+                if (l == k) {
+                    const T app = S(p, p), apq = S(p, q), aqq = S(q, q);
+                    const T r_pp = ck * app - sk * apq, r_pq = ck * apq - sk * aqq;
+                    const T r_qp = sk * app + ck * apq, r_qq = sk * apq + ck * aqq;
+                    S(p, p) = ck * r_pp - sk * r_pq;
+                    S(q, q) = sk * r_qp + ck * r_qq;
+                    S(p, q) = T(0);
+                    continue;
+                }
+                const int u = Pp[l], v = Qq[l];
+                const bool hq = q >= 0, hv = v >= 0;
+                const T a_pu = S(p, u);
+                const T a_pv = hv ? S(p, v) : T(0);
+                const T a_qu = hq ? S(q, u) : T(0);
+                const T a_qv = (hq && hv) ? S(q, v) : T(0);
+                const T r_pu = ck * a_pu - sk * a_qu, r_qu = sk * a_pu + ck * a_qu;
+                const T r_pv = ck * a_pv - sk * a_qv, r_qv = sk * a_pv + ck * a_qv;
+                S(p, u) = cl * r_pu - sl * r_pv;
+                if (hv) S(p, v) = sl * r_pu + cl * r_pv;
+                if (hq) S(q, u) = cl * r_qu - sl * r_qv;
+                if (hq && hv) S(q, v) = sl * r_qu + cl * r_qv;
+            }
+        }
+        __syncthreads();
+    }
+    if (p_sm)
+        for (size_t e = tid; e < np; e += JAC_THREADS) Pg[e] = P[e];
+}
+
+template <class T>
+__global__ void __launch_bounds__(32) k_jac_apply(const JacTask* __restrict__ tasks, const JacRows* __restrict__ rb,
+                                                 int sweep) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const JacRows b = rb[blockIdx.x];
+    const JacTask t = tasks[b.task];
+    const int done = *(volatile const int*)t.done;
+    if (sweep > 0 && done) return;
+    const int n = t.n, ld = n | 1, lane = threadIdx.x;
+    T* R = reinterpret_cast<T*>(sm);
+    for (int e = lane; e < b.rows * n; e += 32) {
+        const int i = e / n, j = e % n;
+        R[i * ld + j] = (sweep == 0 && !t.vinit) ? T(b.r0 + i == j ? 1 : 0) : (T)t.V[(size_t)(b.r0 + i) * n + j];
+    }
+    __syncwarp();
+    if (!done && lane < b.rows) {
+        const int m = n + (n & 1), half = m / 2;
+        const int* rcount = reinterpret_cast<const int*>(t.rot);
+        const RotE<T>* rlist =
+            reinterpret_cast<const RotE<T>*>(reinterpret_cast<const unsigned char*>(t.rot) + align16((size_t)(m - 1) * 4));
+        T* row = R + lane * ld;
+        for (int r = 0; r < m - 1; ++r) {
+            const int c = __ldg(rcount + r);
+            const RotE<T>* L = rlist + (size_t)r * half;
+            for (int j = 0; j < c; ++j) {
+                const RotE<T> e = L[j];
+                const T x = row[e.p], y = row[e.q];
+                row[e.p] = e.c * x - e.s * y;
+                row[e.q] = e.s * x + e.c * y;
+            }
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < b.rows * n; e += 32) {
+        const int i = e / n, j = e % n;
+        t.V[(size_t)(b.r0 + i) * n + j] = (double)R[i * ld + j];
+    }
+}
+
+}  // namespace
+
+size_t jac_p_bytes(int n) { return (size_t)n * (n + 1) / 2 * sizeof(double); }
+size_t jac_rot_bytes(int n) {
+    const int m = n + (n & 1), half = m / 2;
+    return align16((size_t)(m - 1) * 4) + (size_t)(m - 1) * half * sizeof(RotE<double>);
+}
+int jac_rows_per_block(int n, bool f32) {
+    const size_t row = (size_t)(n | 1) * (f32 ? 4 : 8);
+    const size_t r = (size_t)JAC_SMEM / row;
+    return (int)(r < 32 ? (r < 1 ? 1 : r) : 32);
+}
+
+static void jac_attributes() {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_jac_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, JAC_SMEM);
+        cudaFuncSetAttribute(k_jac_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, JAC_SMEM);
+        cudaFuncSetAttribute(k_jac_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, JAC_SMEM);
+        cudaFuncSetAttribute(k_jac_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, JAC_SMEM);
+        attr = true;
+    }
+}
+
+void launch_jac_sweep(const JacTask* tasks, int ntask, int sweep, int maxs, bool f32, cudaStream_t st) {
+    if (ntask <= 0) return;
+    jac_attributes();
+    count_launch();
+    if (f32) k_jac_sweep<float><<<ntask, JAC_THREADS, JAC_SMEM, st>>>(tasks, sweep, maxs);
+    else k_jac_sweep<double><<<ntask, JAC_THREADS, JAC_SMEM, st>>>(tasks, sweep, maxs);
+}
+
+void launch_jac_apply(const JacTask* tasks, const JacRows* rows, int nblocks, int smem, int sweep, bool f32,
+                      cudaStream_t st) {
+    if (nblocks <= 0) return;
+    jac_attributes();
+    count_launch();
+    if (f32) k_jac_apply<float><<<nblocks, 32, smem, st>>>(tasks, rows, sweep);
+    else k_jac_apply<double><<<nblocks, 32, smem, st>>>(tasks, rows, sweep);
+}
+
+}  // namespace mpspt

@@ -113,6 +113,29 @@ def test_e2_e3_match_oracle(L, tiny, gold, h0, which):
     L.mpspt_destroy(ctx)
 
 
+@pytest.mark.parametrize("h0", ["fock", "dyall"])
+def test_eigensolver_paths_agree(L, tiny, gold, h0):
+    """The truncation's eigen-decomposition (Eq. 6 density matrix) has two
+    paths: float32 Jacobi + float64 Newton-Schulz + float64 Jacobi polish
+    (default), and float64 Jacobi from the identity.  Both give the oracle's
+    E2, and the kept states are orthonormal: after the closing right-to-left
+    half sweep every site but the first is right-orthonormal."""
+    run = gold["h0"][h0]["runs"]["16"]
+    e2s = []
+    for fp64_only in (0, 1):
+        ctx = _session(L, tiny, eig_fp64_only=fp64_only)
+        e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, h0, 16)
+        assert abs(e2 - run["E2"]) < 1e-8, (fp64_only, e2, run["E2"])
+        ts, _ = L.mpspt_mps_export(psi)
+        for A in ts[1:]:
+            m = A.reshape(A.shape[0], -1)
+            assert np.abs(m @ m.T - np.eye(A.shape[0])).max() < 1e-12
+        e2s.append(e2)
+        L.mpspt_mps_free(psi)
+        L.mpspt_destroy(ctx)
+    assert abs(e2s[0] - e2s[1]) < 1e-10, e2s
+
+
 def test_errors_are_statuses_not_crashes(L, tiny):
     h, Lc, c, ci = tiny
     ctx = L.mpspt_create()
