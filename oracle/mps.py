@@ -34,7 +34,12 @@ Initial Psi1 (a documented rule shared with the GPU library):
   * entry (l, s, r) of site c: u = splitmix64((seed << 48) + ((4c + s) << 38)
     + (l << 19) + r) >> 11, value = u * 2^-53 - 0.5 (l, r = positions in the
     sorted bond bases);
-  * then brought to right-canonical form.
+  * then brought to right-canonical form by the renormalisation step
+    itself: for i = nsite-2 .. 0 the two-site product A_i A_{i+1} is split
+    right-to-left by its density matrix (truncate with no M cap: every
+    eigenvector above 1e-13 tr rho is kept, the sector filter applies), so
+    the initial state is the random MPS with its negligible directions
+    removed by the same rule the sweep uses.
 """
 import numpy as np
 
@@ -142,6 +147,17 @@ def random_mps(nsite, target, allowed_n, M, seed):
             T[l, s, r] = init_value(seed, c, int(s), int(l), int(r))
         A.append(T)
     return MPS(A, labels)
+
+
+def canonicalize_by_splits(mps, allowed):
+    """Right-canonical form by right-to-left density-matrix splits of the
+    two-site products (the sweep's renormalisation step without an M cap);
+    the norm ends up in A[0]."""
+    for i in range(mps.nsite - 2, -1, -1):
+        x = np.einsum("lsm,mtr->lstr", mps.A[i], mps.A[i + 1])
+        Al, Ar, lab, _ = truncate(x, mps.q[i], mps.q[i + 2], 1 << 30, "RL", allowed.get(i + 1))
+        mps.A[i], mps.A[i + 1], mps.q[i + 1] = Al, Ar, lab
+    return mps
 
 
 def right_canonicalize(mps, tol=1e-14):
@@ -425,7 +441,7 @@ class HylleraasSweep:
         self.WA = mpo_A or build_mpo(prob.h0_terms(), self.k, k_split=prob.k_act)
         self.WV = mpo_V or build_mpo(prob.rhs_terms(), self.k, k_split=prob.k_act)
         self.psi0 = reference_mps(prob.ci, prob.k_act, prob.k_virt)
-        self.psi1 = right_canonicalize(random_mps(self.k, (N, 0), self.allowed, M, seed))
+        self.psi1 = canonicalize_by_splits(random_mps(self.k, (N, 0), self.allowed, M, seed), self.allowed)
         k = self.k
         self.LA = [None] * (k + 1)
         self.LV = [None] * (k + 1)

@@ -1,7 +1,8 @@
 """Writes the stored oracle energies used by the GPU parity tests.
 
 Calls only oracle/ (and the seeded inputs of synthetic/).  Run from the repo
-root:  python tests/golden/make_golden.py [tiny|medium64]
+root:  python tests/golden/make_golden.py [tiny|medium64 [fock|dyall [sweeps]]]
+(medium: the first sweeps of the M = 64 run; the tests compare E2 per sweep).
 """
 import json
 import os
@@ -38,12 +39,12 @@ def tiny():
     return out
 
 
-def medium(M, h0):
+def medium(M, h0, sweeps):
     h, L, c = synthetic.config_integrals("medium")
     ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
     p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
     t = time.time()
-    sw = HylleraasSweep(p, M, tol_e=1e-9, verbose=True)
+    sw = HylleraasSweep(p, M, tol_e=1e-9, max_sweeps=sweeps, verbose=True)
     e2 = sw.run()
     return {"config": "medium", "h0": h0, "M": M, "E_ref": p.E_ref, "E0": p.E0, "E1": p.E1,
             "E2": e2, "sweeps": len(sw.history), "history": sw.history, "tol_e": 1e-9,
@@ -58,7 +59,7 @@ if __name__ == "__main__":
     else:
         M = int(what.replace("medium", ""))
         h0 = sys.argv[2] if len(sys.argv) > 2 else "fock"
-        res = medium(M, h0)
+        res = medium(M, h0, int(sys.argv[3]) if len(sys.argv) > 3 else 4)
         name = f"oracle_medium_{h0}_M{M}.json"
     with open(os.path.join(HERE, name), "w") as f:
         json.dump(res, f, indent=1)

@@ -80,3 +80,32 @@ def test_medium_local_operators(medium, h0):
             assert ratio <= 1e-10, (i, name, ratio)
     L.mpspt_mps_free(psi)
     L.mpspt_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 1e-6)])
+def test_medium_e2_per_sweep_matches_oracle(medium, prec, tol):
+    """E2 after each of the first sweeps at M = 64 (Fock H0) against the
+    oracle's sweep history from the same seeded initial Psi1
+    (tests/golden/oracle_medium_fock_M64.json, written by make_golden.py).
+    M = 64 truncates strongly (discarded weight ~4e-2) and converges slowly,
+    so the comparison is per sweep, not on a converged value."""
+    import json
+    import os
+    from paper_1408_5092_gb300 import _lib as L
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_medium_fock_M64.json")))
+    h, Lc, c, ci = medium
+    o = L.mpspt_default_options()
+    o.prec = L.PREC[prec]
+    o.max_sweeps = 3
+    o.e_tol = 1e-14          # run all three sweeps
+    ctx = L.mpspt_create(o)
+    L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
+    L.mpspt_set_reference(ctx, ci)
+    e0, e1, eref = L.mpspt_energies(ctx, "fock")
+    assert abs(eref - gold["E_ref"]) < 1e-10 and abs(e0 - gold["E0"]) < 1e-10
+    e2, _, rep = L.mpspt_minimize_hylleraas(ctx, "fock", 64, want_psi1=False)
+    hist = [rep.e2_per_sweep[s] for s in range(rep.n_sweeps)]
+    assert rep.n_sweeps == 3
+    for s in range(3):
+        assert abs(hist[s] - gold["history"][s]) < tol, (s, hist[s], gold["history"][s])
+    L.mpspt_destroy(ctx)
