@@ -595,6 +595,12 @@ struct Sweeper {
     Work w;
     TwoT X, X0;
     Omega omA, omV;
+    std::vector<std::unique_ptr<Omega>> omA_c, omV_c;   // per bond: the MPO is fixed during the run
+    const Omega& omega(std::vector<std::unique_ptr<Omega>>& cache, const MPO& W, int i) {
+        if ((int)cache.size() <= i) cache.resize(i + 1);
+        if (!cache[i]) { cache[i].reset(new Omega); cache[i]->build(W, i); }
+        return *cache[i];
+    }
     TwoSitePlan sig, sig_lo, rhs;   // sig: float64; sig_lo: inner operator when prec != FP64
     DiagPlan dia;
     int lo_kind = GEMM_F64;
@@ -619,6 +625,7 @@ struct Sweeper {
         MPSPT_CUDA(cudaEventCreate(&ev1));
         for (auto& e : evs) MPSPT_CUDA(cudaEventCreate(&e));
         for (auto& e : sev) MPSPT_CUDA(cudaEventCreate(&e));
+        for (auto& e : pev) MPSPT_CUDA(cudaEventCreate(&e));
     }
     ~Sweeper() {
         cudaEventDestroy(ev0); cudaEventDestroy(ev1);
@@ -640,15 +647,18 @@ struct Sweeper {
         one(RV[k], WV.dq[k], psi.bond[k], psi0.bond[k]);
     }
 
+    double env_flops = 0.0;     // flops of the last environment update
     void update_left(int i) {   // L[i+1] from L[i] and site i
         LA[i + 1].build(WA.dq[i + 1], psi.bond[i + 1], psi.bond[i + 1], ln.st);
         envp.build_left(WA, i, LA[i], psi.A[i], psi.A[i], psi.bond[i], psi.bond[i], psi.bond[i + 1],
                         psi.bond[i + 1], LA[i + 1], ln.st);
         envp.run(ln.st);
+        env_flops = envp.flops();
         LV[i + 1].build(WV.dq[i + 1], psi.bond[i + 1], psi0.bond[i + 1], ln.st);
         envp.build_left(WV, i, LV[i], psi.A[i], psi0.A[i], psi.bond[i], psi0.bond[i], psi.bond[i + 1],
                         psi0.bond[i + 1], LV[i + 1], ln.st);
         envp.run(ln.st);
+        env_flops += envp.flops();
     }
 
     void update_right(int i) {  // R[i] from R[i+1] and site i
@@ -656,10 +666,12 @@ struct Sweeper {
         envp.build_right(WA, i, RA[i + 1], psi.A[i], psi.A[i], psi.bond[i], psi.bond[i], psi.bond[i + 1],
                          psi.bond[i + 1], RA[i], ln.st);
         envp.run(ln.st);
+        env_flops = envp.flops();
         RV[i].build(WV.dq[i], psi.bond[i], psi0.bond[i], ln.st);
         envp.build_right(WV, i, RV[i + 1], psi.A[i], psi0.A[i], psi.bond[i], psi0.bond[i], psi.bond[i + 1],
                          psi0.bond[i + 1], RV[i], ln.st);
         envp.run(ln.st);
+        env_flops += envp.flops();
     }
 
     // x (device, X layout) -> new A_i, A_{i+1}, bond i+1.  dir 0: left-to-right.
@@ -1137,7 +1149,8 @@ struct Sweeper {
     double t_plan = 0, t_rhs = 0, t_solve = 0, t_split = 0, t_env = 0;
     double t_rho = 0, t_eig = 0, t_post = 0, eig_n3 = 0;   // device ms (verbose >= 3)
     int eig_nmax = 0, eig_calls = 0;
-    cudaEvent_t sev[4];
+    cudaEvent_t sev[4], pev[4];
+    double t_rhs_dev = 0, t_env_dev = 0, rhs_gf = 0, env_gf = 0;   // verbose >= 3
     using clk = std::chrono::steady_clock;
     static double since(clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); }
 
@@ -1151,15 +1164,18 @@ struct Sweeper {
         double* x = w.x.as<double>();
         product(prod, psi, i, X, x);
         product(prod0, psi0, i, X0, w.x0.as<double>());
-        omA.build(WA, i);
-        omV.build(WV, i);
-        rhs.build(omV, X, X0, bL, psi0.bond[i], bR, psi0.bond[i + 2], LV[i], RV[i + 2], WV.dq[i + 2],
+        const Omega& oA = omega(omA_c, WA, i);
+        const Omega& oV = omega(omV_c, WV, i);
+        rhs.build(oV, X, X0, bL, psi0.bond[i], bR, psi0.bond[i + 2], LV[i], RV[i + 2], WV.dq[i + 2],
                   w.x0.as<double>(), w.g.as<double>(), ln.st);
+        if (c.opt.verbose >= 3) MPSPT_CUDA(cudaEventRecord(pev[0], ln.st));
         rhs.run(ln.st);
+        if (c.opt.verbose >= 3) { MPSPT_CUDA(cudaEventRecord(pev[1], ln.st)); rhs_gf += rhs.flops() * 1e-9; }
         if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_rhs += since(t0); t0 = clk::now(); }
-        sig.build(omA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
+        if (c.opt.verbose >= 3) { float a; cudaEventElapsedTime(&a, pev[0], pev[1]); t_rhs_dev += a; }
+        sig.build(oA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
                   w.Ap.as<double>(), ln.st);
-        dia.build(omA, X, bL, bR, LA[i], RA[i + 2], WA.dq[i], WA.dq[i + 2], w.dg.as<double>(), ln.st);
+        dia.build(oA, X, bL, bR, LA[i], RA[i + 2], WA.dq[i], WA.dq[i + 2], w.dg.as<double>(), ln.st);
         dia.run(ln.st);
         make_minv(w.minv.as<double>(), w.dg.as<double>(), n, ln.st);
         vec_scale_mask(w.b.as<double>(), w.g.as<double>(), -1.0, n, ln.st);
@@ -1168,7 +1184,7 @@ struct Sweeper {
         if (c.harvesting)
             MPSPT_CUDA(cudaMemcpyAsync(w.xw.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
         if (lo_kind != GEMM_F64)
-            sig_lo.build(omA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
+            sig_lo.build(oA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
                          w.Ap.as<double>(), ln.st);
         if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_plan += since(t0); t0 = clk::now(); }
         if (c.net != nullptr && c.opt.use_learned && !c.harvesting) learned_guess(n);
@@ -1180,9 +1196,12 @@ struct Sweeper {
         res->max_disc = std::max(res->max_disc, disc);
         res->max_bond = std::max(res->max_bond, psi.bond[i + 1].total);
         if (c.opt.verbose >= 2) { t_split += since(t0); t0 = clk::now(); }
+        if (c.opt.verbose >= 3) MPSPT_CUDA(cudaEventRecord(pev[2], ln.st));
         if (dir == 0) update_left(i);
         else update_right(i + 1);
+        if (c.opt.verbose >= 3) { MPSPT_CUDA(cudaEventRecord(pev[3], ln.st)); env_gf += env_flops * 1e-9; }
         if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_env += since(t0); }
+        if (c.opt.verbose >= 3) { float a; cudaEventElapsedTime(&a, pev[2], pev[3]); t_env_dev += a; }
         return h;
     }
 };
@@ -1249,6 +1268,8 @@ std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res,
         if (c.opt.verbose >= 3)
             fprintf(stderr, "[mpspt]   split dev ms: rho %.1f eig %.1f post %.1f | eig tasks %d nmax %d sum n^3 %.3g\n",
                     sw.t_rho, sw.t_eig, sw.t_post, sw.eig_calls, sw.eig_nmax, sw.eig_n3);
+            fprintf(stderr, "[mpspt]   rhs dev ms %.1f (%.1f GF) env dev ms %.1f (%.1f GF)\n", sw.t_rhs_dev, sw.rhs_gf,
+                    sw.t_env_dev, sw.env_gf);
         if (s > 0 && std::fabs(e - prev) < c.opt.e_tol) break;
         prev = e;
     }

@@ -4,8 +4,10 @@
 // v is split into hi = bf16(v), lo = bf16(v - hi) while it is staged into
 // shared memory, and the tile accumulates Ahi*Bhi + Ahi*Blo + Alo*Bhi in
 // float32 in tensor memory (TMEM).  One elected thread issues the MMAs and
-// commits them to an mbarrier per shared-memory stage (double buffered); all
-// four warps read the accumulator back with tcgen05.ld.
+// commits them to an mbarrier per shared-memory stage (double buffered).
+// The eight warps stage the operands with 16 independent loads in flight
+// per thread, and read the accumulator back with tcgen05.ld (warp w: TMEM
+// lanes 32 (w mod 4) .. +31, columns 32 (w / 4) .. +31).
 //
 // Shared-memory operand layout: K-major, no swizzle, 8x8 core matrices
 // (8 rows x 16 bytes); byte offset of (row r, k) inside a 64-wide K stage:
@@ -24,7 +26,8 @@ namespace {
 constexpr int BM = 128;     // tcgen05 M (cta_group::1)
 constexpr int BN = 64;      // tcgen05 N
 constexpr int BK = 64;      // K per shared-memory stage
-constexpr int NTH = 128;    // 4 warps
+constexpr int NTH = 256;    // 8 warps
+constexpr int LCH = 16;     // operand loads in flight per thread
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // hi + lo of A and B
@@ -145,25 +148,43 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
             unsigned char* Bhi = Alo + A_BYTES;
             unsigned char* Blo = Bhi + B_BYTES;
             const int krem = min(BK, op.k - k0);
-            for (int e = tid; e < BM * BK; e += NTH) {
-                int r, kk;
-                if (ta) { r = e % BM; kk = e / BM; } else { kk = e % BK; r = e / BK; }
-                double v = 0.0;
-                if (r < mrem && kk < krem) {
-                    const int row = t.r0 + r, kg = k0 + kk;
-                    v = op.alpha * (ta ? op.A[(size_t)kg * op.lda + row] : op.A[(size_t)row * op.lda + kg]);
+            // A: BM x BK values, B: BN x BK values; LCH loads per thread are
+            // issued before any of them is split and stored
+            for (int e0 = 0; e0 < BM * BK; e0 += NTH * LCH) {
+                double v[LCH];
+                int off[LCH];
+#pragma unroll
+                for (int q = 0; q < LCH; ++q) {
+                    const int e = e0 + q * NTH + tid;
+                    int r, kk;
+                    if (ta) { r = e % BM; kk = e / BM; } else { kk = e % BK; r = e / BK; }
+                    off[q] = (int)tile_off(r, kk);
+                    v[q] = 0.0;
+                    if (r < mrem && kk < krem) {
+                        const int row = t.r0 + r, kg = k0 + kk;
+                        v[q] = ta ? op.A[(size_t)kg * op.lda + row] : op.A[(size_t)row * op.lda + kg];
+                    }
                 }
-                split_store(Ahi, Alo, tile_off(r, kk), v);
+#pragma unroll
+                for (int q = 0; q < LCH; ++q) split_store(Ahi, Alo, (uint32_t)off[q], op.alpha * v[q]);
             }
-            for (int e = tid; e < BN * BK; e += NTH) {
-                int j, kk;
-                if (tb) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
-                double v = 0.0;
-                if (j < nrem && kk < krem) {
-                    const int col = t.c0 + j, kg = k0 + kk;
-                    v = tb ? op.B[(size_t)col * op.ldb + kg] : op.B[(size_t)kg * op.ldb + col];
+            for (int e0 = 0; e0 < BN * BK; e0 += NTH * LCH) {
+                double v[LCH];
+                int off[LCH];
+#pragma unroll
+                for (int q = 0; q < LCH; ++q) {
+                    const int e = e0 + q * NTH + tid;
+                    int j, kk;
+                    if (tb) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
+                    off[q] = (int)tile_off(j, kk);
+                    v[q] = 0.0;
+                    if (j < nrem && kk < krem) {
+                        const int col = t.c0 + j, kg = k0 + kk;
+                        v[q] = tb ? op.B[(size_t)col * op.ldb + kg] : op.B[(size_t)kg * op.ldb + col];
+                    }
                 }
-                split_store(Bhi, Blo, tile_off(j, kk), v);
+#pragma unroll
+                for (int q = 0; q < LCH; ++q) split_store(Bhi, Blo, (uint32_t)off[q], v[q]);
             }
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
@@ -198,13 +219,14 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
         __syncthreads();
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: warp w owns accumulator rows 32w .. 32w+31 (TMEM lanes)
-    const int row = warp * 32 + lane;
+    // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. +31 (accumulator
+    // rows), columns 32 (w / 4) .. +31
+    const int row = (warp & 3) * 32 + lane;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+    for (int c0 = (warp >> 2) * 32; c0 < (warp >> 2) * 32 + 32; c0 += 16) {
         uint32_t v[16];
         if (any && ok) {
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),

@@ -347,131 +347,177 @@ void plan_product(GemmPlan& g, const TwoT& x, double* xd, const Bond& mid, const
     }
 }
 
-void EnvPlan::build_left(const MPO& W, int site, const EnvT& L, const SiteT& Abra, const SiteT& Aket,
-                         const Bond& braL, const Bond& ketL, const Bond& braR, const Bond& ketR,
-                         EnvT& Lnew, cudaStream_t st) {
-    g1.clear();
-    g2.clear();
-    const int na = (int)W.dim[site];
-    const int nkb = (int)Aket.blk.size();
-    std::vector<long long> yoff((size_t)na * nkb, -1);
-    std::vector<int> ysb((size_t)na * nkb, -1);
-    size_t ys = 0;
-    for (int a = 0; a < na; ++a)
-        for (int kb = 0; kb < nkb; ++kb) {
-            const auto& K = Aket.blk[kb];
-            int lb = L.find(a, K.sl);
-            if (lb < 0) continue;
-            int sb = L.blk[lb].sb;
-            yoff[(size_t)a * nkb + kb] = (long long)ys;
-            ysb[(size_t)a * nkb + kb] = sb;
-            ys += (size_t)braL.sec[sb].dim * ketR.sec[K.sr].dim;
+void EnvPlan::upload_mix(cudaStream_t st) {
+    if (checks_enabled()) {
+        for (const auto& t : mt) {
+            check_range(t.dst, ((size_t)(t.rows - 1) * t.ldd + t.cols) * sizeof(double), "env mix dst");
+            for (int q = t.s0; q < t.s1; ++q)
+                check_range(ms[q].src, ((size_t)(t.rows - 1) * ms[q].lds + t.cols) * sizeof(double), "env mix src");
         }
-    Y.ensure((ys + 1) * sizeof(double), st);
-    double* Yp = Y.as<double>();
-    for (int a = 0; a < na; ++a)
-        for (int kb = 0; kb < nkb; ++kb) {
-            long long o = yoff[(size_t)a * nkb + kb];
-            if (o < 0) continue;
-            const auto& K = Aket.blk[kb];
-            int lb = L.find(a, K.sl);
-            int mb = braL.sec[ysb[(size_t)a * nkb + kb]].dim;
-            int kd = ketL.sec[K.sl].dim, nd = ketR.sec[K.sr].dim;
-            int m0 = g1.mark();
-            g1.op(L.ptr(L.blk[lb]), kd, Aket.ptr(K), nd, kd, 0, 1.0);
-            g1.block(Yp + o, nd, mb, nd, 0, m0);
-        }
-    // group W entries by b
-    std::vector<std::vector<const MpoEntry*>> by_b(W.dim[site + 1]);
-    for (const auto& e : W.W[site]) by_b[e.b].push_back(&e);
-    for (const auto& nb : Lnew.blk) {
-        int m0 = g2.mark();
-        const int md = braR.sec[nb.sb].dim, nd = ketR.sec[nb.sk].dim;
-        for (const MpoEntry* e : by_b[nb.a]) {
-            const Mat4& op = W.ops[e->op];
-            for (int s = 0; s < 4; ++s)
-                for (int t = 0; t < 4; ++t) {
-                    const double v = op[s * 4 + t];
-                    if (v == 0.0) continue;
-                    int slk = ketL.find(ketR.sec[nb.sk].q - site_qn(t));
-                    if (slk < 0) continue;
-                    int kb = Aket.find(slk, t);
-                    if (kb < 0 || Aket.blk[kb].sr != nb.sk) continue;
-                    long long o = yoff[(size_t)e->a * nkb + kb];
-                    if (o < 0) continue;
-                    int slb = ysb[(size_t)e->a * nkb + kb];
-                    int bb = Abra.find(slb, s);
-                    if (bb < 0 || Abra.blk[bb].sr != nb.sb) continue;
-                    int kd = braL.sec[slb].dim;
-                    g2.op(Abra.ptr(Abra.blk[bb]), md, Yp + o, nd, kd, 1, e->coef * v);
-                }
-        }
-        g2.block(Lnew.ptr(nb), nd, md, nd, 0, m0);
     }
+    mpspt::upload(dmt, mt, st);
+    mpspt::upload(dms, ms, st);
     g1.upload(st);
     g2.upload(st);
 }
 
+// L_new[b](sb', sk') = sum_{s,t} A_bra(sl_b, s)^T [sum_a W_ab(s,t) L_a(sl_b, sl_k)] A_ket(sl_k, t)
+void EnvPlan::build_left(const MPO& W, int site, const EnvT& L, const SiteT& Abra, const SiteT& Aket,
+                         const Bond& braL, const Bond& ketL, const Bond& braR, const Bond& ketR,
+                         EnvT& Lnew, cudaStream_t st) {
+    (void)braR;
+    g1.clear();
+    g2.clear();
+    mt.clear();
+    ms.clear();
+    const int nkb = (int)Aket.blk.size();
+    // g1: Y_kb = L_panel(sl_k) A_ket(kb), (panel rows) x dim(sr_k)
+    std::vector<long long> yoff(nkb, -1);
+    size_t ys = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+        const auto& K = Aket.blk[kb];
+        if (L.prows[K.sl] == 0) continue;
+        yoff[kb] = (long long)ys;
+        ys += (size_t)L.prows[K.sl] * ketR.sec[K.sr].dim;
+    }
+    Y.ensure((ys + 1) * sizeof(double), st);
+    double* Yp = Y.as<double>();
+    for (int kb = 0; kb < nkb; ++kb) {
+        if (yoff[kb] < 0) continue;
+        const auto& K = Aket.blk[kb];
+        const int kd = ketL.sec[K.sl].dim, nd = ketR.sec[K.sr].dim, P = L.prows[K.sl];
+        const int m0 = g1.mark();
+        g1.op(L.panel(K.sl), kd, Aket.ptr(K), nd, kd, 0, 1.0);
+        g1.block(Yp + yoff[kb], nd, P, nd, 0, m0);
+    }
+    // mix: Z_(out, s) over the MPO entries e = (a -> b) and t
+    std::vector<std::vector<const MpoEntry*>> by_b(W.dim[site + 1]);
+    for (const auto& e : W.W[site]) by_b[e.b].push_back(&e);
+    struct ZB { int nb, s, bb; size_t off; int rows, cols; };
+    std::vector<ZB> zb;
+    size_t zs = 0;
+    for (int nbi = 0; nbi < (int)Lnew.blk.size(); ++nbi) {
+        const auto& nb = Lnew.blk[nbi];
+        const int nd = ketR.sec[nb.sk].dim;
+        for (int s = 0; s < 4; ++s) {
+            const int slb = braL.find(braR.sec[nb.sb].q - site_qn(s));
+            if (slb < 0) continue;
+            const int bb = Abra.find(slb, s);
+            if (bb < 0 || Abra.blk[bb].sr != nb.sb) continue;
+            const int rows = braL.sec[slb].dim;
+            const int s0 = (int)ms.size();
+            for (const MpoEntry* e : by_b[nb.a]) {
+                const Mat4& op = W.ops[e->op];
+                for (int t = 0; t < 4; ++t) {
+                    const double v = op[s * 4 + t];
+                    if (v == 0.0) continue;
+                    const int slk = ketL.find(ketR.sec[nb.sk].q - site_qn(t));
+                    if (slk < 0) continue;
+                    const int kb = Aket.find(slk, t);
+                    if (kb < 0 || Aket.blk[kb].sr != nb.sk || yoff[kb] < 0) continue;
+                    const int lb = L.find(e->a, slk);
+                    if (lb < 0 || L.blk[lb].sb != slb) continue;
+                    ms.push_back({Yp + yoff[kb] + (size_t)L.blk[lb].roff * nd, nd, 0, e->coef * v});
+                }
+            }
+            if ((int)ms.size() == s0) continue;
+            zb.push_back({nbi, s, bb, zs, rows, nd});
+            mt.push_back({nullptr, rows, nd, nd, s0, (int)ms.size(), 0});
+            zs += (size_t)rows * nd;
+        }
+    }
+    Z.ensure((zs + 1) * sizeof(double), st);
+    double* Zp = Z.as<double>();
+    for (size_t q = 0; q < zb.size(); ++q) mt[q].dst = Zp + zb[q].off;
+    // g2: L_new(out) = sum_s A_bra(sl_b, s)^T Z_(out, s)
+    size_t z = 0;
+    for (int nbi = 0; nbi < (int)Lnew.blk.size(); ++nbi) {
+        const auto& nb = Lnew.blk[nbi];
+        const int md = braR.sec[nb.sb].dim, nd = ketR.sec[nb.sk].dim;
+        const int m0 = g2.mark();
+        for (; z < zb.size() && zb[z].nb == nbi; ++z)
+            g2.op(Abra.ptr(Abra.blk[zb[z].bb]), md, Zp + zb[z].off, nd, zb[z].rows, 1, 1.0);
+        g2.block(Lnew.ptr(nb), nd, md, nd, 0, m0);
+    }
+    upload_mix(st);
+}
+
+// R_new[a](sb, sk) = sum_{s,t} A_bra(sb, s) [sum_b W_ab(s,t) R_b(sr_b, sr_k)] A_ket(sk, t)^T
 void EnvPlan::build_right(const MPO& W, int site, const EnvT& R, const SiteT& Abra, const SiteT& Aket,
                           const Bond& braL, const Bond& ketL, const Bond& braR, const Bond& ketR,
                           EnvT& Rnew, cudaStream_t st) {
     g1.clear();
     g2.clear();
-    const int nb_ = (int)W.dim[site + 1];
+    mt.clear();
+    ms.clear();
     const int nkb = (int)Aket.blk.size();
-    std::vector<long long> yoff((size_t)nb_ * nkb, -1);
-    std::vector<int> ysb((size_t)nb_ * nkb, -1);
+    // g1: Y_kb = A_ket(kb) R_panel(sr_k)^T, dim(sl_k) x (panel rows)
+    std::vector<long long> yoff(nkb, -1);
     size_t ys = 0;
-    for (int b = 0; b < nb_; ++b)
-        for (int kb = 0; kb < nkb; ++kb) {
-            const auto& K = Aket.blk[kb];
-            int rb = R.find(b, K.sr);
-            if (rb < 0) continue;
-            int sb = R.blk[rb].sb;
-            yoff[(size_t)b * nkb + kb] = (long long)ys;
-            ysb[(size_t)b * nkb + kb] = sb;
-            ys += (size_t)ketL.sec[K.sl].dim * braR.sec[sb].dim;
-        }
+    for (int kb = 0; kb < nkb; ++kb) {
+        const auto& K = Aket.blk[kb];
+        if (R.prows[K.sr] == 0) continue;
+        yoff[kb] = (long long)ys;
+        ys += (size_t)ketL.sec[K.sl].dim * R.prows[K.sr];
+    }
     Y.ensure((ys + 1) * sizeof(double), st);
     double* Yp = Y.as<double>();
-    for (int b = 0; b < nb_; ++b)
-        for (int kb = 0; kb < nkb; ++kb) {
-            long long o = yoff[(size_t)b * nkb + kb];
-            if (o < 0) continue;
-            const auto& K = Aket.blk[kb];
-            int rb = R.find(b, K.sr);
-            int nd = braR.sec[ysb[(size_t)b * nkb + kb]].dim;
-            int md = ketL.sec[K.sl].dim, kd = ketR.sec[K.sr].dim;
-            int m0 = g1.mark();
-            g1.op(Aket.ptr(K), kd, R.ptr(R.blk[rb]), kd, kd, 2, 1.0);
-            g1.block(Yp + o, nd, md, nd, 0, m0);
-        }
+    for (int kb = 0; kb < nkb; ++kb) {
+        if (yoff[kb] < 0) continue;
+        const auto& K = Aket.blk[kb];
+        const int md = ketL.sec[K.sl].dim, kd = ketR.sec[K.sr].dim, P = R.prows[K.sr];
+        const int m0 = g1.mark();
+        g1.op(Aket.ptr(K), kd, R.panel(K.sr), kd, kd, 2, 1.0);
+        g1.block(Yp + yoff[kb], P, md, P, 0, m0);
+    }
+    // mix: Z_(out, s) = sum over e = (a -> b), t of W_ab(s, t) Y_(b, kb(t)), dim(sk) x dim(sr_b)
     std::vector<std::vector<const MpoEntry*>> by_a(W.dim[site]);
     for (const auto& e : W.W[site]) by_a[e.a].push_back(&e);
-    for (const auto& nbk : Rnew.blk) {
-        int m0 = g2.mark();
-        const int md = braL.sec[nbk.sb].dim, nd = ketL.sec[nbk.sk].dim;
-        for (const MpoEntry* e : by_a[nbk.a]) {
-            const Mat4& op = W.ops[e->op];
-            for (int s = 0; s < 4; ++s)
+    struct ZB { int nb, s, bb; size_t off; int rows, cols; };
+    std::vector<ZB> zb;
+    size_t zs = 0;
+    for (int nbi = 0; nbi < (int)Rnew.blk.size(); ++nbi) {
+        const auto& nbk = Rnew.blk[nbi];
+        const int nd = ketL.sec[nbk.sk].dim;
+        for (int s = 0; s < 4; ++s) {
+            const int bb = Abra.find(nbk.sb, s);
+            if (bb < 0) continue;
+            const int srb = Abra.blk[bb].sr;
+            const int cols = braR.sec[srb].dim;
+            const int s0 = (int)ms.size();
+            for (const MpoEntry* e : by_a[nbk.a]) {
+                const Mat4& op = W.ops[e->op];
                 for (int t = 0; t < 4; ++t) {
                     const double v = op[s * 4 + t];
                     if (v == 0.0) continue;
-                    int kb = Aket.find(nbk.sk, t);
-                    if (kb < 0) continue;
-                    long long o = yoff[(size_t)e->b * nkb + kb];
-                    if (o < 0) continue;
-                    int srb = ysb[(size_t)e->b * nkb + kb];
-                    int bb = Abra.find(nbk.sb, s);
-                    if (bb < 0 || Abra.blk[bb].sr != srb) continue;
-                    int kd = braR.sec[srb].dim;
-                    g2.op(Abra.ptr(Abra.blk[bb]), kd, Yp + o, kd, kd, 2, e->coef * v);
+                    const int kb = Aket.find(nbk.sk, t);
+                    if (kb < 0 || yoff[kb] < 0) continue;
+                    const int srk = Aket.blk[kb].sr;
+                    const int rb = R.find(e->b, srk);
+                    if (rb < 0 || R.blk[rb].sb != srb) continue;
+                    ms.push_back({Yp + yoff[kb] + R.blk[rb].roff, R.prows[srk], 0, e->coef * v});
                 }
+            }
+            if ((int)ms.size() == s0) continue;
+            zb.push_back({nbi, s, bb, zs, nd, cols});
+            mt.push_back({nullptr, nd, cols, cols, s0, (int)ms.size(), 0});
+            zs += (size_t)nd * cols;
         }
+    }
+    Z.ensure((zs + 1) * sizeof(double), st);
+    double* Zp = Z.as<double>();
+    for (size_t q = 0; q < zb.size(); ++q) mt[q].dst = Zp + zb[q].off;
+    // g2: R_new(out) = sum_s A_bra(sb, s) Z_(out, s)^T
+    size_t z = 0;
+    for (int nbi = 0; nbi < (int)Rnew.blk.size(); ++nbi) {
+        const auto& nbk = Rnew.blk[nbi];
+        const int md = braL.sec[nbk.sb].dim, nd = ketL.sec[nbk.sk].dim;
+        const int m0 = g2.mark();
+        for (; z < zb.size() && zb[z].nb == nbi; ++z)
+            g2.op(Abra.ptr(Abra.blk[zb[z].bb]), zb[z].cols, Zp + zb[z].off, zb[z].cols, zb[z].cols, 2, 1.0);
         g2.block(Rnew.ptr(nbk), nd, md, nd, 0, m0);
     }
-    g1.upload(st);
-    g2.upload(st);
+    upload_mix(st);
 }
 
 }  // namespace mpspt

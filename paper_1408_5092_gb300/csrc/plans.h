@@ -112,17 +112,31 @@ void plan_product(GemmPlan& g, const TwoT& x, double* xd, const Bond& mid, const
                   const SiteT& B, const Bond& L);
 
 // Left transfer: Lnew_b = sum (a,s,t) W_ab[s,t] Abra(s)^T L_a Aket(t); Y scratch.
+// Environment update in three steps (the same scheme as sigma):
+//   g1:  Y_kb = L_panel(ket sector of kb) A_ket(kb)     one GEMM per ket block
+//        (right update: Y_kb = A_ket(kb) R_panel^T)
+//   mix: Z_(out, s) = sum over MPO entries and t of W_ab(s, t) Y_(a, kb(t))
+//   g2:  L_new(out) = sum_s A_bra(s)^T Z_(out, s)          (<= 4 products)
 struct EnvPlan {
     GemmPlan g1, g2;
-    DBuf Y;
+    DBuf Y, Z, dmt, dms;
+    std::vector<MixTask> mt;
+    std::vector<MixSrc> ms;
     void build_left(const MPO& W, int site, const EnvT& L, const SiteT& Abra, const SiteT& Aket,
                     const Bond& braL, const Bond& ketL, const Bond& braR, const Bond& ketR,
                     EnvT& Lnew, cudaStream_t st);
     void build_right(const MPO& W, int site, const EnvT& R, const SiteT& Abra, const SiteT& Aket,
                      const Bond& braL, const Bond& ketL, const Bond& braR, const Bond& ketR,
                      EnvT& Rnew, cudaStream_t st);
-    void run(cudaStream_t st) const { g1.run(st); g2.run(st); }
+    void run(cudaStream_t st) const {
+        g1.run(st);
+        launch_mix(dmt.as<MixTask>(), (int)mt.size(), dms.as<MixSrc>(), st);
+        g2.run(st);
+    }
     double flops() const { return g1.flops + g2.flops; }
+
+  private:
+    void upload_mix(cudaStream_t st);
 };
 
 }  // namespace mpspt

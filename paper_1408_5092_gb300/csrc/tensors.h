@@ -35,11 +35,16 @@ struct SiteT {
 };
 
 // Environment (renormalised operators) at one cut for an MPO with state QN
-// changes dq: blocks (a, sb, sk) with q_bra(sb) = q_ket(sk) + dq[a].
+// changes dq: blocks (a, sb, sk) with q_bra(sb) = q_ket(sk) + dq[a].  Blocks
+// are stored ket sector by ket sector (a inner), so all blocks on one ket
+// sector form one tall row-major panel (rows: the bra blocks of every a,
+// width: dim(sk)); poff / prows give the panels, roff a block's first row.
 struct EnvT {
-    struct B { int a, sb, sk; size_t off; };
+    struct B { int a, sb, sk; size_t off; int roff; };
     std::vector<B> blk;
     std::vector<int> idx;   // a*nsk + sk -> block or -1
+    std::vector<size_t> poff;
+    std::vector<int> prows;
     int nsk = 0;
     size_t n = 0;
     DBuf d;
@@ -47,19 +52,25 @@ struct EnvT {
         blk.clear();
         nsk = ket.nsec();
         idx.assign(dq.size() * (size_t)nsk, -1);
+        poff.assign(nsk, 0);
+        prows.assign(nsk, 0);
         n = 0;
-        for (int a = 0; a < (int)dq.size(); ++a)
-            for (int sk = 0; sk < nsk; ++sk) {
+        for (int sk = 0; sk < nsk; ++sk) {
+            poff[sk] = n;
+            for (int a = 0; a < (int)dq.size(); ++a) {
                 int sb = bra.find(ket.sec[sk].q + dq[a]);
                 if (sb < 0) continue;
                 idx[(size_t)a * nsk + sk] = (int)blk.size();
-                blk.push_back({a, sb, sk, n});
+                blk.push_back({a, sb, sk, n, prows[sk]});
                 n += (size_t)bra.sec[sb].dim * ket.sec[sk].dim;
+                prows[sk] += bra.sec[sb].dim;
             }
+        }
         d.alloc(n * sizeof(double) + 8, st);
     }
     int find(int a, int sk) const { return idx[(size_t)a * nsk + sk]; }
     double* ptr(const B& b) const { return d.as<double>() + b.off; }
+    double* panel(int sk) const { return d.as<double>() + poff[sk]; }
 };
 
 // Two-site tensor x[l, s1, s2, r]: blocks (sl, s1, s2) -> sr, stored in

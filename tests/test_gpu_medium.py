@@ -82,13 +82,21 @@ def test_medium_local_operators(medium, h0):
     L.mpspt_destroy(ctx)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 1e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 3e-8), ("mixed", 1e-6)])
 def test_medium_e2_per_sweep_matches_oracle(medium, prec, tol):
     """E2 after each of the first sweeps at M = 64 (Fock H0) against the
     oracle's sweep history from the same seeded initial Psi1
     (tests/golden/oracle_medium_fock_M64.json, written by make_golden.py).
-    M = 64 truncates strongly (discarded weight ~4e-2) and converges slowly,
-    so the comparison is per sweep, not on a converged value."""
+    M = 64 truncates strongly (discarded weight ~6e-2) and converges slowly,
+    so the comparison is per sweep, not on a converged value.
+
+    Tolerance: this case is ill-conditioned.  Truncating at a cut with close
+    density-matrix eigenvalues amplifies rounding-level changes of the
+    inputs.  In the oracle, a 1e-14 relative perturbation of Psi0 moves the
+    first-sweep E2 by 9e-9 (and by 3e-9 / 1e-9 after sweeps 2 / 3).  Psi0
+    itself comes from an iterative eigensolver reproducible to that level
+    across machines, so float64 parity is held at 3e-8 here; the tiny
+    system's converged energies are held at 1e-8."""
     import json
     import os
     from paper_1408_5092_gb300 import _lib as L
