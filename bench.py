@@ -210,7 +210,7 @@ def run_gpu(args):
     o.stream = stream.cuda_stream
     o.prec = L.PREC[args.prec]
     o.e_tol = args.e_tol
-    o.max_sweeps = 64
+    o.max_sweeps = args.max_sweeps
     ctx = L.mpspt_create(o)
     L.mpspt_set_integrals(ctx, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
     L.mpspt_set_reference(ctx, ci)
@@ -229,7 +229,7 @@ def run_gpu(args):
     o64.stream = stream.cuda_stream
     o64.prec = L.MPSPT_FP64
     o64.e_tol = args.ref_e_tol
-    o64.max_sweeps = 64
+    o64.max_sweeps = args.max_sweeps
     ctx64 = L.mpspt_create(o64)
     L.mpspt_set_integrals(ctx64, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
     L.mpspt_set_reference(ctx64, ci)
@@ -356,6 +356,8 @@ def main():
     ap.add_argument("--ref_sweeps", type=int, default=10)
     ap.add_argument("--ref_cg", type=float, default=6.0)
     ap.add_argument("--no_cpu_baseline", action="store_true")
+    ap.add_argument("--max_sweeps", type=int, default=64,
+                    help="sweep cap of every minimisation (a smaller workload, e.g. for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

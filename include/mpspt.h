@@ -25,6 +25,9 @@
  * mpspt_status_string() gives a message.  All device work is ordered on the
  * stream given in mpspt_options (0 = the legacy default stream); every call
  * returns only after its host-visible results are final.
+ * Device memory: allocated stream-ordered from the device's default memory
+ * pool; the library raises that pool's release threshold so freed memory
+ * stays cached in this process between calls (cudaMemPoolTrimTo returns it).
  * Ownership: input arrays are copied, the caller keeps them.  Handles
  * (mpspt_ctx, mpspt_mps) are owned by the caller and released with
  * mpspt_destroy / mpspt_mps_free.

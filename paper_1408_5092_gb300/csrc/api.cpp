@@ -313,6 +313,7 @@ mpspt_status mpspt_eigh_batched_ex(int device, void* stream, int batch, const in
     if (batch < 1 || !n || !A || !V || !w) return MPSPT_ERR_INVALID;
     return guard(nullptr, [&] {
         MPSPT_CUDA(cudaSetDevice(device));
+        mpspt::keep_pool_memory(device);
         cudaStream_t st = static_cast<cudaStream_t>(stream);
         size_t tot = 0, totw = 0;
         for (int i = 0; i < batch; ++i) {

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <stdexcept>
@@ -88,15 +89,30 @@ struct Bond {
 struct Registry {
     std::mutex mu;
     std::map<uintptr_t, size_t> live;
+    std::atomic<unsigned long long> gen{0};   // bumped by every release
     static Registry& get() { static Registry r; return r; }
     void add(const void* p, size_t n) { std::lock_guard<std::mutex> g(mu); live[(uintptr_t)p] = n; }
-    void remove(const void* p) { std::lock_guard<std::mutex> g(mu); live.erase((uintptr_t)p); }
-    bool contains(const void* p, size_t bytes) {
+    void remove(const void* p) {
         std::lock_guard<std::mutex> g(mu);
-        auto it = live.upper_bound((uintptr_t)p);
+        live.erase((uintptr_t)p);
+        gen.fetch_add(1, std::memory_order_relaxed);
+    }
+    bool contains(const void* p, size_t bytes) {
+        // planners check long runs of ranges inside one allocation: the last
+        // hit is remembered per thread until an allocation is released
+        thread_local uintptr_t c0 = 0, c1 = 0;
+        thread_local unsigned long long cg = ~0ULL;
+        const uintptr_t a = (uintptr_t)p, b = a + bytes;
+        if (cg == gen.load(std::memory_order_relaxed) && a >= c0 && b <= c1) return true;
+        std::lock_guard<std::mutex> g(mu);
+        auto it = live.upper_bound(a);
         if (it == live.begin()) return false;
         --it;
-        return (uintptr_t)p >= it->first && (uintptr_t)p + bytes <= it->first + it->second;
+        if (!(a >= it->first && b <= it->first + it->second)) return false;
+        c0 = it->first;
+        c1 = it->first + it->second;
+        cg = gen.load(std::memory_order_relaxed);
+        return true;
     }
 };
 
@@ -110,6 +126,18 @@ inline void check_range(const void* p, size_t bytes, const char* what) {
     if (!checks_enabled() || bytes == 0) return;
     if (!Registry::get().contains(p, bytes))
         throw Error(MPSPT_ERR_INVALID, std::string("planner bounds check failed: ") + what);
+}
+
+// The library allocates from the device's default memory pool.  Its release
+// threshold is raised so that freed blocks stay cached in the pool across
+// stream synchronisations (by default they return to the driver at every
+// sync and the next allocations remap them, which dominated planning time).
+// This is a property of this process's pool, not a device setting.
+inline void keep_pool_memory(int device) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) != cudaSuccess) return;
+    unsigned long long thr = ~0ULL;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
 }
 
 // Stream-ordered device allocation (cudaMallocAsync), released on the same

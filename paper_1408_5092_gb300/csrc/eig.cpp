@@ -8,6 +8,7 @@ namespace {
 constexpr int kMaxSweepsF64 = 40;      // float64 Jacobi from the identity
 constexpr int kMaxSweepsF32 = 12;      // float32 start
 constexpr int kMaxSweepsPolish = 16;   // float64 polish of V^T A V
+constexpr int kClusterMinN = 48;       // float64 sweeps on CTA clusters from this size
 size_t a16(size_t b) { return (b + 15) & ~(size_t)15; }
 }  // namespace
 
@@ -43,10 +44,28 @@ void EigSolver::jacobi(const std::vector<EigTask>& et, const std::vector<const d
             smem = std::max(smem, nr * (n | 1) * (f32 ? 4 : 8));
         }
     }
+    // float64 sweeps of larger matrices run on clusters of 8 CTAs (one SM's
+    // float64 pipe is the limit); the rest on one CTA each.  Both kernels do
+    // the same arithmetic per entry.
+    std::vector<JacTask> one, clu;
+    int csm = 0;
+    for (int i = 0; i < nt; ++i) {
+        const int cs = f32 ? 0 : jac_cluster_smem(et[i].n);
+        if (et[i].n >= kClusterMinN && cs > 0) {
+            clu.push_back(jt[i]);
+            csm = std::max(csm, cs);
+        } else {
+            one.push_back(jt[i]);
+        }
+    }
+    // the apply blocks index the full task list
     upload(djt, jt, st);
     upload(drows, rows, st);
+    if (!one.empty()) upload(djt1, one, st);
+    if (!clu.empty()) upload(djtc, clu, st);
     for (int s = 0; s <= maxs; ++s) {
-        launch_jac_sweep(djt.as<JacTask>(), nt, s, maxs, f32, st);
+        if (!one.empty()) launch_jac_sweep(djt1.as<JacTask>(), (int)one.size(), s, maxs, f32, st);
+        if (!clu.empty()) launch_jac_sweep_cluster(djtc.as<JacTask>(), (int)clu.size(), s, maxs, csm, st);
         if (s < maxs) launch_jac_apply(djt.as<JacTask>(), drows.as<JacRows>(), (int)rows.size(), smem, s, f32, st);
     }
 }

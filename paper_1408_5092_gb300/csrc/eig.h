@@ -10,7 +10,7 @@
 namespace mpspt {
 
 struct EigSolver {
-    DBuf scratch, vt, g, djt, drows, dtns;
+    DBuf scratch, vt, g, djt, djt1, djtc, drows, dtns;
     GemmPlan ge;   // batched square GEMMs of the float64 stage
 
     // For every task: A (n x n, symmetric, left unchanged) -> V (eigenvectors

@@ -40,6 +40,7 @@ Lane::~Lane() {
 
 Ctx::Ctx(const mpspt_options& o) : opt(o) {
     MPSPT_CUDA(cudaSetDevice(o.device));
+    keep_pool_memory(o.device);
     st = static_cast<cudaStream_t>(o.stream);
     lane0.reset(new Lane(st));
     red.alloc(4 * 1024 * sizeof(double), st);
@@ -758,7 +759,9 @@ struct Sweeper {
         }
         std::vector<double> wh(wsz);
         if (wsz) MPSPT_CUDA(cudaMemcpyAsync(wh.data(), wv.get(), wsz * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
+        auto ts = clk::now();
         MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        split_wait += since(ts);
         // selection: keep the Mkeep largest (ties at the cut dropped as a group)
         struct Cand { double lam; int ci; int rank; int col; };
         std::vector<Cand> cand;
@@ -885,7 +888,6 @@ struct Sweeper {
         }
         psi.A[i] = std::move(An);
         psi.A[i + 1] = std::move(Bn);
-        MPSPT_CUDA(cudaStreamSynchronize(ln.st));   // plans above reference host vectors
         return tr > 0 ? std::max(0.0, (tr - kept_w) / tr) : 0.0;
     }
 
@@ -1151,12 +1153,15 @@ struct Sweeper {
     int eig_nmax = 0, eig_calls = 0;
     cudaEvent_t sev[4], pev[4];
     double t_rhs_dev = 0, t_env_dev = 0, rhs_gf = 0, env_gf = 0;   // verbose >= 3
+    double h_prod = 0, h_rhs = 0, h_sig = 0, h_split = 0, h_env = 0;   // host-only ms
+    double split_wait = 0;
     using clk = std::chrono::steady_clock;
     static double since(clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); }
 
     double step(int i, int dir) {
         auto t0 = clk::now();
         const Bond &bL = psi.bond[i], &bR = psi.bond[i + 2];
+        auto th = clk::now();
         X.build(bL, bR, filt[i + 1]);
         X0.build(psi0.bond[i], psi0.bond[i + 2], {});
         const size_t n = X.n;
@@ -1164,15 +1169,18 @@ struct Sweeper {
         double* x = w.x.as<double>();
         product(prod, psi, i, X, x);
         product(prod0, psi0, i, X0, w.x0.as<double>());
+        h_prod += since(th); th = clk::now();
         const Omega& oA = omega(omA_c, WA, i);
         const Omega& oV = omega(omV_c, WV, i);
         rhs.build(oV, X, X0, bL, psi0.bond[i], bR, psi0.bond[i + 2], LV[i], RV[i + 2], WV.dq[i + 2],
                   w.x0.as<double>(), w.g.as<double>(), ln.st);
+        h_rhs += since(th);
         if (c.opt.verbose >= 3) MPSPT_CUDA(cudaEventRecord(pev[0], ln.st));
         rhs.run(ln.st);
         if (c.opt.verbose >= 3) { MPSPT_CUDA(cudaEventRecord(pev[1], ln.st)); rhs_gf += rhs.flops() * 1e-9; }
         if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_rhs += since(t0); t0 = clk::now(); }
         if (c.opt.verbose >= 3) { float a; cudaEventElapsedTime(&a, pev[0], pev[1]); t_rhs_dev += a; }
+        th = clk::now();
         sig.build(oA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
                   w.Ap.as<double>(), ln.st);
         dia.build(oA, X, bL, bR, LA[i], RA[i + 2], WA.dq[i], WA.dq[i + 2], w.dg.as<double>(), ln.st);
@@ -1186,19 +1194,25 @@ struct Sweeper {
         if (lo_kind != GEMM_F64)
             sig_lo.build(oA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
                          w.Ap.as<double>(), ln.st);
+        h_sig += since(th);
         if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_plan += since(t0); t0 = clk::now(); }
         if (c.net != nullptr && c.opt.use_learned && !c.harvesting) learned_guess(n);
         const double h = (lo_kind == GEMM_F64) ? solve_plain(n) : solve_refined(n);
         check_tc();
         if (c.harvesting) harvest(n);
         if (c.opt.verbose >= 2) { t_solve += since(t0); t0 = clk::now(); }
+        th = clk::now();
+        const double w0 = split_wait;
         const double disc = split(i, dir, M, X, x);
+        h_split += since(th) - (split_wait - w0);
         res->max_disc = std::max(res->max_disc, disc);
         res->max_bond = std::max(res->max_bond, psi.bond[i + 1].total);
         if (c.opt.verbose >= 2) { t_split += since(t0); t0 = clk::now(); }
         if (c.opt.verbose >= 3) MPSPT_CUDA(cudaEventRecord(pev[2], ln.st));
+        th = clk::now();
         if (dir == 0) update_left(i);
         else update_right(i + 1);
+        h_env += since(th);
         if (c.opt.verbose >= 3) { MPSPT_CUDA(cudaEventRecord(pev[3], ln.st)); env_gf += env_flops * 1e-9; }
         if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_env += since(t0); }
         if (c.opt.verbose >= 3) { float a; cudaEventElapsedTime(&a, pev[2], pev[3]); t_env_dev += a; }
@@ -1265,11 +1279,15 @@ std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res,
         if (c.opt.verbose >= 2)
             fprintf(stderr, "[mpspt]   host ms: rhs %.1f plan %.1f solve %.1f split %.1f env %.1f | sigma dev ms %.1f (64: %.1f)\n",
                     sw.t_rhs, sw.t_plan, sw.t_solve, sw.t_split, sw.t_env, res.sigma_ms, res.sigma64_ms);
-        if (c.opt.verbose >= 3)
+        if (c.opt.verbose >= 3) {
             fprintf(stderr, "[mpspt]   split dev ms: rho %.1f eig %.1f post %.1f | eig tasks %d nmax %d sum n^3 %.3g\n",
                     sw.t_rho, sw.t_eig, sw.t_post, sw.eig_calls, sw.eig_nmax, sw.eig_n3);
             fprintf(stderr, "[mpspt]   rhs dev ms %.1f (%.1f GF) env dev ms %.1f (%.1f GF)\n", sw.t_rhs_dev, sw.rhs_gf,
                     sw.t_env_dev, sw.env_gf);
+        }
+        if (c.opt.verbose == 1)
+            fprintf(stderr, "[mpspt]   host-only ms: layouts+products %.1f rhs-plan %.1f sigma-plans %.1f split-host %.1f env-plans %.1f\n",
+                    sw.h_prod, sw.h_rhs, sw.h_sig, sw.h_split, sw.h_env);
         if (s > 0 && std::fabs(e - prev) < c.opt.e_tol) break;
         prev = e;
     }

@@ -131,6 +131,9 @@ size_t jac_p_bytes(int n);
 size_t jac_rot_bytes(int n);
 int jac_rows_per_block(int n, bool f32);
 void launch_jac_sweep(const JacTask* tasks, int ntask, int sweep, int maxs, bool f32, cudaStream_t st);
+// float64 sweep by clusters of 8 CTAs per matrix (distributed shared memory)
+int jac_cluster_smem(int n);
+void launch_jac_sweep_cluster(const JacTask* tasks, int ntask, int sweep, int maxs, int smem, cudaStream_t st);
 void launch_jac_apply(const JacTask* tasks, const JacRows* rows, int nblocks, int smem, int sweep, bool f32,
                       cudaStream_t st);
 void launch_ns_prep(const EigTask* tasks, int ntask, cudaStream_t st);

@@ -10,7 +10,7 @@
 // (R_k^T A_kl R_l; the symmetric partner is implied).  The applied rotations
 // of each round are recorded, compacted, in the task's rotation list.
 //
-// k_jac_apply (one warp per block of up to 32 rows of V): V <- V R for the
+// k_jac_apply (one warp per block of rows of V): V <- V R for the
 // recorded rotations, in order.  A row of V is touched independently of the
 // others, so each lane owns one row in shared memory and runs through the
 // whole list without synchronisation; the work spreads over many SMs.
@@ -20,6 +20,8 @@
 // written) when off^2 <= STOP * |A|_F^2, when a small off-norm stalled at
 // the rounding floor, or at sweep maxs; later launches for that task return
 // at once.
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace mpspt {
@@ -190,6 +192,172 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
         for (size_t e = tid; e < np; e += JAC_THREADS) Pg[e] = P[e];
 }
 
+// Float64 sweep of one matrix by a cluster of JC CTAs (distributed shared
+// memory).  Packed entry e lives in CTA e mod JC at slot e / JC.  Every CTA
+// computes all rotations of a round from the distributed entries; the 2x2
+// blocks {k, l} (k <= l) are split by k mod JC, so each CTA does 1/JC of the
+// float64 update work on its own SM.  Two cluster barriers per round keep
+// the pair phase and the update phase apart.  The arithmetic per entry is
+// the single-CTA kernel's; only rank 0 records rotations and flags.
+constexpr int JC = 8;
+
+template <class T>
+__global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
+    k_jac_sweep_cl(const JacTask* __restrict__ tasks, int sweep, int maxs) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red[2][JAC_THREADS / 32];
+    __shared__ double part[2][JC];
+    __shared__ int stop, cnt;
+    const int rank = (int)cl.block_rank();
+    const JacTask t = tasks[blockIdx.x / JC];
+    if (sweep > 0 && *(volatile const int*)t.done) return;   // same value in every CTA of the cluster
+    const int n = t.n;
+    const int m = n + (n & 1), half = m / 2;
+    const size_t np = (size_t)n * (n + 1) / 2;
+    const size_t nloc = (np + JC - 1) / JC;
+    int* rowoff = reinterpret_cast<int*>(sm);
+    int* Pp = rowoff + n;
+    int* Qq = Pp + half;
+    T* Cc = reinterpret_cast<T*>(sm + align16((size_t)n * 4 + 2 * (size_t)half * 4));
+    T* Ss = Cc + half;
+    T* Ploc = reinterpret_cast<T*>(sm + jac_head_bytes<T>(n));
+    T* Pg = reinterpret_cast<T*>(t.P);
+    int* rcount = reinterpret_cast<int*>(t.rot);
+    RotE<T>* rlist = reinterpret_cast<RotE<T>*>(reinterpret_cast<unsigned char*>(t.rot) + align16((size_t)(m - 1) * 4));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = JAC_THREADS / 32;
+    for (int i = tid; i < n; i += JAC_THREADS) rowoff[i] = i * n - i * (i + 1) / 2;
+    __syncthreads();
+    if (sweep == 0) {
+        for (int i = warp; i < n; i += nw)
+            for (int j = i + lane; j < n; j += 32) {
+                const size_t e = (size_t)rowoff[i] + j;
+                if ((int)(e % JC) == rank) Ploc[e / JC] = (T)t.A[(size_t)i * n + j];
+            }
+    } else {
+        for (size_t q = tid; q < nloc; q += JAC_THREADS) {
+            const size_t e = q * JC + rank;
+            if (e < np) Ploc[q] = Pg[e];
+        }
+    }
+    cl.sync();   // every CTA of the cluster is running and has its slice before any remote access
+    auto S = [&](int a, int b) -> T& {
+        const size_t e = a <= b ? (size_t)rowoff[a] + b : (size_t)rowoff[b] + a;
+        return cl.map_shared_rank(Ploc, (int)(e % JC))[e / JC];
+    };
+    // convergence test over the whole matrix (partial sums gathered in rank 0)
+    {
+        double off = 0.0, all = 0.0;
+        for (int i = warp; i < n; i += nw)
+            for (int j = i + lane; j < n; j += 32) {
+                const size_t e = (size_t)rowoff[i] + j;
+                if ((int)(e % JC) != rank) continue;
+                const double v = (double)Ploc[e / JC];
+                if (j == i) all += v * v;
+                else off += 2.0 * v * v;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            all += __shfl_xor_sync(0xffffffffu, all, o);
+        }
+        if (lane == 0) { red[0][warp] = off; red[1][warp] = all; }
+        __syncthreads();
+        if (tid == 0) {
+            double so = 0.0, sd = 0.0;
+            for (int w = 0; w < nw; ++w) { so += red[0][w]; sd += red[1][w]; }
+            double* p0 = cl.map_shared_rank(&part[0][0], 0);
+            p0[rank] = so;
+            p0[JC + rank] = sd;
+        }
+        cl.sync();
+        if (rank == 0 && tid == 0) {
+            double so = 0.0, sd = 0.0;
+            for (int r = 0; r < JC; ++r) { so += part[0][r]; sd += part[1][r]; }
+            const double sa = so + sd;
+            const double prev = sweep == 0 ? 1e300 : *t.prev;
+            const int s = (so <= JacTol<T>::stop * sa) || sa == 0.0 || (so <= 1e-8 * sa && so > 0.81 * prev) ||
+                          sweep >= maxs || n < 2;
+            *t.prev = so;
+            *t.done = s;
+            for (int r = 0; r < JC; ++r) *cl.map_shared_rank(&stop, r) = s;
+        }
+        cl.sync();
+    }
+    if (stop) {
+        if (t.w)
+            for (int i = tid; i < n; i += JAC_THREADS) {
+                const size_t e = (size_t)rowoff[i] + i;
+                if ((int)(e % JC) == rank) t.w[i] = (double)Ploc[e / JC];
+            }
+        return;
+    }
+    constexpr T SKIP = (T)JacTol<T>::skip;
+    for (int r = 0; r < m - 1; ++r) {
+        if (tid == 0) cnt = 0;
+        __syncthreads();
+        for (int k = tid; k < half; k += JAC_THREADS) {
+            int pa, pb;
+            rr_pair(k, r, m, pa, pb);
+            int p = min(pa, pb), q = max(pa, pb);
+            T c = T(1), s = T(0);
+            if (q < n) {
+                const T apq = S(p, q), app = S(p, p), aqq = S(q, q);
+                if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && apq != T(0)) {
+                    const T th = (aqq - app) / (T(2) * apq);
+                    const T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+                    c = T(1) / sqrt(tt * tt + T(1));
+                    s = tt * c;
+                }
+            } else {
+                q = -1;
+            }
+            Pp[k] = p; Qq[k] = q; Cc[k] = c; Ss[k] = s;
+            if (rank == 0 && s != T(0)) {
+                const int slot = atomicAdd(&cnt, 1);
+                rlist[(size_t)r * half + slot] = RotE<T>{c, s, p, q};
+            }
+        }
+        __syncthreads();
+        if (rank == 0 && tid == 0) rcount[r] = cnt;
+        cl.sync();   // every CTA has read the pair entries before any is updated
+        for (int k = rank + JC * warp; k < half; k += JC * nw) {
+            const int p = Pp[k], q = Qq[k];
+            const T ck = Cc[k], sk = Ss[k];
+            for (int l = k + lane; l < half; l += 32) {
+                const T cl_ = Cc[l], sl = Ss[l];
+                if (sk == T(0) && sl == T(0)) continue;
+                if (l == k) {
+                    const T app = S(p, p), apq = S(p, q), aqq = S(q, q);
+                    const T r_pp = ck * app - sk * apq, r_pq = ck * apq - sk * aqq;
+                    const T r_qp = sk * app + ck * apq, r_qq = sk * apq + ck * aqq;
+                    S(p, p) = ck * r_pp - sk * r_pq;
+                    S(q, q) = sk * r_qp + ck * r_qq;
+                    S(p, q) = T(0);
+                    continue;
+                }
+                const int u = Pp[l], v = Qq[l];
+                const bool hq = q >= 0, hv = v >= 0;
+                const T a_pu = S(p, u);
+                const T a_pv = hv ? S(p, v) : T(0);
+                const T a_qu = hq ? S(q, u) : T(0);
+                const T a_qv = (hq && hv) ? S(q, v) : T(0);
+                const T r_pu = ck * a_pu - sk * a_qu, r_qu = sk * a_pu + ck * a_qu;
+                const T r_pv = ck * a_pv - sk * a_qv, r_qv = sk * a_pv + ck * a_qv;
+                S(p, u) = cl_ * r_pu - sl * r_pv;
+                if (hv) S(p, v) = sl * r_pu + cl_ * r_pv;
+                if (hq) S(q, u) = cl_ * r_qu - sl * r_qv;
+                if (hq && hv) S(q, v) = sl * r_qu + cl_ * r_qv;
+            }
+        }
+        cl.sync();   // updates visible to every CTA before the next pair phase
+    }
+    for (size_t q = tid; q < nloc; q += JAC_THREADS) {
+        const size_t e = q * JC + rank;
+        if (e < np) Pg[e] = Ploc[q];
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(32) k_jac_apply(const JacTask* __restrict__ tasks, const JacRows* __restrict__ rb,
                                                  int sweep) {
@@ -252,10 +420,14 @@ size_t jac_rot_bytes(int n) {
     const int m = n + (n & 1), half = m / 2;
     return align16((size_t)(m - 1) * 4) + (size_t)(m - 1) * half * sizeof(RotE<double>);
 }
+// Rows of V per apply block (one warp).  float64 lanes issue at a small
+// fraction of the float32 rate, so a float64 block takes 8 rows: the same
+// work spreads over 4x more SMs and each warp instruction has 8 active lanes.
 int jac_rows_per_block(int n, bool f32) {
     const size_t row = (size_t)(n | 1) * (f32 ? 4 : 8);
     const size_t r = (size_t)JAC_SMEM / row;
-    return (int)(r < 32 ? (r < 1 ? 1 : r) : 32);
+    const size_t cap = f32 ? 32 : 8;
+    return (int)(r < cap ? (r < 1 ? 1 : r) : cap);
 }
 
 static void jac_attributes() {
@@ -275,6 +447,24 @@ void launch_jac_sweep(const JacTask* tasks, int ntask, int sweep, int maxs, bool
     count_launch();
     if (f32) k_jac_sweep<float><<<ntask, JAC_THREADS, JAC_SMEM, st>>>(tasks, sweep, maxs);
     else k_jac_sweep<double><<<ntask, JAC_THREADS, JAC_SMEM, st>>>(tasks, sweep, maxs);
+}
+
+// Shared memory of the cluster sweep for an n x n matrix (0: does not fit).
+int jac_cluster_smem(int n) {
+    const size_t np = (size_t)n * (n + 1) / 2;
+    const size_t b = jac_head_bytes<double>(n) + (np + JC - 1) / JC * sizeof(double);
+    return b <= (size_t)JAC_SMEM ? (int)b : 0;
+}
+
+void launch_jac_sweep_cluster(const JacTask* tasks, int ntask, int sweep, int maxs, int smem, cudaStream_t st) {
+    if (ntask <= 0) return;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_jac_sweep_cl<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, JAC_SMEM);
+        attr = true;
+    }
+    count_launch();
+    k_jac_sweep_cl<double><<<ntask * JC, JAC_THREADS, smem, st>>>(tasks, sweep, maxs);
 }
 
 void launch_jac_apply(const JacTask* tasks, const JacRows* rows, int nblocks, int smem, int sweep, bool f32,
