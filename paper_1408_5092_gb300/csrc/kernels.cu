@@ -16,6 +16,32 @@ inline void counted() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 constexpr int TK = 16;
 constexpr int NT = 256;
 
+// float64 operand -> arithmetic type.  To float32 the rounding is done with
+// integer operations: the float64 pipe of this GPU is narrow and the
+// conversion instruction would bound the tile staging.  Magnitudes below
+// the float32 normal range become signed zero.
+__device__ __forceinline__ float d2f_rn(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+    if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+    const int fe = e - 1023 + 127;
+    if (fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+    const unsigned mant = (unsigned)(m >> 29);
+    const unsigned rem = (unsigned)(m & 0x1FFFFFFFULL);
+    unsigned f = sign | ((unsigned)fe << 23) | mant;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) f += 1u;
+    return __uint_as_float(f);
+}
+template <class U>
+__device__ __forceinline__ U conv(double v);
+template <>
+__device__ __forceinline__ double conv<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float conv<float>(double v) { return d2f_rn(v); }
+
 // Grouped GEMM: one CTA per output tile, looping over the tile's K-list.
 // 16x16 threads; thread (tx, ty) owns rows ty + 16 i (i < TM/16) and
 // cols tx + 16 j (j < TN/16).  T: storage type, U: arithmetic type.
@@ -39,30 +65,30 @@ __global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks,
     for (int o = t.op0; o < t.op1; ++o) {
         const Op op = ops[o];
         const bool ta = op.trans & 1, tb = op.trans & 2;
+        const U alpha = conv<U>(op.alpha);
         for (int k0 = 0; k0 < op.k; k0 += TK) {
             const int krem = min(TK, op.k - k0);
             for (int e = threadIdx.x; e < TM * TK; e += NT) {
                 int i, kk;
                 if (ta) { i = e % TM; kk = e / TM; }
                 else { kk = e % TK; i = e / TK; }
-                T v = T(0);
+                U v = U(0);
                 if (i < mrem && kk < krem) {
                     const int row = t.r0 + i, kg = k0 + kk;
-                    v = ta ? op.A[(size_t)kg * op.lda + row] : op.A[(size_t)row * op.lda + kg];
-                    v *= op.alpha;
+                    v = conv<U>(ta ? op.A[(size_t)kg * op.lda + row] : op.A[(size_t)row * op.lda + kg]) * alpha;
                 }
-                As[kk][i] = (U)v;
+                As[kk][i] = v;
             }
             for (int e = threadIdx.x; e < TN * TK; e += NT) {
                 int j, kk;
                 if (tb) { kk = e % TK; j = e / TK; }
                 else { j = e % TN; kk = e / TN; }
-                T v = T(0);
+                U v = U(0);
                 if (j < nrem && kk < krem) {
                     const int col = t.c0 + j, kg = k0 + kk;
-                    v = tb ? op.B[(size_t)col * op.ldb + kg] : op.B[(size_t)kg * op.ldb + col];
+                    v = conv<U>(tb ? op.B[(size_t)col * op.ldb + kg] : op.B[(size_t)kg * op.ldb + col]);
                 }
-                Bs[kk][j] = (U)v;
+                Bs[kk][j] = v;
             }
             __syncthreads();
 #pragma unroll

@@ -420,14 +420,11 @@ size_t jac_rot_bytes(int n) {
     const int m = n + (n & 1), half = m / 2;
     return align16((size_t)(m - 1) * 4) + (size_t)(m - 1) * half * sizeof(RotE<double>);
 }
-// Rows of V per apply block (one warp).  float64 lanes issue at a small
-// fraction of the float32 rate, so a float64 block takes 8 rows: the same
-// work spreads over 4x more SMs and each warp instruction has 8 active lanes.
+// Rows of V per apply block (one warp, one row per lane).
 int jac_rows_per_block(int n, bool f32) {
     const size_t row = (size_t)(n | 1) * (f32 ? 4 : 8);
     const size_t r = (size_t)JAC_SMEM / row;
-    const size_t cap = f32 ? 32 : 8;
-    return (int)(r < cap ? (r < 1 ? 1 : r) : cap);
+    return (int)(r < 32 ? (r < 1 ? 1 : r) : 32);
 }
 
 static void jac_attributes() {

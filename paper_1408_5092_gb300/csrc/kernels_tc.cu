@@ -91,8 +91,27 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
         smem_u32(bar)));
 }
 
-__device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, uint32_t off, double v) {
-    const float f = (float)v;
+// float64 -> float32, round to nearest even, with integer operations only
+// (the float64 pipe of this GPU is narrow: the conversion instruction would
+// bound the operand staging).  Magnitudes below the float32 normal range
+// (2^-126) become signed zero, above it infinity; NaN stays NaN.
+__device__ __forceinline__ float d2f_rn(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+    if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+    const int fe = e - 1023 + 127;
+    if (fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+    const unsigned mant = (unsigned)(m >> 29);
+    const unsigned rem = (unsigned)(m & 0x1FFFFFFFULL);
+    unsigned f = sign | ((unsigned)fe << 23) | mant;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) f += 1u;   // carry may reach the exponent
+    return __uint_as_float(f);
+}
+
+__device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, uint32_t off, float f) {
     const __nv_bfloat16 h = __float2bfloat16_rn(f);
     const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
     *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
@@ -136,6 +155,7 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
     for (int o = t.op0; o < t.op1 && ok; ++o) {
         const GemmOp op = ops[o];
         const bool ta = op.trans & 1, tb = op.trans & 2;
+        const float alpha = d2f_rn(op.alpha);
         for (int k0 = 0; k0 < op.k; k0 += BK) {
             const int buf = stage & 1;
             if (stage >= 2) {   // stage buffer free once the MMAs of stage-2 completed
@@ -166,7 +186,7 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < LCH; ++q) split_store(Ahi, Alo, (uint32_t)off[q], op.alpha * v[q]);
+                for (int q = 0; q < LCH; ++q) split_store(Ahi, Alo, (uint32_t)off[q], alpha * d2f_rn(v[q]));
             }
             for (int e0 = 0; e0 < BN * BK; e0 += NTH * LCH) {
                 double v[LCH];
@@ -184,7 +204,7 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < LCH; ++q) split_store(Bhi, Blo, (uint32_t)off[q], v[q]);
+                for (int q = 0; q < LCH; ++q) split_store(Bhi, Blo, (uint32_t)off[q], d2f_rn(v[q]));
             }
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
