@@ -382,21 +382,21 @@ __global__ void __launch_bounds__(32) k_jac_apply(const JacTask* __restrict__ ta
         for (int r = 0; r < m - 1; ++r) {
             const int c = __ldg(rcount + r);
             const RotE<T>* L = rlist + (size_t)r * half;
-            // the rotations of one round act on disjoint columns: four at a
+            // the rotations of one round act on disjoint columns: eight at a
             // time, all loads before all stores
             int j = 0;
-            for (; j + 4 <= c; j += 4) {
-                const RotE<T> e0 = L[j], e1 = L[j + 1], e2 = L[j + 2], e3 = L[j + 3];
-                const T x0 = row[e0.p], y0 = row[e0.q], x1 = row[e1.p], y1 = row[e1.q];
-                const T x2 = row[e2.p], y2 = row[e2.q], x3 = row[e3.p], y3 = row[e3.q];
-                row[e0.p] = e0.c * x0 - e0.s * y0;
-                row[e0.q] = e0.s * x0 + e0.c * y0;
-                row[e1.p] = e1.c * x1 - e1.s * y1;
-                row[e1.q] = e1.s * x1 + e1.c * y1;
-                row[e2.p] = e2.c * x2 - e2.s * y2;
-                row[e2.q] = e2.s * x2 + e2.c * y2;
-                row[e3.p] = e3.c * x3 - e3.s * y3;
-                row[e3.q] = e3.s * x3 + e3.c * y3;
+            for (; j + 8 <= c; j += 8) {
+                RotE<T> e[8];
+                T x[8], y[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) e[q] = L[j + q];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { x[q] = row[e[q].p]; y[q] = row[e[q].q]; }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    row[e[q].p] = e[q].c * x[q] - e[q].s * y[q];
+                    row[e[q].q] = e[q].s * x[q] + e[q].c * y[q];
+                }
             }
             for (; j < c; ++j) {
                 const RotE<T> e = L[j];

@@ -46,8 +46,10 @@ def medium(M, h0, sweeps):
     t = time.time()
     sw = HylleraasSweep(p, M, tol_e=1e-9, max_sweeps=sweeps, verbose=True)
     e2 = sw.run()
+    e3 = third_order(sw)
+    print("E3", e3, flush=True)
     return {"config": "medium", "h0": h0, "M": M, "E_ref": p.E_ref, "E0": p.E0, "E1": p.E1,
-            "E2": e2, "sweeps": len(sw.history), "history": sw.history, "tol_e": 1e-9,
+            "E2": e2, "E3": e3, "sweeps": len(sw.history), "history": sw.history, "tol_e": 1e-9,
             "oracle_s": time.time() - t}
 
 
@@ -59,7 +61,7 @@ if __name__ == "__main__":
     else:
         M = int(what.replace("medium", ""))
         h0 = sys.argv[2] if len(sys.argv) > 2 else "fock"
-        res = medium(M, h0, int(sys.argv[3]) if len(sys.argv) > 3 else 4)
+        res = medium(M, h0, int(sys.argv[3]) if len(sys.argv) > 3 else 3)
         name = f"oracle_medium_{h0}_M{M}.json"
     with open(os.path.join(HERE, name), "w") as f:
         json.dump(res, f, indent=1)
