@@ -2,9 +2,12 @@
 
     python -m paper_1408_5092_gb300.cli --config medium --M 256 --h0 dyall \
         --prec mixed [--sweeps 64] [--e_tol 1e-7] [--e3] [--verbose 1]
+    python -m paper_1408_5092_gb300.cli --config medium --partitions 300 \
+        [--streams 8] [--M 0]      (partitioned mode, uneven seeded M_P)
 
 Prints one JSON line: E2 (and E3), the per-sweep energies and device times,
-the local-solver counters and the kernel launch count.  The system comes
+the local-solver counters and the kernel launch count; in partitioned mode
+the total E2, the partitions per second and the wall time.  The system comes
 from the seeded generator in synthetic/ (run from the repository root).
 """
 import argparse
@@ -27,6 +30,9 @@ def main(argv=None):
     ap.add_argument("--eig_fp64_only", type=int, default=0)
     ap.add_argument("--e3", action="store_true")
     ap.add_argument("--verbose", type=int, default=0)
+    ap.add_argument("--partitions", type=int, default=0,
+                    help="partitioned mode: the first N virtual pairs (a <= b, a then b)")
+    ap.add_argument("--streams", type=int, default=8)
     a = ap.parse_args(argv)
     import synthetic
     seed = synthetic.EVAL_SEED if a.seed is None else a.seed
@@ -42,6 +48,18 @@ def main(argv=None):
     try:
         L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
         L.mpspt_set_reference(ctx, ci)
+        if a.partitions > 0:
+            kv = h.shape[0] - c["k_act"]
+            pairs = [(x, y) for x in range(kv) for y in range(x, kv)][: a.partitions]
+            Ms = synthetic.partition_bond_dims(len(pairs)) if a.M <= 0 else [a.M] * len(pairs)
+            t = time.time()
+            tot, ep, rep = L.mpspt_minimize_partitioned(ctx, a.h0, pairs, Ms, n_streams=a.streams)
+            wall = time.time() - t
+            print(json.dumps({"config": a.config, "h0": a.h0, "prec": a.prec, "partitions": len(pairs),
+                              "M_part": "seeded from {32,...,512}" if a.M <= 0 else a.M, "E2": tot,
+                              "wall_s": wall, "partitions_per_s": len(pairs) / wall, "streams": a.streams,
+                              "cg_iters": rep.cg_iters, "kernel_launches": rep.kernel_launches}), flush=True)
+            return 0
         t = time.time()
         e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, a.h0, a.M, want_psi1=a.e3)
         wall = time.time() - t

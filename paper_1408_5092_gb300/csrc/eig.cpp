@@ -36,7 +36,7 @@ void EigSolver::jacobi(const std::vector<EigTask>& et, const std::vector<const d
         check_range(R, jac_rot_bytes(n), "jacobi rot");
         check_range(S, 16, "jacobi state");
         jt[i] = {in[i], P, R, et[i].V, want_w ? et[i].w : nullptr, reinterpret_cast<double*>(S),
-                 reinterpret_cast<int*>(S + 8), n, vinit};
+                 reinterpret_cast<int*>(S + 8), n, vinit, (vinit && !f32) ? 1 : 0, 0};
         const int rpb = jac_rows_per_block(n, f32);
         for (int r0 = 0; r0 < n; r0 += rpb) {
             const int nr = std::min(rpb, n - r0);

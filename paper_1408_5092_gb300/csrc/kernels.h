@@ -78,6 +78,8 @@ struct JacTask {
     double* prev;      // scratch: off-norm of the previous sweep
     int* done;         // scratch: set once the matrix has converged
     int n, vinit;
+    int sched;         // pair schedule: 0 round robin, 1 large-diagonal indices first
+    int pad;
 };
 struct JacRows {       // rows [r0, r0 + rows) of task's V for one apply block
     int task, r0, rows, pad;

@@ -54,18 +54,130 @@ __device__ __forceinline__ void rr_pair(int k, int r, int m, int& pa, int& pb) {
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-// shared-memory head of the sweep kernel: rowoff[n], Pp[half], Qq[half], Cc, Ss
+// Rounds of one sweep at most (either schedule), and the rotation-list
+// layout: [nrounds][rcount per round] then `half` entries per round.
+__host__ __device__ inline int jac_max_rounds(int n) { return 2 * n + 4; }
+__host__ __device__ inline size_t jac_rot_head(int n) { return align16((size_t)(1 + jac_max_rounds(n)) * 4); }
+
+// shared-memory head of the sweep kernels: rowoff, Pp, Qq, perm (n ints each),
+// Cc, Ss (n T each), dg (n doubles); the packed triangle follows
 template <class T>
 __host__ __device__ inline size_t jac_head_bytes(int n) {
-    const int half = (n + (n & 1)) / 2;
-    return align16((size_t)n * 4 + 2 * (size_t)half * 4) + align16(2 * (size_t)half * sizeof(T));
+    return align16((size_t)n * 16) + align16(2 * (size_t)n * sizeof(T)) + align16((size_t)n * 8);
+}
+
+// Pair schedule of one sweep.  A round is a list of slots; a slot is a pair
+// (p < q) or a single index (q = -1) that is not rotated in that round, and
+// every index is in exactly one slot, so the 2x2 block update over all slot
+// pairs touches every matrix entry once.
+//  mode 0: the round-robin ordering (m - 1 rounds of m/2 slots).
+//  mode 1 (float64 polish after the float32 start): indices sorted by
+//    decreasing diagonal; S = those within 1e-8 of the largest, the rest R.
+//    Rounds: all S x S pairs (round robin on S), then all S x R pairs (the
+//    smaller side against cyclic shifts of the larger), then R x R (round
+//    robin on R).  Couplings of the large eigenvalues to the near-null
+//    directions are removed before rotations inside the near-null cluster
+//    move them around, which the round-robin order keeps doing sweep after
+//    sweep (linear instead of quadratic convergence from a float32 start).
+struct Sched {
+    int mode, n, m, half;
+    int kS, R, mS, mR, rA, rB, rC, a, b;
+    bool smallS;
+    const int* perm;
+    __device__ void init(int mode_, int n_, const int* perm_, int kS_) {
+        mode = mode_; n = n_; m = n + (n & 1); half = m / 2; perm = perm_;
+        kS = kS_; R = n - kS;
+        mS = kS + (kS & 1); mR = R + (R & 1);
+        rA = kS >= 2 ? mS - 1 : 0;
+        smallS = kS <= R;
+        a = smallS ? kS : R;
+        b = smallS ? R : kS;
+        rB = (kS > 0 && R > 0) ? b : 0;
+        rC = R >= 2 ? mR - 1 : 0;
+    }
+    __device__ int rounds() const { return mode == 0 ? m - 1 : rA + rB + rC; }
+    __device__ int slots(int r) const {
+        if (mode == 0) return half;
+        if (r < rA) return mS / 2 + R;
+        r -= rA;
+        if (r < rB) return b;
+        return mR / 2 + kS;
+    }
+    __device__ void slot(int r, int k, int& p, int& q) const {
+        int x, y;
+        if (mode == 0) {
+            rr_pair(k, r, m, x, y);
+            p = min(x, y);
+            q = max(x, y);
+            if (q >= n) q = -1;
+            return;
+        }
+        if (r < rA) {
+            if (k < mS / 2) {
+                rr_pair(k, r, mS, x, y);
+                const int lo = min(x, y), hi = max(x, y);
+                p = perm[lo];
+                q = hi < kS ? perm[hi] : -1;
+            } else {
+                p = perm[kS + (k - mS / 2)];
+                q = -1;
+            }
+        } else if ((r -= rA) < rB) {
+            const int jl = (k + r) % b;
+            const int li = smallS ? kS + jl : jl;
+            if (k < a) { p = perm[smallS ? k : kS + k]; q = perm[li]; }
+            else { p = perm[li]; q = -1; }
+        } else {
+            r -= rB;
+            if (k < mR / 2) {
+                rr_pair(k, r, mR, x, y);
+                const int lo = min(x, y), hi = max(x, y);
+                p = perm[kS + lo];
+                q = hi < R ? perm[kS + hi] : -1;
+            } else {
+                p = perm[k - mR / 2];
+                q = -1;
+            }
+        }
+        if (q >= 0 && q < p) { const int t = p; p = q; q = t; }
+    }
+};
+
+// perm = indices by decreasing dg (ties by index), *kS = #{dg >= 1e-8 max}
+__device__ void sort_diag(const double* dg, int n, int* perm, int* kS, double* red) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double mx = -1e300;
+    for (int i = tid; i < n; i += blockDim.x) mx = fmax(mx, dg[i]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    if (tid == 0) *kS = 0;
+    __syncthreads();
+    if (tid == 0) {
+        double v = red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+        red[0] = v;
+    }
+    __syncthreads();
+    const double thr = 1e-8 * red[0];
+    int cnt = 0;
+    for (int i = tid; i < n; i += blockDim.x) {
+        const double d = dg[i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += (dg[j] > d) || (dg[j] == d && j < i);
+        perm[r] = i;
+        cnt += d >= thr;
+    }
+    atomicAdd(kS, cnt);
+    __syncthreads();
+    if (tid == 0 && *kS < 1) *kS = 1;
+    __syncthreads();
 }
 
 template <class T>
 __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __restrict__ tasks, int sweep, int maxs) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double red[2][JAC_THREADS / 32];
-    __shared__ int stop, cnt;
+    __shared__ int stop, cnt, kS;
     const JacTask t = tasks[blockIdx.x];
     if (sweep > 0 && *(volatile const int*)t.done) return;
     const int n = t.n;
@@ -73,15 +185,17 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
     const size_t np = (size_t)n * (n + 1) / 2;
     int* rowoff = reinterpret_cast<int*>(sm);
     int* Pp = rowoff + n;
-    int* Qq = Pp + half;
-    T* Cc = reinterpret_cast<T*>(sm + align16((size_t)n * 4 + 2 * (size_t)half * 4));
-    T* Ss = Cc + half;
+    int* Qq = Pp + n;
+    int* perm = Qq + n;
+    T* Cc = reinterpret_cast<T*>(sm + align16((size_t)n * 16));
+    T* Ss = Cc + n;
+    double* dg = reinterpret_cast<double*>(sm + align16((size_t)n * 16) + align16(2 * (size_t)n * sizeof(T)));
     const size_t head = jac_head_bytes<T>(n);
     const bool p_sm = head + np * sizeof(T) <= (size_t)JAC_SMEM;
     T* P = p_sm ? reinterpret_cast<T*>(sm + head) : reinterpret_cast<T*>(t.P);
     T* Pg = reinterpret_cast<T*>(t.P);
-    int* rcount = reinterpret_cast<int*>(t.rot);
-    RotE<T>* rlist = reinterpret_cast<RotE<T>*>(reinterpret_cast<unsigned char*>(t.rot) + align16((size_t)(m - 1) * 4));
+    int* rhead = reinterpret_cast<int*>(t.rot);          // [0]: rounds, [1 + r]: count of round r
+    RotE<T>* rlist = reinterpret_cast<RotE<T>*>(reinterpret_cast<unsigned char*>(t.rot) + jac_rot_head(n));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = JAC_THREADS / 32;
     for (int i = tid; i < n; i += JAC_THREADS) rowoff[i] = i * n - i * (i + 1) / 2;
     __syncthreads();
@@ -128,16 +242,25 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
             for (int i = tid; i < n; i += JAC_THREADS) t.w[i] = (double)P[rowoff[i] + i];
         return;
     }
+    if (t.sched == 1) {
+        for (int i = tid; i < n; i += JAC_THREADS) dg[i] = (double)P[rowoff[i] + i];
+        __syncthreads();
+        sort_diag(dg, n, perm, &kS, &red[0][0]);
+    }
+    Sched sc;
+    sc.init(t.sched, n, perm, t.sched == 1 ? kS : 0);
+    const int nr = sc.rounds();
+    if (tid == 0) rhead[0] = nr;
     constexpr T SKIP = (T)JacTol<T>::skip;
-    for (int r = 0; r < m - 1; ++r) {
+    for (int r = 0; r < nr; ++r) {
+        const int ns = sc.slots(r);
         if (tid == 0) cnt = 0;
         __syncthreads();
-        for (int k = tid; k < half; k += JAC_THREADS) {
-            int pa, pb;
-            rr_pair(k, r, m, pa, pb);
-            int p = min(pa, pb), q = max(pa, pb);
+        for (int k = tid; k < ns; k += JAC_THREADS) {
+            int p, q;
+            sc.slot(r, k, p, q);
             T c = T(1), s = T(0);
-            if (q < n) {
+            if (q >= 0) {
                 const T apq = P[rowoff[p] + q];
                 const T app = P[rowoff[p] + p], aqq = P[rowoff[q] + q];
                 if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && apq != T(0)) {
@@ -146,8 +269,6 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
                     c = T(1) / sqrt(tt * tt + T(1));
                     s = tt * c;
                 }
-            } else {
-                q = -1;   // dummy player
             }
             Pp[k] = p; Qq[k] = q; Cc[k] = c; Ss[k] = s;
             if (s != T(0)) {
@@ -156,11 +277,11 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
             }
         }
         __syncthreads();
-        if (tid == 0) rcount[r] = cnt;
-        for (int k = warp; k < half; k += nw) {
+        if (tid == 0) rhead[1 + r] = cnt;
+        for (int k = warp; k < ns; k += nw) {
             const int p = Pp[k], q = Qq[k];
             const T ck = Cc[k], sk = Ss[k];
-            for (int l = k + lane; l < half; l += 32) {
+            for (int l = k + lane; l < ns; l += 32) {
                 const T cl = Cc[l], sl = Ss[l];
                 if (sk == T(0) && sl == T(0)) continue;
                 if (l == k) {
@@ -209,7 +330,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double red[2][JAC_THREADS / 32];
     __shared__ double part[2][JC];
-    __shared__ int stop, cnt;
+    __shared__ int stop, cnt, kS;
     const int rank = (int)cl.block_rank();
     const JacTask t = tasks[blockIdx.x / JC];
     if (sweep > 0 && *(volatile const int*)t.done) return;   // same value in every CTA of the cluster
@@ -219,13 +340,15 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
     const size_t nloc = (np + JC - 1) / JC;
     int* rowoff = reinterpret_cast<int*>(sm);
     int* Pp = rowoff + n;
-    int* Qq = Pp + half;
-    T* Cc = reinterpret_cast<T*>(sm + align16((size_t)n * 4 + 2 * (size_t)half * 4));
-    T* Ss = Cc + half;
+    int* Qq = Pp + n;
+    int* perm = Qq + n;
+    T* Cc = reinterpret_cast<T*>(sm + align16((size_t)n * 16));
+    T* Ss = Cc + n;
+    double* dg = reinterpret_cast<double*>(sm + align16((size_t)n * 16) + align16(2 * (size_t)n * sizeof(T)));
     T* Ploc = reinterpret_cast<T*>(sm + jac_head_bytes<T>(n));
     T* Pg = reinterpret_cast<T*>(t.P);
-    int* rcount = reinterpret_cast<int*>(t.rot);
-    RotE<T>* rlist = reinterpret_cast<RotE<T>*>(reinterpret_cast<unsigned char*>(t.rot) + align16((size_t)(m - 1) * 4));
+    int* rhead = reinterpret_cast<int*>(t.rot);
+    RotE<T>* rlist = reinterpret_cast<RotE<T>*>(reinterpret_cast<unsigned char*>(t.rot) + jac_rot_head(n));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = JAC_THREADS / 32;
     for (int i = tid; i < n; i += JAC_THREADS) rowoff[i] = i * n - i * (i + 1) / 2;
     __syncthreads();
@@ -292,16 +415,25 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
             }
         return;
     }
+    if (t.sched == 1) {   // every CTA sorts the same diagonal the same way
+        for (int i = tid; i < n; i += JAC_THREADS) dg[i] = (double)S(i, i);
+        __syncthreads();
+        sort_diag(dg, n, perm, &kS, &red[0][0]);
+    }
+    Sched sc;
+    sc.init(t.sched, n, perm, t.sched == 1 ? kS : 0);
+    const int nr = sc.rounds();
+    if (rank == 0 && tid == 0) rhead[0] = nr;
     constexpr T SKIP = (T)JacTol<T>::skip;
-    for (int r = 0; r < m - 1; ++r) {
+    for (int r = 0; r < nr; ++r) {
+        const int ns = sc.slots(r);
         if (tid == 0) cnt = 0;
         __syncthreads();
-        for (int k = tid; k < half; k += JAC_THREADS) {
-            int pa, pb;
-            rr_pair(k, r, m, pa, pb);
-            int p = min(pa, pb), q = max(pa, pb);
+        for (int k = tid; k < ns; k += JAC_THREADS) {
+            int p, q;
+            sc.slot(r, k, p, q);
             T c = T(1), s = T(0);
-            if (q < n) {
+            if (q >= 0) {
                 const T apq = S(p, q), app = S(p, p), aqq = S(q, q);
                 if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && apq != T(0)) {
                     const T th = (aqq - app) / (T(2) * apq);
@@ -309,8 +441,6 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
                     c = T(1) / sqrt(tt * tt + T(1));
                     s = tt * c;
                 }
-            } else {
-                q = -1;
             }
             Pp[k] = p; Qq[k] = q; Cc[k] = c; Ss[k] = s;
             if (rank == 0 && s != T(0)) {
@@ -319,12 +449,12 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
             }
         }
         __syncthreads();
-        if (rank == 0 && tid == 0) rcount[r] = cnt;
+        if (rank == 0 && tid == 0) rhead[1 + r] = cnt;
         cl.sync();   // every CTA has read the pair entries before any is updated
-        for (int k = rank + JC * warp; k < half; k += JC * nw) {
+        for (int k = rank + JC * warp; k < ns; k += JC * nw) {
             const int p = Pp[k], q = Qq[k];
             const T ck = Cc[k], sk = Ss[k];
-            for (int l = k + lane; l < half; l += 32) {
+            for (int l = k + lane; l < ns; l += 32) {
                 const T cl_ = Cc[l], sl = Ss[l];
                 if (sk == T(0) && sl == T(0)) continue;
                 if (l == k) {
@@ -375,12 +505,13 @@ __global__ void __launch_bounds__(32) k_jac_apply(const JacTask* __restrict__ ta
     __syncwarp();
     if (!done && lane < b.rows) {
         const int m = n + (n & 1), half = m / 2;
-        const int* rcount = reinterpret_cast<const int*>(t.rot);
+        const int* rhead = reinterpret_cast<const int*>(t.rot);
         const RotE<T>* rlist =
-            reinterpret_cast<const RotE<T>*>(reinterpret_cast<const unsigned char*>(t.rot) + align16((size_t)(m - 1) * 4));
+            reinterpret_cast<const RotE<T>*>(reinterpret_cast<const unsigned char*>(t.rot) + jac_rot_head(n));
         T* row = R + lane * ld;
-        for (int r = 0; r < m - 1; ++r) {
-            const int c = __ldg(rcount + r);
+        const int nr = __ldg(rhead);
+        for (int r = 0; r < nr; ++r) {
+            const int c = __ldg(rhead + 1 + r);
             const RotE<T>* L = rlist + (size_t)r * half;
             // the rotations of one round act on disjoint columns: eight at a
             // time, all loads before all stores
@@ -418,7 +549,7 @@ __global__ void __launch_bounds__(32) k_jac_apply(const JacTask* __restrict__ ta
 size_t jac_p_bytes(int n) { return (size_t)n * (n + 1) / 2 * sizeof(double); }
 size_t jac_rot_bytes(int n) {
     const int m = n + (n & 1), half = m / 2;
-    return align16((size_t)(m - 1) * 4) + (size_t)(m - 1) * half * sizeof(RotE<double>);
+    return jac_rot_head(n) + (size_t)jac_max_rounds(n) * half * sizeof(RotE<double>);
 }
 // Rows of V per apply block (one warp, one row per lane).
 int jac_rows_per_block(int n, bool f32) {

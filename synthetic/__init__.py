@@ -20,7 +20,8 @@ Conventions (shared by every consumer):
   basis state is the product of creators in ascending spin-orbital order
   (p0a, p0b, p1a, p1b, ...) applied to the vacuum.
 """
-from .integrals import integrals, config_integrals, CONFIGS, EVAL_SEED, TRAIN_SEED
+from .integrals import integrals, config_integrals, partition_bond_dims, CONFIGS, EVAL_SEED, TRAIN_SEED
 from .reference import fci_reference
 
-__all__ = ["integrals", "config_integrals", "CONFIGS", "EVAL_SEED", "TRAIN_SEED", "fci_reference"]
+__all__ = ["integrals", "config_integrals", "partition_bond_dims", "CONFIGS", "EVAL_SEED", "TRAIN_SEED",
+           "fci_reference"]

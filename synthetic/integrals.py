@@ -45,3 +45,10 @@ def config_integrals(name, seed=EVAL_SEED):
     c = CONFIGS[name]
     h, L = integrals(seed, c["k_act"], c["k_virt"], c["n_chol"])
     return h, L, c
+
+
+def partition_bond_dims(n_part, seed=20140819, choices=(32, 64, 128, 256, 512)):
+    """Uneven bond dimensions of the virtual-pair partitions: drawn uniformly
+    from `choices` with numpy PCG64(seed), in partition order."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [int(choices[i]) for i in rng.integers(0, len(choices), size=n_part)]

@@ -1,7 +1,7 @@
 """Writes the stored oracle energies used by the GPU parity tests.
 
 Calls only oracle/ (and the seeded inputs of synthetic/).  Run from the repo
-root:  python tests/golden/make_golden.py [tiny|medium64 [fock|dyall [sweeps]]]
+root:  python tests/golden/make_golden.py [tiny|medium_partitions|medium64 [fock|dyall [sweeps]]]
 (medium: the first sweeps of the M = 64 run; the tests compare E2 per sweep).
 """
 import json
@@ -39,6 +39,22 @@ def tiny():
     return out
 
 
+def medium_partitions(M, h0, pairs):
+    """Per-partition E2 of a few virtual-pair partitions of the medium system."""
+    from oracle.partition import SubProblem
+    h, L, c = synthetic.config_integrals("medium")
+    ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
+    p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
+    out = {"config": "medium", "h0": h0, "M": M, "parts": []}
+    for a, b in pairs:
+        t = time.time()
+        sub = SubProblem(p, a, b)
+        e2 = HylleraasSweep(sub, M, allowed=sub.allowed).run()
+        out["parts"].append({"a": a, "b": b, "E2": e2, "oracle_s": time.time() - t})
+        print(a, b, e2, flush=True)
+    return out
+
+
 def medium(M, h0, sweeps):
     h, L, c = synthetic.config_integrals("medium")
     ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
@@ -58,6 +74,9 @@ if __name__ == "__main__":
     if what == "tiny":
         res = tiny()
         name = "oracle_tiny.json"
+    elif what == "medium_partitions":
+        res = medium_partitions(16, "fock", [(0, 0), (3, 17), (23, 23)])
+        name = "oracle_medium_partitions_fock_M16.json"
     else:
         M = int(what.replace("medium", ""))
         h0 = sys.argv[2] if len(sys.argv) > 2 else "fock"

@@ -6,8 +6,11 @@ float64 Jacobi (mpspt_eigh_batched) and the sweep-per-launch solver of the
 truncation step, from float64 sweeps alone or from a float32 start with a
 float64 polish (mpspt_eigh_batched_ex).  The sizes straddle the kernels'
 placement limits (single launch: A and V in shared memory up to n = 112, A
-alone up to 158; sweep-per-launch: packed A in shared memory up to n = 221
-in float64, 313 in float32)."""
+alone up to 158; sweep-per-launch: packed A in shared memory of one CTA up to
+n = 218 in float64 and 308 in float32, float64 sweeps of n >= 48 on 8-CTA
+clusters up to n = 594, larger ones on one CTA with A in global memory).
+The float64 polish after the float32 start uses the large-diagonal-first
+pair schedule; the others the round-robin one."""
 
 ENTRIES = [("mpspt_eigh_batched", ()), ("mpspt_eigh_batched_ex", (0,)), ("mpspt_eigh_batched_ex", (1,))]
 import numpy as np
@@ -30,7 +33,7 @@ def test_eigh_batched_matches_numpy(entry, extra):
     import torch
     from paper_1408_5092_gb300 import _lib as L
     rng = np.random.default_rng(1)
-    sizes = [1, 2, 7, 64, 112, 113, 158, 159, 184, 221, 222, 313, 314, 400]
+    sizes = [1, 2, 7, 47, 48, 64, 112, 113, 158, 159, 184, 218, 219, 308, 309, 400, 600]
     mats = _batch(rng, sizes)
     A = torch.tensor(np.concatenate([m.ravel() for m in mats]), device="cuda", dtype=torch.float64)
     V = torch.zeros_like(A)

@@ -61,3 +61,26 @@ def test_partitioned_exact_limit_equals_brute_force(tiny):
         tot, ep, rep = L.mpspt_minimize_partitioned(ctx, "fock", pairs, [64] * len(pairs), n_streams=8)
         assert abs(tot - e_ex) < (1e-9 if prec == "fp64" else 1e-6), (prec, tot, e_ex)
         L.mpspt_destroy(ctx)
+
+
+def test_medium_partitions_match_oracle():
+    """Virtual-pair partitions of the medium system (8e/8o + 24 virtual; the
+    sub-chains carry the exact M0 = 256 reference) at M_P = 16 against the
+    oracle's partition sweeps (tests/golden/oracle_medium_partitions_fock_M16.json),
+    run concurrently on four streams."""
+    import json
+    import os
+    from paper_1408_5092_gb300 import _lib as L
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "oracle_medium_partitions_fock_M16.json")))
+    h, Lc, c = synthetic.config_integrals("medium")
+    ci, _ = synthetic.fci_reference(h, Lc, c["k_act"], c["n_elec"])
+    o = L.mpspt_default_options()
+    ctx = L.mpspt_create(o)
+    L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
+    L.mpspt_set_reference(ctx, ci)
+    pairs = [(p["a"], p["b"]) for p in gold["parts"]]
+    tot, ep, rep = L.mpspt_minimize_partitioned(ctx, "fock", pairs, [gold["M"]] * len(pairs), n_streams=4)
+    ref = np.array([p["E2"] for p in gold["parts"]])
+    assert np.max(np.abs(ep - ref)) < 1e-8, (ep, ref)
+    L.mpspt_destroy(ctx)
