@@ -36,7 +36,7 @@ void EigSolver::jacobi(const std::vector<EigTask>& et, const std::vector<const d
         check_range(R, jac_rot_bytes(n), "jacobi rot");
         check_range(S, 16, "jacobi state");
         jt[i] = {in[i], P, R, et[i].V, want_w ? et[i].w : nullptr, reinterpret_cast<double*>(S),
-                 reinterpret_cast<int*>(S + 8), n, vinit, (vinit && !f32) ? 1 : 0, 0};
+                 reinterpret_cast<int*>(S + 8), reinterpret_cast<int*>(S + 12), n, vinit, (vinit && !f32) ? 1 : 0, 0};
         const int rpb = jac_rows_per_block(n, f32);
         for (int r0 = 0; r0 < n; r0 += rpb) {
             const int nr = std::min(rpb, n - r0);
@@ -67,6 +67,17 @@ void EigSolver::jacobi(const std::vector<EigTask>& et, const std::vector<const d
         if (!one.empty()) launch_jac_sweep(djt1.as<JacTask>(), (int)one.size(), s, maxs, f32, st);
         if (!clu.empty()) launch_jac_sweep_cluster(djtc.as<JacTask>(), (int)clu.size(), s, maxs, csm, st);
         if (s < maxs) launch_jac_apply(djt.as<JacTask>(), drows.as<JacRows>(), (int)rows.size(), smem, s, f32, st);
+    }
+    if (stats) {   // sweeps per matrix (diagnostics; synchronises)
+        for (int i = 0; i < nt; ++i) {
+            int k = 0;
+            MPSPT_CUDA(cudaMemcpyAsync(&k, jt[i].nsw, sizeof(int), cudaMemcpyDeviceToHost, st));
+            MPSPT_CUDA(cudaStreamSynchronize(st));
+            long long* acc = f32 ? sweeps32 : (vinit ? sweeps_polish : sweeps64);
+            acc[0] += k;
+            acc[1] += 1;
+            acc[2] = std::max<long long>(acc[2], k);
+        }
     }
 }
 

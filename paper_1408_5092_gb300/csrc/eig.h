@@ -12,6 +12,8 @@ namespace mpspt {
 struct EigSolver {
     DBuf scratch, vt, g, djt, djt1, djtc, drows, dtns;
     GemmPlan ge;   // batched square GEMMs of the float64 stage
+    bool stats = false;   // count sweeps per matrix (sum, matrices, max)
+    long long sweeps32[3] = {0, 0, 0}, sweeps_polish[3] = {0, 0, 0}, sweeps64[3] = {0, 0, 0};
 
     // For every task: A (n x n, symmetric, left unchanged) -> V (eigenvectors
     // as columns) and w (unsorted eigenvalues).  All pointers must lie in

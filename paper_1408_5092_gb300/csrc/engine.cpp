@@ -627,11 +627,13 @@ struct Sweeper {
         for (auto& e : evs) MPSPT_CUDA(cudaEventCreate(&e));
         for (auto& e : sev) MPSPT_CUDA(cudaEventCreate(&e));
         for (auto& e : pev) MPSPT_CUDA(cudaEventCreate(&e));
+        eig.stats = c.opt.verbose >= 3;
     }
     ~Sweeper() {
         cudaEventDestroy(ev0); cudaEventDestroy(ev1);
         for (auto& e : evs) cudaEventDestroy(e);
         for (auto& e : sev) cudaEventDestroy(e);
+        for (auto& e : pev) cudaEventDestroy(e);
     }
 
     void boundary_envs() {
@@ -1284,6 +1286,11 @@ std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res,
                     sw.t_rho, sw.t_eig, sw.t_post, sw.eig_calls, sw.eig_nmax, sw.eig_n3);
             fprintf(stderr, "[mpspt]   rhs dev ms %.1f (%.1f GF) env dev ms %.1f (%.1f GF)\n", sw.t_rhs_dev, sw.rhs_gf,
                     sw.t_env_dev, sw.env_gf);
+            const auto& E = sw.eig;
+            fprintf(stderr, "[mpspt]   jacobi sweeps (mean/max): float32 %.2f/%lld polish %.2f/%lld float64 %.2f/%lld\n",
+                    E.sweeps32[1] ? (double)E.sweeps32[0] / E.sweeps32[1] : 0.0, E.sweeps32[2],
+                    E.sweeps_polish[1] ? (double)E.sweeps_polish[0] / E.sweeps_polish[1] : 0.0, E.sweeps_polish[2],
+                    E.sweeps64[1] ? (double)E.sweeps64[0] / E.sweeps64[1] : 0.0, E.sweeps64[2]);
         }
         if (c.opt.verbose == 1)
             fprintf(stderr, "[mpspt]   host-only ms: layouts+products %.1f rhs-plan %.1f sigma-plans %.1f split-host %.1f env-plans %.1f\n",

@@ -77,6 +77,7 @@ struct JacTask {
     double* w;         // n eigenvalues (unsorted), or null
     double* prev;      // scratch: off-norm of the previous sweep
     int* done;         // scratch: set once the matrix has converged
+    int* nsw;          // scratch: sweeps performed (written when the matrix stops)
     int n, vinit;
     int sched;         // pair schedule: 0 round robin, 1 large-diagonal indices first
     int pad;

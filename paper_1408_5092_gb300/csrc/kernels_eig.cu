@@ -38,13 +38,17 @@ struct RotE {
 
 template <class T>
 struct JacTol;
+// stop: off(A)^2 <= stop |A|_F^2.  A pair is not rotated when |a_pq| <=
+// skip sqrt|a_pp a_qq| (relative) or |a_pq| <= absf |A|_F (rounding level of
+// the format): once only such entries are left a sweep rotates nothing and
+// the stall test ends the solve, instead of rotating noise sweep after sweep.
 template <>
 struct JacTol<double> {
-    static constexpr double stop = 1e-30, skip = 1e-18;
+    static constexpr double stop = 1e-30, skip = 1e-18, absf = 1e-17;
 };
 template <>
 struct JacTol<float> {
-    static constexpr double stop = 1e-11, skip = 1e-9;
+    static constexpr double stop = 1e-11, skip = 1e-9, absf = 3e-8;
 };
 
 __device__ __forceinline__ void rr_pair(int k, int r, int m, int& pa, int& pb) {
@@ -177,6 +181,7 @@ template <class T>
 __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __restrict__ tasks, int sweep, int maxs) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double red[2][JAC_THREADS / 32];
+    __shared__ double thr;
     __shared__ int stop, cnt, kS;
     const JacTask t = tasks[blockIdx.x];
     if (sweep > 0 && *(volatile const int*)t.done) return;
@@ -233,7 +238,9 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
                           sweep >= maxs || n < 2;
             *t.prev = so;
             *t.done = s;
+            if (s) *t.nsw = sweep;
             stop = s;
+            thr = JacTol<T>::absf * sqrt(sa);
         }
         __syncthreads();
     }
@@ -263,7 +270,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
             if (q >= 0) {
                 const T apq = P[rowoff[p] + q];
                 const T app = P[rowoff[p] + p], aqq = P[rowoff[q] + q];
-                if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && apq != T(0)) {
+                if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && (double)fabs(apq) > thr && apq != T(0)) {
                     const T th = (aqq - app) / (T(2) * apq);
                     const T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
                     c = T(1) / sqrt(tt * tt + T(1));
@@ -330,6 +337,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double red[2][JAC_THREADS / 32];
     __shared__ double part[2][JC];
+    __shared__ double thr;
     __shared__ int stop, cnt, kS;
     const int rank = (int)cl.block_rank();
     const JacTask t = tasks[blockIdx.x / JC];
@@ -403,7 +411,9 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
                           sweep >= maxs || n < 2;
             *t.prev = so;
             *t.done = s;
-            for (int r = 0; r < JC; ++r) *cl.map_shared_rank(&stop, r) = s;
+            if (s) *t.nsw = sweep;
+            const double th = JacTol<T>::absf * sqrt(sa);
+            for (int r = 0; r < JC; ++r) { *cl.map_shared_rank(&stop, r) = s; *cl.map_shared_rank(&thr, r) = th; }
         }
         cl.sync();
     }
@@ -435,7 +445,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
             T c = T(1), s = T(0);
             if (q >= 0) {
                 const T apq = S(p, q), app = S(p, p), aqq = S(q, q);
-                if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && apq != T(0)) {
+                if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && (double)fabs(apq) > thr && apq != T(0)) {
                     const T th = (aqq - app) / (T(2) * apq);
                     const T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
                     c = T(1) / sqrt(tt * tt + T(1));
