@@ -111,9 +111,13 @@ def test_medium_e2_per_sweep_matches_oracle(medium, prec, tol):
     L.mpspt_set_reference(ctx, ci)
     e0, e1, eref = L.mpspt_energies(ctx, "fock")
     assert abs(eref - gold["E_ref"]) < 1e-10 and abs(e0 - gold["E0"]) < 1e-10
-    e2, _, rep = L.mpspt_minimize_hylleraas(ctx, "fock", 64, want_psi1=False)
+    e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, "fock", 64)
     hist = [rep.e2_per_sweep[s] for s in range(rep.n_sweeps)]
     assert rep.n_sweeps == 3
     for s in range(3):
         assert abs(hist[s] - gold["history"][s]) < tol, (s, hist[s], gold["history"][s])
+    # E3 (Eq. 5) of the three-sweep Psi1, conditioned like E2
+    e3 = L.mpspt_third_order(ctx, "fock", psi)
+    assert abs(e3 - gold["E3"]) < (1e-7 if prec == "fp64" else 1e-6), (e3, gold["E3"])
+    L.mpspt_mps_free(psi)
     L.mpspt_destroy(ctx)
