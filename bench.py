@@ -162,6 +162,20 @@ def _oracle_sample(name, h0, M, cg_per_step, bonds_active, bonds_virtual):
     return per_a * bonds_active + per_v * bonds_virtual, sample
 
 
+def _fp64_roofline(reps, peaks, src):
+    """The float64 sigma of the refinement (same grouped GEMM kernel as the
+    RHS and environment updates) against the float64 peak (the measured bf16
+    burst scaled by the nominal float64 / bf16 ratio of GB300)."""
+    flops = sum(r.sigma64_flops for r in reps)
+    ms = sum(r.sigma64_ms for r in reps)
+    peak = peaks["bf16_tflops"] * NOMINAL_FP64_TFLOPS / NOMINAL_BF16_TFLOPS
+    ach = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    return {"bound": "fp64_alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak if peak else None, "traffic": None,
+            "peak_source": f"{src} bf16 burst x nominal fp64/bf16 ratio",
+            "kernel": "k_gemm<64, 64, double> (float64 refinement sigma)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -319,6 +333,7 @@ def run_gpu(args):
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
                      "traffic": traffic, "peak_source": peak_note,
                      "kernel": "k_gemm (sigma grouped block GEMM)"},
+        "roofline_fp64_sigma": _fp64_roofline(reps, peaks, src),
         "e2e": {"value": e2e, "unit": "s",
                 "h2d_bytes_per_step": int(h.nbytes + Lc.nbytes + ci.nbytes), "d2h_bytes_per_step": 8},
         "gpu_launches": int(sum(r.kernel_launches for r in reps)),
