@@ -22,6 +22,7 @@
 // at once.
 #include <cooperative_groups.h>
 
+#include "jacobi_schedule.h"
 #include "kernels.h"
 
 namespace mpspt {
@@ -53,10 +54,6 @@ struct JacTol<float> {
     static constexpr double stop = 1e-11, skip = 1e-9, absf = 0.0, stall = 1e-8;
 };
 
-__device__ __forceinline__ void rr_pair(int k, int r, int m, int& pa, int& pb) {
-    pa = (k == 0) ? 0 : ((k - 1 + r) % (m - 1)) + 1;
-    pb = ((m - 1 - k - 1 + r) % (m - 1)) + 1;
-}
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -71,83 +68,6 @@ template <class T>
 __host__ __device__ inline size_t jac_head_bytes(int n) {
     return align16((size_t)n * 16) + align16(2 * (size_t)n * sizeof(T)) + align16((size_t)n * 8);
 }
-
-// Pair schedule of one sweep.  A round is a list of slots; a slot is a pair
-// (p < q) or a single index (q = -1) that is not rotated in that round, and
-// every index is in exactly one slot, so the 2x2 block update over all slot
-// pairs touches every matrix entry once.
-//  mode 0: the round-robin ordering (m - 1 rounds of m/2 slots).
-//  mode 1 (float64 polish after the float32 start): indices sorted by
-//    decreasing diagonal; S = those within 1e-8 of the largest, the rest R.
-//    Rounds: all S x S pairs (round robin on S), then all S x R pairs (the
-//    smaller side against cyclic shifts of the larger), then R x R (round
-//    robin on R).  Couplings of the large eigenvalues to the near-null
-//    directions are removed before rotations inside the near-null cluster
-//    move them around, which the round-robin order keeps doing sweep after
-//    sweep (linear instead of quadratic convergence from a float32 start).
-struct Sched {
-    int mode, n, m, half;
-    int kS, R, mS, mR, rA, rB, rC, a, b;
-    bool smallS;
-    const int* perm;
-    __device__ void init(int mode_, int n_, const int* perm_, int kS_) {
-        mode = mode_; n = n_; m = n + (n & 1); half = m / 2; perm = perm_;
-        kS = kS_; R = n - kS;
-        mS = kS + (kS & 1); mR = R + (R & 1);
-        rA = kS >= 2 ? mS - 1 : 0;
-        smallS = kS <= R;
-        a = smallS ? kS : R;
-        b = smallS ? R : kS;
-        rB = (kS > 0 && R > 0) ? b : 0;
-        rC = R >= 2 ? mR - 1 : 0;
-    }
-    __device__ int rounds() const { return mode == 0 ? m - 1 : rA + rB + rC; }
-    __device__ int slots(int r) const {
-        if (mode == 0) return half;
-        if (r < rA) return mS / 2 + R;
-        r -= rA;
-        if (r < rB) return b;
-        return mR / 2 + kS;
-    }
-    __device__ void slot(int r, int k, int& p, int& q) const {
-        int x, y;
-        if (mode == 0) {
-            rr_pair(k, r, m, x, y);
-            p = min(x, y);
-            q = max(x, y);
-            if (q >= n) q = -1;
-            return;
-        }
-        if (r < rA) {
-            if (k < mS / 2) {
-                rr_pair(k, r, mS, x, y);
-                const int lo = min(x, y), hi = max(x, y);
-                p = perm[lo];
-                q = hi < kS ? perm[hi] : -1;
-            } else {
-                p = perm[kS + (k - mS / 2)];
-                q = -1;
-            }
-        } else if ((r -= rA) < rB) {
-            const int jl = (k + r) % b;
-            const int li = smallS ? kS + jl : jl;
-            if (k < a) { p = perm[smallS ? k : kS + k]; q = perm[li]; }
-            else { p = perm[li]; q = -1; }
-        } else {
-            r -= rB;
-            if (k < mR / 2) {
-                rr_pair(k, r, mR, x, y);
-                const int lo = min(x, y), hi = max(x, y);
-                p = perm[kS + lo];
-                q = hi < R ? perm[kS + hi] : -1;
-            } else {
-                p = perm[k - mR / 2];
-                q = -1;
-            }
-        }
-        if (q >= 0 && q < p) { const int t = p; p = q; q = t; }
-    }
-};
 
 // perm = indices by decreasing dg (ties by index), *kS = #{dg >= 1e-8 max}
 __device__ void sort_diag(const double* dg, int n, int* perm, int* kS, double* red) {

@@ -37,3 +37,34 @@ def test_upper_bound_and_monotone_in_m(tiny):
     assert e16 >= e32 - 1e-10
     assert e32 >= ex.e2() - 1e-10
     assert e16 - ex.e2() > 1e-4      # M = 16 really truncates
+
+
+def test_initial_state_canonicalisation():
+    """Reading R8: the seeded random MPS is made right-canonical by
+    right-to-left density-matrix splits (no M cap, states above 1e-13 tr rho
+    kept).  The state changes only by the dropped directions (relative norm
+    below sqrt of their weight), every site but the first is right-
+    orthonormal, and no bond grows."""
+    import numpy as np
+    from oracle.mps import canonicalize_by_splits, random_mps
+    k, N = 8, 4
+    allowed = {4: {N - 1, N - 2}}
+    m0 = random_mps(k, (N, 0), allowed, 12, 1408)
+    before = m0.to_dense().copy()
+    dims0 = m0.dims()
+    m1 = canonicalize_by_splits(random_mps(k, (N, 0), allowed, 12, 1408), allowed)
+    after = m1.to_dense()
+    rel = np.linalg.norm(after - before) / np.linalg.norm(before)
+    assert rel < 1e-6, rel
+    for A in m1.A[1:]:
+        X = A.reshape(A.shape[0], -1)
+        assert np.abs(X @ X.T - np.eye(A.shape[0])).max() < 1e-12
+    assert all(d1 <= d0 for d0, d1 in zip(dims0, m1.dims()))
+
+
+def test_partition_bond_dims_are_seeded_and_in_range():
+    import synthetic
+    a = synthetic.partition_bond_dims(1830)
+    b = synthetic.partition_bond_dims(1830)
+    assert a == b and len(a) == 1830
+    assert set(a) <= {32, 64, 128, 256, 512} and len(set(a)) == 5
