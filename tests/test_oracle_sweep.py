@@ -26,8 +26,7 @@ def test_exact_at_full_bond_dimension(tiny, h0):
     p, ex, m_exact = tiny[h0]
     sw = HylleraasSweep(p, m_exact)
     assert abs(sw.run() - ex.e2()) < 1e-9
-    if h0 == "fock":
-        assert abs(third_order(sw) - ex.e3()) < 1e-9
+    assert abs(third_order(sw) - ex.e3()) < 1e-9
 
 
 def test_upper_bound_and_monotone_in_m(tiny):
