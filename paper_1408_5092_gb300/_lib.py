@@ -26,6 +26,9 @@ H0 = {"fock": MPSPT_H0_FOCK, "dyall": MPSPT_H0_DYALL}
 PREC = {"fp64": MPSPT_FP64, "fp32": MPSPT_FP32, "mixed": MPSPT_MIXED_BF16}
 STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "NOT_SPD", -4: "NOT_CONVERGED",
           -5: "TIMEOUT", -6: "CUDA", -7: "STATE"}
+# mpspt_status values of include/mpspt.h
+MPSPT_OK, MPSPT_ERR_INVALID, MPSPT_ERR_OOM, MPSPT_ERR_NOT_SPD = 0, -1, -2, -3
+MPSPT_ERR_NOT_CONVERGED, MPSPT_ERR_TIMEOUT, MPSPT_ERR_CUDA, MPSPT_ERR_STATE = -4, -5, -6, -7
 
 
 class mpspt_options(ctypes.Structure):
