@@ -75,3 +75,29 @@ def test_e2_invariant_under_virtual_rotation():
     L2 = np.einsum("pi,Qpq,qj->Qij", C, L, C)
     e2 = ExactFirstOrder(Problem(h2, L2, 3, 4, ci, h0="fock")).e2()
     assert abs(e - e2) < 1e-12
+
+
+@pytest.mark.parametrize("h0", ["fock", "dyall"])
+def test_hylleraas_functional_is_the_quadratic_with_minimum_e2(h0):
+    """Eq. 1 on X is J(x) = x^T A x + 2 x^T g with A = H0 - E0 symmetric:
+    J(x* + d) - J(x*) = d^T A d exactly, J(x*) = g^T x* = E2*, and (A > 0)
+    J(x) >= E2* for every x."""
+    h, L = synthetic.integrals(3, 3, 3, 8)
+    ci, _ = synthetic.fci_reference(h, L, 3, 4)
+    ex = ExactFirstOrder(Problem(h, L, 3, 4, ci, h0=h0))
+    A = ex.A.toarray()
+    assert np.abs(A - A.T).max() < 1e-14
+    lam = np.linalg.eigvalsh(A)
+    assert lam.min() > 0.0
+    e2 = ex.e2()
+    xs = ex.psi1
+    assert abs(ex.hylleraas(xs) - e2) < 1e-12
+    assert np.linalg.norm(A @ xs + ex.g) < 1e-10 * np.linalg.norm(ex.g)
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        d = rng.normal(size=xs.shape) * 0.1
+        dJ = ex.hylleraas(xs + d) - e2
+        assert abs(dJ - d @ (A @ d)) < 1e-10 * max(1.0, abs(dJ))
+        assert dJ > 0.0
+        x = rng.normal(size=xs.shape)
+        assert ex.hylleraas(x) >= e2
