@@ -1,0 +1,67 @@
+"""The oracle's local operators at a bond (Fig. 1C: the two-site sigma,
+right-hand side and diagonal built from renormalised environments) equal the
+brute-force operators projected on the two-site space of the MPS:
+A_loc = Phi^T (H0 - E0) Phi and g = Phi^T V Psi0, with Phi the orthonormal
+embedding given by the left- and right-canonical sites.  The determinant
+operators apply each elementary operator to bit strings (no MPO), and Psi0 is
+the CI vector placed on the empty virtual sites, so neither side shares the
+oracle's MPS code."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle.brute import DetSpace, dets_to_site_index, operator_matrix
+from oracle.mps import HylleraasSweep
+from oracle.operators import Problem
+
+
+def _dense_operator(terms, k):
+    H = np.zeros((4 ** k, 4 ** k))
+    for N in range(2 * k + 1):
+        for sz in range(-N, N + 1, 2):
+            S = DetSpace.sector(k, N, sz)
+            if len(S) == 0:
+                continue
+            idx = dets_to_site_index(S.dets, k)
+            H[np.ix_(idx, idx)] = operator_matrix(terms, S).toarray()
+    return H
+
+
+def _embedding(mps, i):
+    k = mps.nsite
+    Lb = np.ones((1, 1))
+    for c in range(i):
+        Lb = np.einsum("xl,lsr->xsr", Lb, mps.A[c]).reshape(-1, mps.A[c].shape[2])
+    Rb = np.ones((1, 1))
+    for c in range(k - 1, i + 1, -1):
+        Rb = np.einsum("lsr,rx->lsx", mps.A[c], Rb).reshape(mps.A[c].shape[0], -1)
+    return np.kron(np.kron(Lb, np.eye(16)), Rb.T)
+
+
+@pytest.mark.parametrize("h0", ["fock", "dyall"])
+def test_local_operators_equal_projected_brute_force(h0):
+    h, L = synthetic.integrals(7, 2, 3, 5)
+    ci, _ = synthetic.fci_reference(h, L, 2, 2)
+    p = Problem(h, L, 2, 2, ci, h0=h0)
+    k = p.k
+    Hd = _dense_operator(p.h0_terms(), k)
+    Vd = _dense_operator(p.rhs_terms(), k)
+    psi0 = np.kron(ci, np.eye(4 ** p.k_virt)[0])       # virtual sites empty
+    sw = HylleraasSweep(p, 4, seed=5)
+    rng = np.random.default_rng(2)
+    checked = 0
+    for i in range(k - 1):                               # left to right; every bond once
+        x0, g, apply, diag, mask = sw.local_problem(i)
+        Phi = _embedding(sw.psi1, i)
+        assert np.abs(Phi.T @ Phi - np.eye(Phi.shape[1])).max() < 1e-12
+        Aloc = Phi.T @ Hd @ Phi
+        m = mask.ravel().astype(bool)
+        x = rng.normal(size=x0.shape) * mask
+        got = (apply(x) * mask).ravel()[m]
+        want = (Aloc @ x.ravel())[m]
+        assert np.abs(got - want).max() < 1e-11 * max(1.0, np.abs(want).max()), i
+        assert np.abs(g.ravel()[m] - (Phi.T @ (Vd @ psi0))[m]).max() < 1e-12, i
+        assert np.abs(diag.ravel()[m] - np.diag(Aloc)[m]).max() < 1e-11, i
+        checked += int(m.sum() > 0)
+        sw.step(i, "LR")
+    assert checked >= k - 2
