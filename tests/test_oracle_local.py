@@ -5,7 +5,12 @@ A_loc = Phi^T (H0 - E0) Phi and g = Phi^T V Psi0, with Phi the orthonormal
 embedding given by the left- and right-canonical sites.  The determinant
 operators apply each elementary operator to bit strings (no MPO), and Psi0 is
 the CI vector placed on the empty virtual sites, so neither side shares the
-oracle's MPS code."""
+oracle's MPS code.
+
+A transposed left environment block, a dropped or sign-flipped MPO term in
+sigma, or a transposed block inside the left transfer each fail this test.
+H0's right environments cover only virtual sites here, where H0 is diagonal
+(sum_a eps_a n_a), so their transposition is invisible to H0 by symmetry."""
 import numpy as np
 import pytest
 
