@@ -7,10 +7,11 @@ operators apply each elementary operator to bit strings (no MPO), and Psi0 is
 the CI vector placed on the empty virtual sites, so neither side shares the
 oracle's MPS code.
 
-A transposed left environment block, a dropped or sign-flipped MPO term in
-sigma, or a transposed block inside the left transfer each fail this test.
-H0's right environments cover only virtual sites here, where H0 is diagonal
-(sum_a eps_a n_a), so their transposition is invisible to H0 by symmetry."""
+A transposed environment block, a dropped or sign-flipped MPO term in sigma,
+or a transposed block inside a transfer each fail this test.  The systems
+have three and four active sites, so active sites also enter the right
+environments and their transfers; virtual sites alone give diagonal H0
+blocks (sum_a eps_a n_a), where a transposition cannot show."""
 import numpy as np
 import pytest
 
@@ -43,11 +44,12 @@ def _embedding(mps, i):
     return np.kron(np.kron(Lb, np.eye(16)), Rb.T)
 
 
+@pytest.mark.parametrize("k_act,k_virt", [(3, 2), (4, 1)])
 @pytest.mark.parametrize("h0", ["fock", "dyall"])
-def test_local_operators_equal_projected_brute_force(h0):
-    h, L = synthetic.integrals(7, 2, 3, 5)
-    ci, _ = synthetic.fci_reference(h, L, 2, 2)
-    p = Problem(h, L, 2, 2, ci, h0=h0)
+def test_local_operators_equal_projected_brute_force(h0, k_act, k_virt):
+    h, L = synthetic.integrals(7, k_act, k_virt, 5)
+    ci, _ = synthetic.fci_reference(h, L, k_act, 4)
+    p = Problem(h, L, k_act, 4, ci, h0=h0)
     k = p.k
     Hd = _dense_operator(p.h0_terms(), k)
     Vd = _dense_operator(p.rhs_terms(), k)
@@ -55,7 +57,8 @@ def test_local_operators_equal_projected_brute_force(h0):
     sw = HylleraasSweep(p, 4, seed=5)
     rng = np.random.default_rng(2)
     checked = 0
-    for i in range(k - 1):                               # left to right; every bond once
+    order = [(i, "LR") for i in range(k - 1)] + [(i, "RL") for i in range(k - 2, -1, -1)]
+    for i, direction in order:                           # one full sweep; every bond twice
         x0, g, apply, diag, mask = sw.local_problem(i)
         Phi = _embedding(sw.psi1, i)
         assert np.abs(Phi.T @ Phi - np.eye(Phi.shape[1])).max() < 1e-12
@@ -68,5 +71,5 @@ def test_local_operators_equal_projected_brute_force(h0):
         assert np.abs(g.ravel()[m] - (Phi.T @ (Vd @ psi0))[m]).max() < 1e-12, i
         assert np.abs(diag.ravel()[m] - np.diag(Aloc)[m]).max() < 1e-11, i
         checked += int(m.sum() > 0)
-        sw.step(i, "LR")
-    assert checked >= k - 2
+        sw.step(i, direction)
+    assert checked >= 2 * (k - 2)
