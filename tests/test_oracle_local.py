@@ -73,3 +73,22 @@ def test_local_operators_equal_projected_brute_force(h0, k_act, k_virt):
         checked += int(m.sum() > 0)
         sw.step(i, direction)
     assert checked >= 2 * (k - 2)
+
+
+@pytest.mark.parametrize("h0", ["fock", "dyall"])
+def test_third_order_transfer_equals_dense_formula_at_truncating_m(h0):
+    """Eq. 5 by MPO transfers on a truncated Psi1 (M = 4) equals the same
+    formula on the dense Psi1 with brute-force operators:
+    E3 = <H> - <H0 - E0> - (E0 + E1) <1>."""
+    from oracle.mps import third_order
+    h, L = synthetic.integrals(7, 3, 2, 5)
+    ci, _ = synthetic.fci_reference(h, L, 3, 4)
+    p = Problem(h, L, 3, 4, ci, h0=h0)
+    sw = HylleraasSweep(p, 4, seed=5, max_sweeps=2)
+    sw.run()
+    psi = sw.psi1.to_dense()
+    Hd = _dense_operator(p.hamiltonian_terms(), p.k)
+    Ad = _dense_operator(p.h0_terms(), p.k)
+    want = psi @ Hd @ psi - psi @ Ad @ psi - (p.E0 + p.E1) * (psi @ psi)
+    assert abs(third_order(sw) - want) < 1e-12 * max(1.0, abs(want))
+    assert abs(psi @ psi - 1.0) > 1e-6          # Psi1 is not normalised: the <1> term matters
