@@ -67,3 +67,19 @@ def test_partition_bond_dims_are_seeded_and_in_range():
     b = synthetic.partition_bond_dims(1830)
     assert a == b and len(a) == 1830
     assert set(a) <= {32, 64, 128, 256, 512} and len(set(a)) == 5
+
+
+def test_splitmix64_reproduces_the_published_stream():
+    """Reading R8 keys the initial Psi1 entries by SplitMix64 (Steele, Lea,
+    Flood 2014).  The generator's first outputs from state 0 are its
+    published reference values; the oracle's function maps the state
+    before the increment to the output."""
+    from oracle.mps import init_value, splitmix64
+    gamma = 0x9E3779B97F4A7C15
+    mask = (1 << 64) - 1
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    assert [splitmix64((i * gamma) & mask) for i in range(4)] == want
+    # entries are u * 2^-53 - 0.5 with u the top 53 bits: in [-0.5, 0.5)
+    v = [init_value(1408, c, s, l, r) for c in range(3) for s in range(4) for l in range(3) for r in range(3)]
+    assert min(v) >= -0.5 and max(v) < 0.5 and len(set(v)) == len(v)
+    assert init_value(1408, 0, 0, 0, 0) == (splitmix64(1408 << 48) >> 11) * 2.0 ** -53 - 0.5
