@@ -48,3 +48,22 @@ def test_gradients_match_finite_differences():
             q[k][idx] -= 2 * h
             lm = L(q)
             assert abs((lp - lm) / (2 * h) - g[k][idx]) < 1e-6, (k, idx)
+
+
+def test_forward_hand_computed():
+    """x -> relu(x W1^T + b1) -> relu(. W2^T + b2) -> . W3^T + b3 on values
+    exact in bf16, worked by hand: z1 = (1, -2, -0.5) -> h1 = (1, 0, 0);
+    z2 = (1, 1, 0) -> h2 = (1, 1, 0); y = 1 + 2 - 1 = 2.  The weights the
+    forward pass uses are the bf16 roundings of the masters."""
+    p = {"W1": np.array([[1.0, 0.0], [0.0, 1.0], [1.0, 1.0]]), "b1": np.array([0.0, 0.0, 0.5]),
+         "W2": np.eye(3), "b2": np.array([0.0, 1.0, 0.0]),
+         "W3": np.array([[1.0, 2.0, 3.0]]), "b3": np.array([-1.0])}
+    x = np.array([[1.0, -2.0]])
+    y, (_, z1, h1, z2, h2) = forward(p, x)
+    assert np.array_equal(z1, [[1.0, -2.0, -0.5]]) and np.array_equal(h1, [[1.0, 0.0, 0.0]])
+    assert np.array_equal(z2, [[1.0, 1.0, 0.0]]) and np.array_equal(h2, [[1.0, 1.0, 0.0]])
+    assert np.array_equal(y, [[2.0]])
+    q = dict(p)
+    q["W3"] = p["W3"] + np.array([[2 ** -9, 0.0, 0.0]])     # rounds back to 1.0 (tie to even)
+    assert np.array_equal(forward(q, x)[0], [[2.0]])
+    assert loss(p, x, np.array([[0.5]])) == 0.5 * 1.5 ** 2
