@@ -101,3 +101,29 @@ def test_hylleraas_functional_is_the_quadratic_with_minimum_e2(h0):
         assert dJ > 0.0
         x = rng.normal(size=xs.shape)
         assert ex.hylleraas(x) >= e2
+
+
+def test_preprocessing_invariants():
+    """Reading R5 and the active 1-RDM: gamma is symmetric with trace N and
+    occupations in [0, 2]; the semicanonical rotation is orthogonal, acts on
+    the virtual block only, makes f_vv diagonal in ascending order, and gives
+    every virtual orbital a positive largest-magnitude coefficient."""
+    h, L = synthetic.integrals(5, 3, 4, 8)
+    ci, _ = synthetic.fci_reference(h, L, 3, 4)
+    p = Problem(h, L, 3, 4, ci, h0="fock")
+    g = p.gamma
+    assert np.abs(g - g.T).max() < 1e-13
+    assert abs(np.trace(g) - 4) < 1e-12
+    occ = np.linalg.eigvalsh(g)
+    assert occ.min() > -1e-12 and occ.max() < 2 + 1e-12
+    C = p.rotation
+    assert np.abs(C.T @ C - np.eye(7)).max() < 1e-13
+    assert np.array_equal(C[:3, :3], np.eye(3)) and not C[:3, 3:].any() and not C[3:, :3].any()
+    fv = p.f[3:, 3:]
+    assert np.abs(fv - np.diag(np.diag(fv))).max() < 1e-12
+    assert np.all(np.diff(np.diag(fv)) >= 0)
+    U = C[3:, 3:]
+    for j in range(4):
+        assert U[int(np.argmax(np.abs(U[:, j]))), j] > 0
+    # the integrals are those of the rotated orbitals
+    assert np.abs(p.h - C.T @ h @ C).max() < 1e-13
