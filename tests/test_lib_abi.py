@@ -101,3 +101,20 @@ def test_status_constants_match_the_header():
     assert len(vals) == 8
     for k, v in vals.items():
         assert getattr(L, k) == v, k
+
+
+def test_shell_driver_fails_loudly_without_a_gpu():
+    import subprocess
+    import sys
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    _lib()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-m", "paper_1408_5092_gb300.cli", "--config", "tiny", "--M", "16"],
+                       cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0 and r.stdout == ""
+    assert "MpsptError" in r.stderr and "(CUDA)" in r.stderr
+    bad = subprocess.run([sys.executable, "-m", "paper_1408_5092_gb300.cli", "--prec", "fp16"],
+                         cwd=root, capture_output=True, text=True, timeout=300)
+    assert bad.returncode == 2 and "invalid choice" in bad.stderr
