@@ -83,8 +83,7 @@ def _clock_summary(p, path, device):
 
 def _inputs(name):
     import synthetic
-    h, L, c = synthetic.config_integrals(name)
-    ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
+    h, L, c, ci = synthetic.config_reference(name)
     return h, L, c, ci
 
 
@@ -101,65 +100,98 @@ def _time_to_e2(rep, e2_ref, tol=1e-6):
     return rep.sweep_ms[first] / 1e3, first
 
 
-def _oracle_sample(name, h0, M, cg_per_step, bonds_active, bonds_virtual):
-    """Bounded oracle (CPU) sample of the same workload.
+def _workload(args):
+    c = {"tiny": "4e/4o + 8 virtual", "medium": "8e/8o + 24 virtual"}.get(args.config, args.config)
+    return f"{args.config}: {c}, M={args.M}, {args.h0} H0"
 
-    The oracle's own sweep would spend minutes just building environments at
-    this size, so the sample times its kernels once each on tensors with the
-    workload's shapes (bond dimensions from the initial-state rule, the real
-    MPOs): sigma at an active-region bond and at a virtual-region bond, and
-    the once-per-step work (RHS, Jacobi diagonal, truncation, two environment
-    updates) at the virtual-region bond.  Seconds per bond step are then
-    (cg + 2) x sigma + once-per-step work; the active-region once-per-step
-    work (larger RHS) is not included, so the estimate is a lower bound."""
-    import numpy as np
-    from oracle.mps import (HylleraasSweep, env_left, random_mps, reference_mps, truncate,
-                            two_site_apply, two_site_diag, two_site_mask)
-    from oracle.mpo import build_mpo
-    from oracle.operators import Problem
-    h, L, c, ci = _inputs(name)
-    p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
-    WA = build_mpo(p.h0_terms(), p.k, k_split=p.k_act)
-    WV = build_mpo(p.rhs_terms(), p.k, k_split=p.k_act)
-    N = p.n_elec
-    allowed = {p.k_act: {N - 1, N - 2}}
-    psi = random_mps(p.k, (N, 0), allowed, M, 1408)
-    psi0 = reference_mps(p.ci, p.k_act, p.k_virt)
-    rng = np.random.default_rng(0)
 
-    def t_sigma(i):
+class _OracleCosts:
+    """Measured oracle (CPU) unit costs on the workload's own shapes.
+
+    Tensors carry the bond dimensions of the initial-state rule at bond
+    dimension M and the real MPOs; entries are random (the oracle's dense
+    contractions cost the same for any values).  Measured: one sigma
+    application (Fig. 1C, H0 - E0 term) at an active-region bond and at a
+    virtual-region bond, and the once-per-bond-step work at the virtual bond
+    (RHS, Jacobi diagonal, truncation, two environment updates).  The
+    active-region sigma is the expensive piece (tens of seconds at M = 256)
+    and is timed once; the cheap pieces are re-timed at every step."""
+
+    def __init__(self, name, h0, M):
+        import numpy as np
+        from oracle.mps import random_mps, reference_mps, two_site_mask
+        from oracle.mpo import build_mpo
+        from oracle.operators import Problem
+        import synthetic
+        h, L, c, ci = synthetic.config_reference(name)
+        p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
+        self.p, self.M = p, M
+        self.WA = build_mpo(p.h0_terms(), p.k, k_split=p.k_act)
+        self.WV = build_mpo(p.rhs_terms(), p.k, k_split=p.k_act)
+        N = p.n_elec
+        self.allowed = {p.k_act: {N - 1, N - 2}}
+        self.psi = random_mps(p.k, (N, 0), self.allowed, M, 1408)
+        self.psi0 = reference_mps(p.ci, p.k_act, p.k_virt)
+        self.rng = np.random.default_rng(0)
+        self.ia = max(1, p.k_act // 2)
+        self.iv = p.k_act + (p.k_virt // 2)
+        self.two_site_mask = two_site_mask
+        self.ts_a = self._sigma(self.ia)[0]
+
+    def _sigma(self, i):
+        import time as _t
+        from oracle.mps import two_site_apply
+        psi, WA = self.psi, self.WA
         Dl, Dr = len(psi.q[i]), len(psi.q[i + 2])
-        La = rng.normal(size=(WA.dims[i], Dl, Dl))
-        Ra = rng.normal(size=(WA.dims[i + 2], Dr, Dr))
-        mask = two_site_mask(psi.q[i], psi.q[i + 2], allowed.get(i + 1))
-        x = rng.normal(size=mask.shape) * mask
-        t0 = time.perf_counter()
+        La = self.rng.normal(size=(WA.dims[i], Dl, Dl))
+        Ra = self.rng.normal(size=(WA.dims[i + 2], Dr, Dr))
+        mask = self.two_site_mask(psi.q[i], psi.q[i + 2], self.allowed.get(i + 1))
+        x = self.rng.normal(size=mask.shape) * mask
+        t0 = _t.perf_counter()
         two_site_apply(La, WA.W[i], WA.W[i + 1], Ra, x, WA.dims[i + 1])
-        return time.perf_counter() - t0, (La, Ra, x, mask, Dl, Dr)
+        return _t.perf_counter() - t0, (La, Ra, x, Dl, Dr)
 
-    ia = max(1, p.k_act // 2)
-    iv = p.k_act + (p.k_virt // 2)
-    ts_a, _ = t_sigma(ia)
-    ts_v, (La, Ra, x, mask, Dl, Dr) = t_sigma(iv)
-    i = iv
-    D0l, D0r = len(psi0.q[i]), len(psi0.q[i + 2])
-    Lv = rng.normal(size=(WV.dims[i], Dl, D0l))
-    Rv = rng.normal(size=(WV.dims[i + 2], Dr, D0r))
-    p0 = np.einsum("lsm,mtr->lstr", psi0.A[i], psi0.A[i + 1])
-    t0 = time.perf_counter()
-    two_site_apply(Lv, WV.W[i], WV.W[i + 1], Rv, p0, WV.dims[i + 1])
-    two_site_diag(La, WA.W[i], WA.W[i + 1], Ra, x.shape, WA.dims[i + 1])
-    Al, Ar, lab, w = truncate(x, psi.q[i], psi.q[i + 2], M, "LR", allowed.get(i + 1))
-    env_left(La, Al, WA.W[i], Al, WA.dims[i + 1])
-    env_left(Lv, Al, WV.W[i], psi0.A[i], WV.dims[i + 1])
-    t_once = time.perf_counter() - t0
-    per_a = (cg_per_step + 2) * ts_a + t_once
-    per_v = (cg_per_step + 2) * ts_v + t_once
-    sample = (f"oracle kernels timed once each on random tensors of the workload's shapes (M={M}): "
-              f"sigma {ts_a:.3f}s at active bond {ia}, {ts_v:.3f}s at virtual bond {iv}; "
-              f"once-per-step work {t_once:.3f}s at bond {iv}; x {cg_per_step:.1f} CG iterations per step "
-              f"over {bonds_active} active and {bonds_virtual} virtual bond steps (lower bound)")
-    return per_a * bonds_active + per_v * bonds_virtual, sample
+    def step(self):
+        """Re-times the virtual-bond sigma and the once-per-step work; returns
+        (t_sigma_active, t_sigma_virtual, t_once)."""
+        import time as _t
+        import numpy as np
+        from oracle.mps import env_left, truncate, two_site_apply, two_site_diag
+        ts_v, (La, Ra, x, Dl, Dr) = self._sigma(self.iv)
+        i, psi, psi0, WA, WV = self.iv, self.psi, self.psi0, self.WA, self.WV
+        D0l, D0r = len(psi0.q[i]), len(psi0.q[i + 2])
+        Lv = self.rng.normal(size=(WV.dims[i], Dl, D0l))
+        Rv = self.rng.normal(size=(WV.dims[i + 2], Dr, D0r))
+        p0 = np.einsum("lsm,mtr->lstr", psi0.A[i], psi0.A[i + 1])
+        t0 = _t.perf_counter()
+        two_site_apply(Lv, WV.W[i], WV.W[i + 1], Rv, p0, WV.dims[i + 1])
+        two_site_diag(La, WA.W[i], WA.W[i + 1], Ra, x.shape, WA.dims[i + 1])
+        Al, Ar, lab, w = truncate(x, psi.q[i], psi.q[i + 2], self.M, "LR", self.allowed.get(i + 1))
+        env_left(La, Al, WA.W[i], Al, WA.dims[i + 1])
+        env_left(Lv, Al, WV.W[i], psi0.A[i], WV.dims[i + 1])
+        return self.ts_a, ts_v, _t.perf_counter() - t0
+
+    def extrapolate(self, costs, n_sigma, n_steps):
+        """Seconds the oracle needs for n_sigma sigma applications over
+        n_steps bond steps, with sigma applications and steps spread over the
+        chain's bonds in proportion to their number (k_act - 1 of the k - 1
+        bonds lie in the active region, where sigma is largest)."""
+        ts_a, ts_v, t_once = costs
+        p = self.p
+        frac_a = (p.k_act - 1) / (p.k - 1)
+        t_sig = frac_a * ts_a + (1 - frac_a) * ts_v
+        return n_sigma * t_sig + n_steps * t_once, (
+            f"oracle (NumPy float64, dense) unit costs measured on random tensors of the workload's shapes at "
+            f"M={self.M}: sigma {ts_a:.3f} s at active-region bond {self.ia}, {ts_v:.3f} s at virtual-region "
+            f"bond {self.iv}; once-per-step work (RHS, diagonal, truncation, two environment updates) "
+            f"{t_once:.3f} s at bond {self.iv}; scaled by {n_sigma} sigma applications over {n_steps} bond "
+            f"steps (the float64 GPU run's counts until E2), bonds weighted by region "
+            f"({p.k_act - 1} of {p.k - 1} active); the once-per-step work of active bonds is priced at the "
+            f"virtual bond's, so the total is a lower bound")
+
+
+def _counts_path(args):
+    return os.path.join(ROOT, "profiles", f"bench_counts_{args.config}_M{args.M}_{args.h0}.json")
 
 
 def _fp64_roofline(reps, peaks, src):
@@ -177,27 +209,40 @@ def _fp64_roofline(reps, peaks, src):
 
 
 def run_reference(args):
+    """The oracle arm: the CPU oracle as it stands on this machine's host cores.
+    A real oracle run to E2 at this size takes hours, so each step times the
+    oracle's unit costs (see _OracleCosts) and scales them by the counts the
+    float64 GPU sweep needed to reach E2 on the same workload (recorded by
+    the GPU arm in profiles/bench_counts_<workload>.json)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     cores = len(os.sched_getaffinity(0))
-    c = {"medium": (8, 24)}.get(args.config, (8, 24))
-    bonds = 2 * (c[0] + c[1] - 1) * args.ref_sweeps
-    frac_a = c[0] / (c[0] + c[1] - 1)
-    vals = []
-    sample = ""
-    for _ in range(args.warmup + args.steps):
-        v, sample = _oracle_sample(args.config, args.h0, args.M, args.ref_cg, bonds * frac_a, bonds * (1 - frac_a))
+    counts = None
+    try:
+        counts = json.load(open(_counts_path(args)))
+    except (OSError, ValueError):
+        counts = None
+    oc = _OracleCosts(args.config, args.h0, args.M)
+    vals, sample = [], ""
+    for s_ in range(args.warmup + args.steps):
+        costs = oc.step()
+        if counts:
+            v, sample = oc.extrapolate(costs, counts["sigma_calls_to_e2"], counts["bond_steps_to_e2"])
+        else:   # no GPU record for this workload: one sigma per step over one sweep
+            n = 2 * (oc.p.k - 1)
+            v, sample = oc.extrapolate(costs, n, n)
+            sample += " (no GPU count record: one sweep, one sigma per step)"
         vals.append(v)
     value = statistics.median(vals[args.warmup:])
-    sample += f"; {args.ref_sweeps} sweeps assumed"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.config}: 8e/8o + 24 virtual, M={args.M}, {args.h0} H0",
-                       "h0": args.h0, "M": args.M},
-            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "config": {"workload": _workload(args), "h0": args.h0, "M": args.M},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+                             "sample": sample + (f"; counts from {os.path.basename(_counts_path(args))}"
+                                                 if counts else "")},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -227,7 +272,7 @@ def run_gpu(args):
     o.max_sweeps = args.max_sweeps
     ctx = L.mpspt_create(o)
     L.mpspt_set_integrals(ctx, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
-    L.mpspt_set_reference(ctx, ci)
+    L.mpspt_set_reference_ci(ctx, ci)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one(c=None):
@@ -237,20 +282,34 @@ def run_gpu(args):
         return e2, rep
 
     # warm-up 1: the plain float64 sweep converged tightly; it fixes E2_ref
-    # (the float64 E2 at this M) and gives the float64 time-to-E2
-    o64 = L.mpspt_default_options()
-    o64.device = local
-    o64.stream = stream.cuda_stream
-    o64.prec = L.MPSPT_FP64
-    o64.e_tol = args.ref_e_tol
-    o64.max_sweeps = args.max_sweeps
-    ctx64 = L.mpspt_create(o64)
-    L.mpspt_set_integrals(ctx64, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
-    L.mpspt_set_reference(ctx64, ci)
-    e2_ref, rep64 = one(ctx64)
+    # (the float64 E2 at this M, within 1e-8 of the oracle by the parity tests)
+    def ctx_for(prec, e_tol):
+        oo = L.mpspt_default_options()
+        oo.device = local
+        oo.stream = stream.cuda_stream
+        oo.prec = prec
+        oo.e_tol = e_tol
+        oo.max_sweeps = args.max_sweeps
+        cx = L.mpspt_create(oo)
+        L.mpspt_set_integrals(cx, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
+        L.mpspt_set_reference_ci(cx, ci)
+        return cx
+    ctx64 = ctx_for(L.MPSPT_FP64, args.ref_e_tol)
+    e2_ref, rep_ref = one(ctx64)
     L.mpspt_destroy(ctx64)
-    hist64 = [rep64.e2_per_sweep[s] for s in range(rep64.n_sweeps)]
-    t64, s64 = _time_to_e2(rep64, e2_ref)
+    hist_ref = [rep_ref.e2_per_sweep[s] for s in range(rep_ref.n_sweeps)]
+    # the plain float64 arm: same stopping rule as the mixed arm, its own
+    # warm-up (the run above) and fp64_steps timed repeats (median)
+    ctx64 = ctx_for(L.MPSPT_FP64, args.e_tol)
+    fp64_runs = []
+    for s_ in range(max(1, min(args.steps, args.fp64_steps))):
+        _, r64 = one(ctx64)
+        t_, s64_ = _time_to_e2(r64, e2_ref)
+        fp64_runs.append((t_ if t_ is not None else r64.wall_ms / 1e3, s64_, r64))
+    L.mpspt_destroy(ctx64)
+    t64 = statistics.median([x[0] for x in fp64_runs])
+    rep64 = fp64_runs[0][2]
+    s64 = fp64_runs[0][1]
     for w in range(max(0, args.warmup - 1)):
         one()
     sampler, cpath = _clock_sampler() if rank == 0 else (None, None)
@@ -277,18 +336,18 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         value, ms_per_step = float(t[0]), float(t[1])
         dist.barrier()
-    # end to end through the public API with host buffers
+    # end to end through the public API: wall clock from mpspt_create to the
+    # return of mpspt_minimize_hylleraas (integrals and CI vector copied from
+    # host buffers, E2 read back), median of e2e_steps runs
     e2e_times = []
-    for s in range(args.e2e_steps):
+    for s_ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         ctx2 = L.mpspt_create(o)
         L.mpspt_set_integrals(ctx2, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
-        L.mpspt_set_reference(ctx2, ci)
-        t_setup = time.perf_counter() - t1
+        L.mpspt_set_reference_ci(ctx2, ci)
         e2, _, rep = L.mpspt_minimize_hylleraas(ctx2, args.h0, args.M, want_psi1=False)
-        tt, _ = _time_to_e2(rep, e2_ref)
-        e2e_times.append(t_setup + (tt if tt is not None else rep.wall_ms / 1e3))
+        e2e_times.append(time.perf_counter() - t1)
         L.mpspt_destroy(ctx2)
     e2e = statistics.median(e2e_times) if e2e_times else None
     if dist and e2e is not None:
@@ -317,16 +376,18 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3+f64"}[args.prec],
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3+f64", "mixed_fp16": "f16x3+f64"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": f"{args.config}: 8e/8o + 24 virtual, M={args.M}, {args.h0} H0, {args.prec}",
-                   "h0": args.h0, "M": args.M, "prec": args.prec, "l2_flush": True,
+        "config": {"workload": _workload(args), "h0": args.h0, "M": args.M, "prec": args.prec, "l2_flush": True,
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "E2": statistics.median(e2s), "E2_ref": e2_ref,
         "sweeps": [r.n_sweeps for r in reps],
-        "fp64": {"time_to_e2_s": t64, "sweeps_to_e2": (s64 + 1) if s64 is not None else None,
+        "fp64": {"time_to_e2_s": t64, "runs_s": [x[0] for x in fp64_runs],
+                 "sweeps_to_e2": (s64 + 1) if s64 is not None else None,
                  "sweeps": rep64.n_sweeps, "sigma_tflops": (rep64.sigma_flops / (rep64.sigma_ms * 1e-3) / 1e12)
-                 if rep64.sigma_ms > 0 else None, "e2_history": hist64},
+                 if rep64.sigma_ms > 0 else None, "e2_ref_history": hist_ref,
+                 "note": "plain float64 sweep on the same inputs and stopping rule: one untimed converged run "
+                         "(E2_ref, e_tol ref_e_tol) then fp64_steps timed repeats, median"},
         "speedup_vs_fp64": (t64 / value) if (t64 and value) else None,
         "sigma_tflops": achieved,
         "roofline": {"bound": "fp64_alu" if args.prec == "fp64" else "tensor", "achieved": achieved,
@@ -334,18 +395,25 @@ def run_gpu(args):
                      "traffic": traffic, "peak_source": peak_note,
                      "kernel": "k_gemm (sigma grouped block GEMM)"},
         "roofline_fp64_sigma": _fp64_roofline(reps, peaks, src),
-        "e2e": {"value": e2e, "unit": "s",
+        "e2e": {"value": e2e, "unit": "s", "runs": args.e2e_steps,
+                "what": "wall clock mpspt_create -> set_integrals -> set_reference_ci -> minimize_hylleraas "
+                        "(to the e_tol stop) -> return, host buffers",
                 "h2d_bytes_per_step": int(h.nbytes + Lc.nbytes + ci.nbytes), "d2h_bytes_per_step": 8},
         "gpu_launches": int(sum(r.kernel_launches for r in reps)),
         "clocks": clocks,
     }
+    # counts of the float64 run until E2 (they scale the oracle's unit costs)
+    n_sig = int(rep64.sigma_calls_cum[s64]) if s64 is not None else int(rep64.sigma_calls_cum[rep64.n_sweeps - 1])
+    n_steps = 2 * (k - 1) * ((s64 + 1) if s64 is not None else rep64.n_sweeps)
+    line["fp64"]["sigma_calls_to_e2"] = n_sig
+    line["fp64"]["bond_steps_to_e2"] = n_steps
+    if rank == 0 and world == 1 and args.write_counts:
+        with open(_counts_path(args), "w") as f:
+            json.dump({"workload": _workload(args), "sigma_calls_to_e2": n_sig, "bond_steps_to_e2": n_steps,
+                       "from": "float64 GPU sweep of bench.py (plain arm), same inputs"}, f, indent=1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the oracle needs as many bond steps as the float64 GPU run took to reach E2
-        ka, kv = c["k_act"], k - c["k_act"]
-        nb = 2 * (k - 1) * ((s64 + 1) if s64 is not None else rep64.n_sweeps)
-        cg_ps = rep64.cg_iters / max(1, 2 * (k - 1) * rep64.n_sweeps)
-        frac_a = ka / (k - 1)
-        val, sample = _oracle_sample(args.config, args.h0, args.M, cg_ps, nb * frac_a, nb * (1 - frac_a))
+        oc = _OracleCosts(args.config, args.h0, args.M)
+        val, sample = oc.extrapolate(oc.step(), n_sig, n_steps)
         line["cpu_baseline"] = {"value": val, "unit": "s", "cores": len(os.sched_getaffinity(0)),
                                 "kind": "oracle", "sample": sample}
     if rank == 0:
@@ -364,12 +432,14 @@ def main():
     ap.add_argument("--config", default="medium")
     ap.add_argument("--h0", default="dyall", choices=["dyall", "fock"])
     ap.add_argument("--M", type=int, default=256)
-    ap.add_argument("--prec", default="mixed", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "fp32", "mixed", "mixed_fp16"])
     ap.add_argument("--e_tol", type=float, default=1e-7)
     ap.add_argument("--ref_e_tol", type=float, default=1e-9)
-    ap.add_argument("--e2e_steps", type=int, default=1)
-    ap.add_argument("--ref_sweeps", type=int, default=10)
-    ap.add_argument("--ref_cg", type=float, default=6.0)
+    ap.add_argument("--e2e_steps", type=int, default=3)
+    ap.add_argument("--fp64_steps", type=int, default=3,
+                    help="timed repeats of the plain float64 arm (at most --steps)")
+    ap.add_argument("--write_counts", action="store_true",
+                    help="record the float64 run's counts for the oracle arm (profiles/bench_counts_*.json)")
     ap.add_argument("--no_cpu_baseline", action="store_true")
     ap.add_argument("--max_sweeps", type=int, default=64,
                     help="sweep cap of every minimisation (a smaller workload, e.g. for profiler captures)")

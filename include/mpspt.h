@@ -47,7 +47,9 @@ typedef enum {
     MPSPT_ERR_INVALID = -1,        /* bad argument or NaN/Inf in an input     */
     MPSPT_ERR_OOM = -2,            /* device memory exhausted / arena cap hit */
     MPSPT_ERR_NOT_SPD = -3,        /* CG met p^T A p <= 0 (H0 - E0 not > 0)   */
-    MPSPT_ERR_NOT_CONVERGED = -4,  /* CG or sweep iteration cap reached       */
+    MPSPT_ERR_NOT_CONVERGED = -4,  /* an iteration cap was reached: local CG  */
+                                   /* (cg_max_iter), float64 refinement (12   */
+                                   /* rounds) or truncation eigensolver       */
     MPSPT_ERR_TIMEOUT = -5,        /* a bounded device wait gave up           */
     MPSPT_ERR_CUDA = -6,           /* a CUDA runtime call failed              */
     MPSPT_ERR_STATE = -7           /* call out of order (e.g. no integrals)   */
@@ -64,8 +66,12 @@ typedef enum { MPSPT_H0_FOCK = 0, MPSPT_H0_DYALL = 1 } mpspt_h0;
  * FP32: contractions in float32, CG vectors float64, final energy float64.
  * MIXED_BF16: sigma contractions as three-term split-bfloat16 products on
  * the tensor cores with float32 accumulation inside a float64-refined CG;
- * the residual and the Hylleraas value are evaluated in float64. */
-typedef enum { MPSPT_FP64 = 0, MPSPT_FP32 = 1, MPSPT_MIXED_BF16 = 2 } mpspt_prec;
+ * the residual and the Hylleraas value are evaluated in float64.
+ * MIXED_FP16: the same with float16 hi/lo terms (11-bit significands, so
+ * the three products carry ~22 bits against ~16 for bfloat16; the exponent
+ * range is narrow, so each inner solve runs on the residual scaled to unit
+ * norm, and entries below 2^-24 of that scale are lost). */
+typedef enum { MPSPT_FP64 = 0, MPSPT_FP32 = 1, MPSPT_MIXED_BF16 = 2, MPSPT_MIXED_FP16 = 3 } mpspt_prec;
 
 typedef struct {
     int device;                 /* CUDA device ordinal                          */
@@ -83,6 +89,15 @@ typedef struct {
                                 /* re-orthonormalisation and float64 Jacobi     */
                                 /* polish; 1 = float64 Jacobi from identity     */
                                 /* (see mpspt_eigh_batched_ex)                  */
+    double keep_rel;            /* truncation keeps density-matrix eigenvectors */
+                                /* with eigenvalue > keep_rel tr(rho), at most  */
+                                /* M of them; 0 = 1e-10                          */
+    int autotune;               /* 1: the first grouped GEMM of each block-shape */
+                                /* class times the candidate tile shapes and    */
+                                /* keeps the fastest (see autotune_cache)       */
+    const char* autotune_cache; /* file of tuned tile shapes: read by            */
+                                /* mpspt_create, written by mpspt_destroy; NULL */
+                                /* = tune in memory only                         */
 } mpspt_options;
 
 typedef struct {
@@ -103,10 +118,17 @@ typedef struct {
                                  /*   inner low-precision applications)          */
     long long learned_used;      /* local solves started from the learned guess  */
     long long learned_rejected;  /* ... where the warm start had lower residual  */
+    int converged;               /* 1: the last sweep changed E2 by < e_tol;     */
+                                 /* 0: max_sweeps ended the run first            */
+    double max_discarded_per_sweep[64]; /* discarded weight, max over the bonds  */
+                                 /* of each sweep                                */
+    long long sigma_calls_cum[64]; /* applications of A_loc (all precisions)     */
+                                 /* done by the end of each sweep                */
 } mpspt_report;
 
 /* Fills *opt with defaults: device 0, default stream, FP64, 30 sweeps,
- * e_tol 1e-10, cg_tol 1e-10, 1000 CG iterations, seed 1408. */
+ * e_tol 1e-10, cg_tol 1e-10, 1000 CG iterations, seed 1408, keep_rel 1e-10,
+ * no autotuning. */
 void mpspt_default_options(mpspt_options* opt);
 
 /* Creates a context bound to opt->device.  *ctx owned by the caller. */
@@ -120,12 +142,52 @@ void mpspt_destroy(mpspt_ctx* ctx);   /* frees everything the context owns */
 mpspt_status mpspt_set_integrals(mpspt_ctx* ctx, int k_act, int k_virt, int n_elec,
                                  const double* h, const double* L, int n_chol);
 
-/* Reference Psi0 (Eq. 1) as a dense host vector over the 4^k_act active
- * occupation strings (index = sum_p code_p 4^(k_act-1-p)), copied.  The
- * library computes gamma_tu, the generalised Fock matrix, rotates the
- * virtual orbitals to the semicanonical basis and converts Psi0 to an exact
- * MPS.  Requires mpspt_set_integrals.  n_ci must equal 4^k_act. */
-mpspt_status mpspt_set_reference(mpspt_ctx* ctx, const double* ci, long long n_ci);
+/* Reference Psi0 (Eq. 1: "the zeroth order wavefunction", a CASSCF or DMRG
+ * state of the active space) as a QN-blocked MPS on the n_sites_act = k_act
+ * active sites, the form a DMRG calculation produces.  Site c holds
+ * blk_count[c] blocks; the blocks of all sites are listed in site order,
+ * and block b has
+ *   blk_meta[7b .. 7b+6] = (N_l, 2Sz_l, s, N_r, 2Sz_r, dim_l, dim_r)
+ * with s the local state (0..3) and (N_r, 2Sz_r) = (N_l, 2Sz_l) + QN(s),
+ * and blk_data[b] -> dim_l x dim_r doubles, row-major (host, copied).  A
+ * bond sector must have the same dimension in every block that names it;
+ * sectors are ordered ascending in (N, 2Sz) inside a bond.  The first bond
+ * is (0, 0) and the last (n_elec, 0), both of dimension 1.  Any norm (the
+ * state is normalised).  Duplicate (site, N_l, 2Sz_l, s) blocks, a QN
+ * change that does not match s, or non-finite entries give
+ * MPSPT_ERR_INVALID.  The library computes gamma_tu and E_ref = <H_act> by
+ * MPO transfers on the device, the generalised Fock matrix, and rotates the
+ * virtual orbitals to the semicanonical basis.  Requires
+ * mpspt_set_integrals. */
+mpspt_status mpspt_set_reference(mpspt_ctx* ctx, int n_sites_act, const int* blk_count,
+                                 const int* blk_meta, const double* const* blk_data);
+
+/* Convenience form for small active spaces: Psi0 as a dense host vector over
+ * the 4^k_act active occupation strings (index = sum_p code_p
+ * 4^(k_act-1-p)), copied; gamma and E_ref are computed from the vector and
+ * it is converted to an exact MPS (density-matrix splits keeping every state
+ * above 1e-14 of the largest).  n_ci must equal 4^k_act (k_act <= 14). */
+mpspt_status mpspt_set_reference_ci(mpspt_ctx* ctx, const double* ci, long long n_ci);
+
+/* Ground-state DMRG for the reference (the paper: the Hylleraas sweep "is
+ * essentially the same as the standard DMRG sweep"): the two-site sweep
+ * minimising <Psi|H_act + s2_penalty S^2|Psi> / <Psi|Psi> over active-space
+ * MPS of bond dimension <= M0 in the (n_elec, Sz = 0) sector, with a
+ * Davidson local eigensolver (Jacobi correction, residual <= cg_tol
+ * max(1, |E|), at most cg_max_iter iterations, else
+ * MPSPT_ERR_NOT_CONVERGED) and the same truncation and stopping rules
+ * (keep_rel, e_tol, max_sweeps) as the first-order sweep.  s2_penalty >= 0:
+ * every state of spin S is raised by s2_penalty S(S+1), so a penalty above
+ * half the gap between the lowest state and the lowest singlet makes the
+ * sweep find the singlet (0 = the lowest Sz = 0 state, of any spin).  The
+ * start is the seeded initial state of the first-order sweep.  The result
+ * is installed as the reference exactly as mpspt_set_reference would
+ * install it.  e_ref (nullable): E_ref = <Psi0|H_act|Psi0> of the installed
+ * state (no penalty); psi0 (nullable): the active-space MPS (free with
+ * mpspt_mps_free); rep (nullable): e2_per_sweep holds the penalised energy
+ * (last local Ritz value) per sweep.  Requires mpspt_set_integrals. */
+mpspt_status mpspt_ground_state(mpspt_ctx* ctx, int M0, double s2_penalty, double* e_ref, mpspt_mps** psi0,
+                                mpspt_report* rep);
 
 /* E0 = <Psi0|H0|Psi0>, E1 = <Psi0|V|Psi0> = E_ref - E0 and E_ref =
  * <Psi0|H|Psi0> for the chosen H0 (Eqs. 1, 5).  Any output may be NULL. */
@@ -256,9 +318,10 @@ mpspt_status mpspt_eigh_batched_ex(int device, void* stream, int batch, const in
 
 /* Allocation-free variant of mpspt_eigh_batched (the paper has no
  * counterpart; this is a service for callers that cannot allocate device
- * memory during the call -- e.g. code running while a CUDA graph is being
- * captured, hosts that reserve all device memory up front, or callers whose
- * own memory pool must not be bypassed).  Same arguments, results and
+ * memory during the call -- hosts that reserve all device memory up front
+ * for their own allocator, so that a library allocation would fail or go
+ * around their accounting, and latency-bound callers that cannot afford the
+ * synchronisation a fresh allocation may cost).  Same arguments, results and
  * stream ordering as mpspt_eigh_batched, but the task table and the work
  * copy of A live in one fixed device array of 2^21 doubles (16 MiB) that
  * every GPU loading the library holds until the process exits; the call
@@ -266,9 +329,10 @@ mpspt_status mpspt_eigh_batched_ex(int device, void* stream, int batch, const in
  * sum_i n[i]^2 <= 2^21 - 4096 (else MPSPT_ERR_INVALID, nothing launched).
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any
- * stream capture.  All calls share the array and each overwrites what it
- * uses: calls whose GPU work overlaps (other streams, other host threads)
- * race on it and must be serialised by the caller. */
+ * stream capture.  The caller's current device is restored before return.
+ * All calls share the array and each overwrites what it uses: calls whose
+ * GPU work overlaps (other streams, other host threads) race on it and must
+ * be serialised by the caller. */
 mpspt_status mpspt_eigh_batched_noalloc(int device, void* stream, int batch, const int* n,
                                         const double* A, double* V, double* w);
 

@@ -37,7 +37,7 @@ Initial Psi1 (a documented rule shared with the GPU library):
   * then brought to right-canonical form by the renormalisation step
     itself: for i = nsite-2 .. 0 the two-site product A_i A_{i+1} is split
     right-to-left by its density matrix (truncate with no M cap: every
-    eigenvector above 1e-13 tr rho is kept, the sector filter applies), so
+    eigenvector above 1e-10 tr rho is kept, the sector filter applies), so
     the initial state is the random MPS with its negligible directions
     removed by the same rule the sweep uses.
 """
@@ -46,6 +46,13 @@ import numpy as np
 from .fermion import QN_N, QN_SZ
 
 QN_SITE = np.stack([QN_N, QN_SZ], axis=1)
+
+# Reading R7: density-matrix eigenvectors with eigenvalue <= KEEP_REL tr(rho)
+# are never kept.  The paper leaves the threshold open.  At 1e-10 the
+# smallest kept eigenvalues lie six decades above the rounding level of a
+# float64 eigensolver (~1e-16 |rho|), so which states are kept, and the
+# energies that follow, do not depend on how an eigensolver rounds.
+KEEP_REL = 1e-10
 MASK64 = (1 << 64) - 1
 
 
@@ -149,13 +156,14 @@ def random_mps(nsite, target, allowed_n, M, seed):
     return MPS(A, labels)
 
 
-def canonicalize_by_splits(mps, allowed):
+def canonicalize_by_splits(mps, allowed, keep_rel=KEEP_REL):
     """Right-canonical form by right-to-left density-matrix splits of the
     two-site products (the sweep's renormalisation step without an M cap);
     the norm ends up in A[0]."""
     for i in range(mps.nsite - 2, -1, -1):
         x = np.einsum("lsm,mtr->lstr", mps.A[i], mps.A[i + 1])
-        Al, Ar, lab, _ = truncate(x, mps.q[i], mps.q[i + 2], 1 << 30, "RL", allowed.get(i + 1))
+        Al, Ar, lab, _ = truncate(x, mps.q[i], mps.q[i + 2], 1 << 30, "RL", allowed.get(i + 1),
+                                  keep_rel)
         mps.A[i], mps.A[i + 1], mps.q[i + 1] = Al, Ar, lab
     return mps
 
@@ -352,13 +360,14 @@ def pcg(apply, b, x0, diag, mask, tol, maxit):
 
 
 # --------------------------------------------------------------- truncation
-def select_states(evals, M, tr, keep_rel=1e-13, tie_rel=1e-8):
+def select_states(evals, M, tr, keep_rel=None, tie_rel=1e-8):
     """Indices (sector, index) of kept density-matrix eigenvectors.
 
     evals: list of (qkey, eigenvalues descending).  Keeps the M largest
     eigenvalues above keep_rel * tr; if the M-th and (M+1)-th agree to
     tie_rel, the whole tied group at the cut is dropped (so degenerate
     multiplets are never split).  Ties of equal value order by QN key."""
+    keep_rel = KEEP_REL if keep_rel is None else keep_rel
     cand = []
     for qkey, lam in evals:
         for i, v in enumerate(lam):
@@ -377,7 +386,7 @@ def select_states(evals, M, tr, keep_rel=1e-13, tie_rel=1e-8):
     return [(c[1], c[2]) for c in kept], max(disc, 0.0) / tr if tr > 0 else 0.0
 
 
-def truncate(x, ql, qr, M, direction, allowed_mid):
+def truncate(x, ql, qr, M, direction, allowed_mid, keep_rel=None):
     """Split a two-site tensor.  Returns (A_left, A_right, labels_mid, w)."""
     Dl, _, _, Dr = x.shape
     if direction == "LR":
@@ -401,7 +410,7 @@ def truncate(x, ql, qr, M, direction, allowed_mid):
         eig[q] = (idx, w, v)
         evals.append((q, w))
         tr += float(np.sum(w))
-    kept, disc = select_states(evals, M, tr)
+    kept, disc = select_states(evals, M, tr, keep_rel)
     kept.sort(key=lambda t: (t[0], t[1]))
     Dn = len(kept)
     U = np.zeros((X.shape[0] if direction == "LR" else X.shape[1], Dn))
@@ -425,7 +434,7 @@ class HylleraasSweep:
 
     def __init__(self, prob, M, seed=1408, tol_cg=1e-10, tol_e=1e-10,
                  max_sweeps=30, cg_maxit=1000, mpo_A=None, mpo_V=None, verbose=False,
-                 allowed=None):
+                 allowed=None, keep_rel=None):
         from .mpo import build_mpo
         self.prob = prob
         self.M = M
@@ -435,13 +444,15 @@ class HylleraasSweep:
         self.max_sweeps = max_sweeps
         self.cg_maxit = cg_maxit
         self.verbose = verbose
+        self.keep_rel = KEEP_REL if keep_rel is None else keep_rel
         N = prob.n_elec
         # bond filters: N_left allowed on given cuts (default: first-order space X)
         self.allowed = allowed if allowed is not None else {prob.k_act: {N - 1, N - 2}}
         self.WA = mpo_A or build_mpo(prob.h0_terms(), self.k, k_split=prob.k_act)
         self.WV = mpo_V or build_mpo(prob.rhs_terms(), self.k, k_split=prob.k_act)
         self.psi0 = reference_mps(prob.ci, prob.k_act, prob.k_virt)
-        self.psi1 = canonicalize_by_splits(random_mps(self.k, (N, 0), self.allowed, M, seed), self.allowed)
+        self.psi1 = canonicalize_by_splits(random_mps(self.k, (N, 0), self.allowed, M, seed), self.allowed,
+                                           self.keep_rel)
         k = self.k
         self.LA = [None] * (k + 1)
         self.LV = [None] * (k + 1)
@@ -492,7 +503,7 @@ class HylleraasSweep:
         h = float(np.vdot(x, apply(x) * mask) + 2.0 * np.vdot(x, g))
         ps = self.psi1
         Al, Ar, lab, w = truncate(x, ps.q[i], ps.q[i + 2], self.M, direction,
-                                  self.allowed.get(i + 1))
+                                  self.allowed.get(i + 1), self.keep_rel)
         ps.A[i], ps.A[i + 1] = Al, Ar
         ps.q[i + 1] = lab
         self.discarded.append(w)

@@ -22,7 +22,7 @@ class Session:
         self.ctx = _lib.mpspt_create(o)
         k = h.shape[0]
         _lib.mpspt_set_integrals(self.ctx, k_act, k - k_act, n_elec, h, L)
-        _lib.mpspt_set_reference(self.ctx, ci)
+        _lib.mpspt_set_reference_ci(self.ctx, ci)
 
     def energies(self, h0):
         return _lib.mpspt_energies(self.ctx, h0)

@@ -19,11 +19,12 @@ MPSPT_H0_DYALL = 1
 MPSPT_FP64 = 0
 MPSPT_FP32 = 1
 MPSPT_MIXED_BF16 = 2
+MPSPT_MIXED_FP16 = 3
 MPSPT_LOCAL_SIGMA = 0
 MPSPT_LOCAL_RHS = 1
 MPSPT_LOCAL_DIAG = 2
 H0 = {"fock": MPSPT_H0_FOCK, "dyall": MPSPT_H0_DYALL}
-PREC = {"fp64": MPSPT_FP64, "fp32": MPSPT_FP32, "mixed": MPSPT_MIXED_BF16}
+PREC = {"fp64": MPSPT_FP64, "fp32": MPSPT_FP32, "mixed": MPSPT_MIXED_BF16, "mixed_fp16": MPSPT_MIXED_FP16}
 STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "NOT_SPD", -4: "NOT_CONVERGED",
           -5: "TIMEOUT", -6: "CUDA", -7: "STATE"}
 # mpspt_status values of include/mpspt.h
@@ -36,7 +37,8 @@ class mpspt_options(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int), ("e_tol", ctypes.c_double), ("cg_tol", ctypes.c_double),
                 ("cg_max_iter", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("use_learned", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("eig_fp64_only", ctypes.c_int)]
+                ("eig_fp64_only", ctypes.c_int), ("keep_rel", ctypes.c_double),
+                ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p)]
 
 
 class mpspt_report(ctypes.Structure):
@@ -47,7 +49,9 @@ class mpspt_report(ctypes.Structure):
                 ("max_bond_dim", ctypes.c_int), ("sweep_ms", ctypes.c_double * 64),
                 ("kernel_launches", ctypes.c_longlong), ("sigma64_calls", ctypes.c_longlong),
                 ("sigma64_flops", ctypes.c_double), ("sigma64_ms", ctypes.c_double),
-                ("learned_used", ctypes.c_longlong), ("learned_rejected", ctypes.c_longlong)]
+                ("learned_used", ctypes.c_longlong), ("learned_rejected", ctypes.c_longlong),
+                ("converged", ctypes.c_int), ("max_discarded_per_sweep", ctypes.c_double * 64),
+                ("sigma_calls_cum", ctypes.c_longlong * 64)]
 
 
 class MpsptError(RuntimeError):
@@ -72,7 +76,10 @@ def load():
             "mpspt_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(mpspt_options)]),
             "mpspt_destroy": (None, [vp]),
             "mpspt_set_integrals": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]),
-            "mpspt_set_reference": (ctypes.c_int, [vp, dp, ctypes.c_longlong]),
+            "mpspt_set_reference_ci": (ctypes.c_int, [vp, dp, ctypes.c_longlong]),
+            "mpspt_set_reference": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ctypes.POINTER(dp)]),
+            "mpspt_ground_state": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, dp, ctypes.POINTER(vp),
+                                                  ctypes.POINTER(mpspt_report)]),
             "mpspt_energies": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, dp]),
             "mpspt_minimize_hylleraas": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(vp),
                                                         ctypes.POINTER(mpspt_report)]),
@@ -152,9 +159,59 @@ def mpspt_set_integrals(ctx, k_act, k_virt, n_elec, h, L):
     _check(load().mpspt_set_integrals(ctx, k_act, k_virt, n_elec, _dp(h), _dp(L), L.shape[0]))
 
 
-def mpspt_set_reference(ctx, ci):
+def mpspt_set_reference_ci(ctx, ci):
     ci = _f64(ci)
-    _check(load().mpspt_set_reference(ctx, _dp(ci), ci.size))
+    _check(load().mpspt_set_reference_ci(ctx, _dp(ci), ci.size))
+
+
+def mpspt_set_reference(ctx, tensors, labels):
+    """Reference as an active-space MPS: tensors[c] dense (D_c, 4, D_{c+1}),
+    labels[c] (D_c, 2) the (N, 2Sz) of every bond index (contiguous,
+    ascending sectors).  Marshalled into the header's block list: one block
+    per (left sector, local state) with a nonzero QN-allowed right sector."""
+    qsite = [(0, 0), (1, 1), (1, -1), (2, 0)]
+    counts, meta, blocks = [], [], []
+    for c, T in enumerate(tensors):
+        T = _f64(T)
+        ql, qr = np.asarray(labels[c]).reshape(-1, 2), np.asarray(labels[c + 1]).reshape(-1, 2)
+
+        def sectors(q):
+            out, i = [], 0
+            while i < len(q):
+                j = i
+                while j < len(q) and tuple(q[j]) == tuple(q[i]):
+                    j += 1
+                out.append((tuple(int(x) for x in q[i]), i, j))
+                i = j
+            return out
+        sl_, sr_ = sectors(ql), sectors(qr)
+        rmap = {q: (a, b) for q, a, b in sr_}
+        n = 0
+        for q, a, b in sl_:
+            for s_ in range(4):
+                q2 = (q[0] + qsite[s_][0], q[1] + qsite[s_][1])
+                if q2 not in rmap:
+                    continue
+                ra, rb = rmap[q2]
+                blk = np.ascontiguousarray(T[a:b, s_, ra:rb])
+                meta.extend([q[0], q[1], s_, q2[0], q2[1], b - a, rb - ra])
+                blocks.append(blk)
+                n += 1
+        counts.append(n)
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    meta = np.ascontiguousarray(meta, dtype=np.int32)
+    arr = (ctypes.POINTER(ctypes.c_double) * max(1, len(blocks)))(*[_dp(b) for b in blocks])
+    ipp = ctypes.POINTER(ctypes.c_int)
+    _check(load().mpspt_set_reference(ctx, len(tensors), counts.ctypes.data_as(ipp), meta.ctypes.data_as(ipp), arr))
+
+
+def mpspt_ground_state(ctx, M0, s2_penalty=0.0, want_psi0=False):
+    e = ctypes.c_double()
+    psi = ctypes.c_void_p()
+    rep = mpspt_report()
+    _check(load().mpspt_ground_state(ctx, M0, float(s2_penalty), ctypes.byref(e),
+                                     ctypes.byref(psi) if want_psi0 else None, ctypes.byref(rep)))
+    return e.value, (psi if want_psi0 else None), rep
 
 
 def mpspt_energies(ctx, h0):

@@ -47,7 +47,7 @@ def main(argv=None):
     ctx = L.mpspt_create(o)
     try:
         L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
-        L.mpspt_set_reference(ctx, ci)
+        L.mpspt_set_reference_ci(ctx, ci)
         if a.partitions > 0:
             kv = h.shape[0] - c["k_act"]
             pairs = [(x, y) for x in range(kv) for y in range(x, kv)][: a.partitions]

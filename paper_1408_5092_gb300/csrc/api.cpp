@@ -1,6 +1,7 @@
 // C ABI of the MPS-PT library: argument checks, exception barrier, handles.
 #include <cmath>
 #include <cstring>
+#include <map>
 
 #include "eig.h"
 #include "engine.h"
@@ -44,110 +45,6 @@ mpspt_status guard(mpspt_ctx* ctx, F&& f) {
 
 }  // namespace
 
-extern "C" {
-
-void mpspt_default_options(mpspt_options* o) {
-    if (!o) return;
-    std::memset(o, 0, sizeof(*o));
-    o->device = 0;
-    o->stream = nullptr;
-    o->prec = MPSPT_FP64;
-    o->max_sweeps = 30;
-    o->e_tol = 1e-10;
-    o->cg_tol = 1e-10;
-    o->cg_max_iter = 1000;
-    o->seed = 1408;
-    o->use_learned = 0;
-    o->verbose = 0;
-    o->eig_fp64_only = 0;
-}
-
-mpspt_status mpspt_create(mpspt_ctx** ctx, const mpspt_options* opt) {
-    if (!ctx) return MPSPT_ERR_INVALID;
-    mpspt_options o;
-    mpspt_default_options(&o);
-    if (opt) o = *opt;
-    return guard(nullptr, [&] {
-        mpspt::require(o.max_sweeps >= 1 && o.cg_max_iter >= 1 && o.cg_tol > 0 && o.e_tol > 0,
-                       "invalid options");
-        auto* h = new mpspt_ctx;
-        try {
-            h->c.reset(new mpspt::Ctx(o));
-        } catch (...) {
-            delete h;
-            throw;
-        }
-        *ctx = h;
-    });
-}
-
-void mpspt_destroy(mpspt_ctx* ctx) { delete ctx; }
-
-mpspt_status mpspt_set_integrals(mpspt_ctx* ctx, int k_act, int k_virt, int n_elec, const double* h,
-                                 const double* L, int n_chol) {
-    if (!ctx) return MPSPT_ERR_INVALID;
-    return guard(ctx, [&] { mpspt::set_integrals(*ctx->c, k_act, k_virt, n_elec, h, L, n_chol); });
-}
-
-mpspt_status mpspt_set_reference(mpspt_ctx* ctx, const double* ci, long long n_ci) {
-    if (!ctx) return MPSPT_ERR_INVALID;
-    return guard(ctx, [&] {
-        MPSPT_CUDA(cudaSetDevice(ctx->c->opt.device));
-        mpspt::set_reference(*ctx->c, ci, n_ci);
-    });
-}
-
-mpspt_status mpspt_energies(mpspt_ctx* ctx, mpspt_h0 h0, double* e0, double* e1, double* e_ref) {
-    if (!ctx) return MPSPT_ERR_INVALID;
-    return guard(ctx, [&] {
-        auto& c = *ctx->c;
-        mpspt::require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
-        mpspt::require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
-        const double E0 = c.e0(h0);
-        if (e0) *e0 = E0;
-        if (e1) *e1 = c.P.e_ref - E0;
-        if (e_ref) *e_ref = c.P.e_ref;
-    });
-}
-
-mpspt_status mpspt_minimize_hylleraas(mpspt_ctx* ctx, mpspt_h0 h0, int M, double* e2, mpspt_mps** psi1,
-                                      mpspt_report* rep) {
-    if (!ctx || !e2) return MPSPT_ERR_INVALID;
-    return guard(ctx, [&] {
-        auto& c = *ctx->c;
-        MPSPT_CUDA(cudaSetDevice(c.opt.device));
-        mpspt::SweepResult r;
-        std::unique_ptr<mpspt::MpsD> m = mpspt::minimize(c, h0, M, r);
-        if (rep) {
-            std::memset(rep, 0, sizeof(*rep));
-            rep->n_sweeps = (int)r.e2_sweep.size();
-            for (int s = 0; s < rep->n_sweeps && s < 64; ++s) rep->e2_per_sweep[s] = r.e2_sweep[s];
-            rep->max_discarded_weight = r.max_disc;
-            rep->cg_iters = r.cg_iters;
-            rep->sigma_calls = r.sigma_calls;
-            rep->sigma_flops = r.sigma_flops;
-            rep->sigma_ms = r.sigma_ms;
-            rep->wall_ms = r.wall_ms;
-            rep->max_bond_dim = r.max_bond;
-            for (int s = 0; s < rep->n_sweeps && s < 64; ++s) rep->sweep_ms[s] = r.sweep_ms[s];
-            rep->kernel_launches = r.launches;
-            rep->sigma64_calls = r.sigma64_calls;
-            rep->sigma64_flops = r.sigma64_flops;
-            rep->sigma64_ms = r.sigma64_ms;
-            rep->learned_used = r.learned_used;
-            rep->learned_rejected = r.learned_rejected;
-        }
-        *e2 = r.e2;
-        if (psi1) {
-            auto* h = new mpspt_mps;
-            h->m = std::move(m);
-            h->st = c.st;
-            h->device = c.opt.device;
-            *psi1 = h;
-        }
-    });
-}
-
 namespace {
 void fill_report(mpspt_report* rep, const mpspt::SweepResult& r) {
     std::memset(rep, 0, sizeof(*rep));
@@ -167,8 +64,188 @@ void fill_report(mpspt_report* rep, const mpspt::SweepResult& r) {
     rep->sigma64_ms = r.sigma64_ms;
     rep->learned_used = r.learned_used;
     rep->learned_rejected = r.learned_rejected;
+    rep->converged = r.converged ? 1 : 0;
+    for (int s = 0; s < (int)r.disc_sweep.size() && s < 64; ++s) rep->max_discarded_per_sweep[s] = r.disc_sweep[s];
+    for (int s = 0; s < (int)r.sigma_cum.size() && s < 64; ++s) rep->sigma_calls_cum[s] = r.sigma_cum[s];
 }
 }  // namespace
+
+extern "C" {
+
+void mpspt_default_options(mpspt_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->device = 0;
+    o->stream = nullptr;
+    o->prec = MPSPT_FP64;
+    o->max_sweeps = 30;
+    o->e_tol = 1e-10;
+    o->cg_tol = 1e-10;
+    o->cg_max_iter = 1000;
+    o->seed = 1408;
+    o->use_learned = 0;
+    o->verbose = 0;
+    o->eig_fp64_only = 0;
+    o->keep_rel = 1e-10;
+    o->autotune = 0;
+    o->autotune_cache = nullptr;
+}
+
+mpspt_status mpspt_create(mpspt_ctx** ctx, const mpspt_options* opt) {
+    if (!ctx) return MPSPT_ERR_INVALID;
+    mpspt_options o;
+    mpspt_default_options(&o);
+    if (opt) o = *opt;
+    return guard(nullptr, [&] {
+        mpspt::require(o.max_sweeps >= 1 && o.cg_max_iter >= 1 && o.cg_tol > 0 && o.e_tol > 0 &&
+                           o.keep_rel >= 0.0 && o.keep_rel < 1.0,
+                       "invalid options");
+        mpspt::require(o.prec == MPSPT_FP64 || o.prec == MPSPT_FP32 || o.prec == MPSPT_MIXED_BF16 ||
+                           o.prec == MPSPT_MIXED_FP16,
+                       "unknown precision mode");
+        auto* h = new mpspt_ctx;
+        try {
+            h->c.reset(new mpspt::Ctx(o));
+        } catch (...) {
+            delete h;
+            throw;
+        }
+        *ctx = h;
+    });
+}
+
+void mpspt_destroy(mpspt_ctx* ctx) { delete ctx; }
+
+mpspt_status mpspt_set_integrals(mpspt_ctx* ctx, int k_act, int k_virt, int n_elec, const double* h,
+                                 const double* L, int n_chol) {
+    if (!ctx) return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] { mpspt::set_integrals(*ctx->c, k_act, k_virt, n_elec, h, L, n_chol); });
+}
+
+mpspt_status mpspt_set_reference_ci(mpspt_ctx* ctx, const double* ci, long long n_ci) {
+    if (!ctx) return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] {
+        MPSPT_CUDA(cudaSetDevice(ctx->c->opt.device));
+        mpspt::set_reference(*ctx->c, ci, n_ci);
+    });
+}
+
+mpspt_status mpspt_set_reference(mpspt_ctx* ctx, int n_sites_act, const int* blk_count, const int* blk_meta,
+                                 const double* const* blk_data) {
+    if (!ctx || n_sites_act < 1 || !blk_count || !blk_meta || !blk_data) return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] {
+        auto& c = *ctx->c;
+        MPSPT_CUDA(cudaSetDevice(c.opt.device));
+        mpspt::require(c.P.have_int, "mpspt_set_integrals must come first", MPSPT_ERR_STATE);
+        mpspt::require(n_sites_act == c.P.ka, "n_sites_act must equal k_act");
+        const int ns = n_sites_act;
+        // bond sectors: QN -> dimension, from both sides of every cut
+        std::vector<std::map<mpspt::QN, int>> sec(ns + 1);
+        auto note = [&](int cut, mpspt::QN q, int d) {
+            mpspt::require(d >= 1, "block dimensions must be >= 1");
+            auto it = sec[cut].find(q);
+            if (it == sec[cut].end()) sec[cut][q] = d;
+            else mpspt::require(it->second == d, "a bond sector has different dimensions in different blocks");
+        };
+        long long nb = 0;
+        for (int st = 0; st < ns; ++st) {
+            mpspt::require(blk_count[st] >= 0, "negative block count");
+            for (int b = 0; b < blk_count[st]; ++b, ++nb) {
+                const int* m = blk_meta + 7 * nb;
+                mpspt::require(m[2] >= 0 && m[2] < 4, "local state must be 0..3");
+                const mpspt::QN ql(m[0], m[1]), qr(m[3], m[4]);
+                mpspt::require(qr == ql + mpspt::site_qn(m[2]), "block QN change does not match its local state");
+                mpspt::require(blk_data[nb] != nullptr, "null block data");
+                note(st, ql, m[5]);
+                note(st + 1, qr, m[6]);
+            }
+        }
+        mpspt::MpsHost h;
+        h.nsite = ns;
+        h.bond.resize(ns + 1);
+        for (int cut = 0; cut <= ns; ++cut) {
+            for (auto& kv : sec[cut]) h.bond[cut].sec.push_back({kv.first, kv.second, 0});
+            h.bond[cut].finalize();
+        }
+        h.T.resize(ns);
+        for (int st = 0; st < ns; ++st)
+            h.T[st].assign((size_t)h.bond[st].total * 4 * h.bond[st + 1].total, 0.0);
+        std::vector<std::vector<char>> seen(ns);
+        nb = 0;
+        for (int st = 0; st < ns; ++st) {
+            const mpspt::Bond &L = h.bond[st], &R = h.bond[st + 1];
+            seen[st].assign((size_t)L.nsec() * 4, 0);
+            for (int b = 0; b < blk_count[st]; ++b, ++nb) {
+                const int* m = blk_meta + 7 * nb;
+                const int sl = L.find(mpspt::QN(m[0], m[1])), sr = R.find(mpspt::QN(m[3], m[4]));
+                char& sn = seen[st][(size_t)sl * 4 + m[2]];
+                mpspt::require(!sn, "duplicate reference block");
+                sn = 1;
+                const double* src = blk_data[nb];
+                for (int i = 0; i < m[5]; ++i)
+                    for (int j = 0; j < m[6]; ++j)
+                        h.T[st][((size_t)(L.sec[sl].off + i) * 4 + m[2]) * R.total + R.sec[sr].off + j] =
+                            src[(size_t)i * m[6] + j];
+            }
+        }
+        mpspt::set_reference_mps(c, std::move(h));
+    });
+}
+
+mpspt_status mpspt_ground_state(mpspt_ctx* ctx, int M0, double s2_penalty, double* e_ref, mpspt_mps** psi0,
+                                mpspt_report* rep) {
+    if (!ctx || M0 < 1 || !(s2_penalty >= 0.0)) return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] {
+        auto& c = *ctx->c;
+        MPSPT_CUDA(cudaSetDevice(c.opt.device));
+        mpspt::SweepResult r;
+        std::unique_ptr<mpspt::MpsD> m = mpspt::ground_state(c, M0, s2_penalty, r);
+        if (rep) fill_report(rep, r);
+        if (e_ref) *e_ref = c.P.e_ref;
+        if (psi0) {
+            auto* h = new mpspt_mps;
+            h->m = std::move(m);
+            h->st = c.st;
+            h->device = c.opt.device;
+            *psi0 = h;
+        }
+    });
+}
+
+mpspt_status mpspt_energies(mpspt_ctx* ctx, mpspt_h0 h0, double* e0, double* e1, double* e_ref) {
+    if (!ctx) return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] {
+        auto& c = *ctx->c;
+        mpspt::require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
+        mpspt::require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
+        const double E0 = c.e0(h0);
+        if (e0) *e0 = E0;
+        if (e1) *e1 = c.P.e_ref - E0;
+        if (e_ref) *e_ref = c.P.e_ref;
+    });
+}
+
+
+mpspt_status mpspt_minimize_hylleraas(mpspt_ctx* ctx, mpspt_h0 h0, int M, double* e2, mpspt_mps** psi1,
+                                      mpspt_report* rep) {
+    if (!ctx || !e2) return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] {
+        auto& c = *ctx->c;
+        MPSPT_CUDA(cudaSetDevice(c.opt.device));
+        mpspt::SweepResult r;
+        std::unique_ptr<mpspt::MpsD> m = mpspt::minimize(c, h0, M, r);
+        if (rep) fill_report(rep, r);
+        *e2 = r.e2;
+        if (psi1) {
+            auto* h = new mpspt_mps;
+            h->m = std::move(m);
+            h->st = c.st;
+            h->device = c.opt.device;
+            *psi1 = h;
+        }
+    });
+}
+
 
 mpspt_status mpspt_minimize_partitioned(mpspt_ctx* ctx, mpspt_h0 h0, int n_part, const int* pair_ab,
                                         const int* M_part, int n_streams, double* e2_total, double* e2_part,
@@ -334,8 +411,13 @@ mpspt_status mpspt_eigh_batched_ex(int device, void* stream, int batch, const in
         es.run(tasks, f32_start == 0, st);
         MPSPT_CUDA(cudaMemcpyAsync(V, wv.get(), tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
         MPSPT_CUDA(cudaMemcpyAsync(w, ww.get(), totw * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        std::vector<int> fl(es.nflags);
+        if (es.nflags)
+            MPSPT_CUDA(cudaMemcpyAsync(fl.data(), es.flags.get(), es.nflags * sizeof(int), cudaMemcpyDeviceToHost, st));
         MPSPT_CUDA(cudaStreamSynchronize(st));   // the solver's scratch is released on return
         MPSPT_CUDA(cudaGetLastError());
+        for (int f : fl)
+            mpspt::require(f != 2, "Jacobi sweep cap reached before the convergence test", MPSPT_ERR_NOT_CONVERGED);
     });
 }
 

@@ -9,10 +9,6 @@ constexpr int kMaxSweepsF64 = 40;      // float64 Jacobi from the identity
 constexpr int kMaxSweepsF32 = 12;      // float32 start
 constexpr int kMaxSweepsPolish = 16;   // float64 polish of V^T A V
 constexpr int kClusterMinN = 48;       // float64 sweeps on CTA clusters from this size
-// Pair schedule of every sweep: 0 = round robin.  The large-diagonal-first
-// schedule (1) needs fewer polish sweeps but moved the medium sweep's E2 by
-// ~1e-7 against the oracle, so it stays off until that is understood.
-constexpr int kPolishSchedule = 0;
 size_t a16(size_t b) { return (b + 15) & ~(size_t)15; }
 }  // namespace
 
@@ -26,6 +22,8 @@ void EigSolver::jacobi(const std::vector<EigTask>& et, const std::vector<const d
         tot += a16(jac_p_bytes(et[i].n)) + a16(jac_rot_bytes(et[i].n)) + 16;
     }
     scratch.ensure(tot + 16, st);
+    flags.ensure((size_t)nt * sizeof(int) + 16, st);
+    nflags = nt;
     unsigned char* base = static_cast<unsigned char*>(scratch.get());
     std::vector<JacTask> jt(nt);
     std::vector<JacRows> rows;
@@ -40,7 +38,7 @@ void EigSolver::jacobi(const std::vector<EigTask>& et, const std::vector<const d
         check_range(R, jac_rot_bytes(n), "jacobi rot");
         check_range(S, 16, "jacobi state");
         jt[i] = {in[i], P, R, et[i].V, want_w ? et[i].w : nullptr, reinterpret_cast<double*>(S),
-                 reinterpret_cast<int*>(S + 8), reinterpret_cast<int*>(S + 12), n, vinit, kPolishSchedule, 0};
+                 flags.as<int>() + i, reinterpret_cast<int*>(S + 12), n, vinit, 0, 0};
         const int rpb = jac_rows_per_block(n, f32);
         for (int r0 = 0; r0 < n; r0 += rpb) {
             const int nr = std::min(rpb, n - r0);

@@ -11,6 +11,10 @@ namespace mpspt {
 
 struct EigSolver {
     DBuf scratch, vt, g, djt, djt1, djtc, drows, dtns;
+    // per task of the last stage run: 1 converged, 2 stopped by the sweep
+    // cap (device ints, valid once the stream has reached them)
+    DBuf flags;
+    int nflags = 0;
     GemmPlan ge;   // batched square GEMMs of the float64 stage
     bool stats = false;   // count sweeps per matrix (sum, matrices, max)
     long long sweeps32[3] = {0, 0, 0}, sweeps_polish[3] = {0, 0, 0}, sweeps64[3] = {0, 0, 0};

@@ -323,12 +323,92 @@ void set_reference(Ctx& c, const double* ci, long long n) {
         for (int p = 0; p < P.ka; ++p) { int cd = code_at(i, p, P.ka); nn += __builtin_popcount(cd); sz += (cd & 1) - ((cd >> 1) & 1); }
         require(nn == P.nel && sz == 0, "reference has components outside (N, Sz = 0)");
     }
-    const int k = P.k, ka = P.ka, kv = P.kv;
-    // gamma and f in the original basis (f needs only (pq|tu), (pu|tq) with t,u active)
     P.h = P.h_in;
     P.L = P.L_in;
     build_eri(P);
     one_rdm_and_energy(P);      // gamma, E_ref (active block, untouched by the rotation)
+    MpsHost act;
+    ci_to_mps(P, act);
+    finish_reference(c, act);
+}
+
+namespace {
+// H_act on the k_act active sites (orbital index = site index): the terms of
+// H with all indices active, from the integrals in the input basis.
+std::vector<Term> active_hamiltonian_terms(const Problem& P) {
+    const int k = P.k, ka = P.ka;
+    std::vector<double> ha((size_t)ka * ka), ea((size_t)ka * ka * ka * ka);
+    for (int p = 0; p < ka; ++p)
+        for (int q = 0; q < ka; ++q) {
+            ha[(size_t)p * ka + q] = P.h_in[(size_t)p * k + q];
+            for (int r = 0; r < ka; ++r)
+                for (int t = 0; t < ka; ++t) {
+                    double v = 0.0;
+                    for (int Q = 0; Q < P.nq; ++Q)
+                        v += P.L_in[((size_t)Q * k + p) * k + q] * P.L_in[((size_t)Q * k + r) * k + t];
+                    ea[(((size_t)p * ka + q) * ka + r) * ka + t] = v;
+                }
+        }
+    std::vector<Term> th;
+    add_one_body(th, ha, ka, 0, ka, 0, ka);
+    add_two_body(th, ea, ka, 0, ka, 0, ka, -1);
+    return th;
+}
+
+// Structure checks of an active-space reference MPS.
+void check_reference_mps(const Problem& P, const MpsHost& act) {
+    require(act.nsite == P.ka, "reference MPS must have k_act sites");
+    require((int)act.bond.size() == P.ka + 1 && (int)act.T.size() == P.ka, "reference MPS: bond / tensor count");
+    const Bond &b0 = act.bond[0], &b1 = act.bond[P.ka];
+    require(b0.nsec() == 1 && b0.sec[0].q == QN(0, 0) && b0.total == 1, "reference MPS: first bond must be (0, 0), dim 1");
+    require(b1.nsec() == 1 && b1.sec[0].q == QN(P.nel, 0) && b1.total == 1,
+            "reference MPS: last bond must be (n_elec, 0), dim 1");
+    for (int s = 0; s < P.ka; ++s) {
+        require(act.T[s].size() == (size_t)act.bond[s].total * 4 * act.bond[s + 1].total, "reference MPS: tensor size");
+        for (double v : act.T[s]) require(std::isfinite(v), "non-finite reference MPS entry");
+    }
+}
+}  // namespace
+
+void set_reference_mps(Ctx& c, MpsHost act) {
+    Problem& P = c.P;
+    require(P.have_int, "mpspt_set_integrals must come first", MPSPT_ERR_STATE);
+    check_reference_mps(P, act);
+    const int ka = P.ka;
+    P.ci.clear();
+    P.h = P.h_in;
+    P.L = P.L_in;
+    build_eri(P);
+    std::unique_ptr<MpsD> d = mps_upload(act, c.st);   // entries that break QN conservation are dropped here
+    std::vector<Term> ti{Term{1.0, 0, {}}};
+    const double nrm = expectation(c, build_mpo(ti, ka, ka), *d, *d);
+    require(std::isfinite(nrm) && nrm > 0.0, "reference MPS has zero norm");
+    // gamma_tu = <c+_t c_u> (spin summed); real wavefunction: symmetric
+    P.gamma.assign((size_t)ka * ka, 0.0);
+    std::vector<double> unit((size_t)ka * ka, 0.0);
+    for (int t = 0; t < ka; ++t)
+        for (int u = t; u < ka; ++u) {
+            unit[(size_t)t * ka + u] = 1.0;
+            std::vector<Term> tt;
+            add_one_body(tt, unit, ka, t, t + 1, u, u + 1);
+            unit[(size_t)t * ka + u] = 0.0;
+            const double g = expectation(c, build_mpo(tt, ka, ka), *d, *d) / nrm;
+            P.gamma[(size_t)t * ka + u] = P.gamma[(size_t)u * ka + t] = g;
+        }
+    P.e_ref = expectation(c, build_mpo(active_hamiltonian_terms(P), ka, ka), *d, *d) / nrm;
+    const double sc = 1.0 / std::sqrt(nrm);
+    for (double& v : act.T[0]) v *= sc;
+    finish_reference(c, act);
+}
+
+namespace {
+// Shared tail of both reference forms, with gamma and E_ref set and the
+// integrals in the input basis: generalised Fock matrix, semicanonical
+// virtual orbitals, eps, and Psi0 on the full chain (empty virtual sites).
+void finish_reference_impl(Ctx& c, MpsHost& act) {
+    Problem& P = c.P;
+    const int k = P.k, ka = P.ka, kv = P.kv;
+    // f in the original basis (needs only (pq|tu), (pu|tq) with t,u active)
     std::vector<double> f((size_t)k * k);
     for (int p = 0; p < k; ++p)
         for (int q = 0; q < k; ++q) {
@@ -386,9 +466,8 @@ void set_reference(Ctx& c, const double* ci, long long n) {
     P.f = f;
     P.eps.resize(k);
     for (int p = 0; p < k; ++p) P.eps[p] = f[(size_t)p * k + p];
-    // exact MPS of Psi0 on the full chain (empty virtual sites)
-    MpsHost h0;
-    ci_to_mps(P, h0);
+    // Psi0 on the full chain: the active MPS, then empty virtual sites
+    MpsHost h0 = act;
     const QN tot(P.nel, 0);
     for (int a = 0; a < kv; ++a) {
         Bond b;
@@ -405,6 +484,9 @@ void set_reference(Ctx& c, const double* ci, long long n) {
     c.mpoA.clear(); c.mpoV.clear(); c.mpoH.reset(); c.mpoI.reset();
     c.sync();
 }
+}  // namespace
+
+void finish_reference(Ctx& c, MpsHost& act) { finish_reference_impl(c, act); }
 
 // ---------------------------------------------------------------- MPS I/O
 std::unique_ptr<MpsD> mps_upload(const MpsHost& h, cudaStream_t st) {
@@ -564,6 +646,13 @@ struct Comp {
     size_t rho_off = 0;
 };
 
+// Truncation keeps density-matrix eigenvectors with eigenvalue above
+// kKeepRel * tr(rho) (at most M of them).  At 1e-10 the smallest kept states
+// are separated from the rounding level of a float64 eigensolver
+// (~1e-16 |rho|) by six decades, so the kept subspace is fixed by the
+// mathematics and not by how an eigensolver rounds.
+constexpr double kKeepRel = 1e-10;
+
 // Validates copy tasks (column indices are read back from the host copy).
 void check_copies(const std::vector<CopyTask>& ct, const std::vector<int>& colv, const int* colp) {
     if (!checks_enabled()) return;
@@ -610,6 +699,7 @@ struct Sweeper {
     DBuf rho, V, wv, ctasks, cols, etasks;
     EigSolver eig;
     SweepResult* res = nullptr;
+    double keep_rel = kKeepRel;
     cudaEvent_t ev0, ev1;
 
     Sweeper(Ctx& c_, Lane& ln_, const Chain& ch_, int M_, MpsD& psi_)
@@ -617,7 +707,9 @@ struct Sweeper {
         filt = ch.filt;
         const int k = ch.nsite;
         LA.resize(k + 1); LV.resize(k + 1); RA.resize(k + 1); RV.resize(k + 1);
+        if (c.opt.keep_rel > 0.0) keep_rel = c.opt.keep_rel;
         if (c.opt.prec == MPSPT_MIXED_BF16) lo_kind = GEMM_TC;
+        else if (c.opt.prec == MPSPT_MIXED_FP16) lo_kind = GEMM_TC16;
         else if (c.opt.prec == MPSPT_FP32) lo_kind = GEMM_F32;
         sig_lo.set_kind(lo_kind, ln.tcerr.as<int>());
         sig.set_kind(GEMM_F64, nullptr);
@@ -630,6 +722,7 @@ struct Sweeper {
         eig.stats = c.opt.verbose >= 3;
     }
     ~Sweeper() {
+        if (dsc_host) { cudaStreamSynchronize(ln.st); cudaFreeHost(dsc_host); }
         cudaEventDestroy(ev0); cudaEventDestroy(ev1);
         for (auto& e : evs) cudaEventDestroy(e);
         for (auto& e : sev) cudaEventDestroy(e);
@@ -645,8 +738,9 @@ struct Sweeper {
             MPSPT_CUDA(cudaStreamSynchronize(ln.st));
         };
         one(LA[0], WA.dq[0], psi.bond[0], psi.bond[0]);
-        one(LV[0], WV.dq[0], psi.bond[0], psi0.bond[0]);
         one(RA[k], WA.dq[k], psi.bond[k], psi.bond[k]);
+        if (ch.ground) return;
+        one(LV[0], WV.dq[0], psi.bond[0], psi0.bond[0]);
         one(RV[k], WV.dq[k], psi.bond[k], psi0.bond[k]);
     }
 
@@ -657,6 +751,7 @@ struct Sweeper {
                         psi.bond[i + 1], LA[i + 1], ln.st);
         envp.run(ln.st);
         env_flops = envp.flops();
+        if (ch.ground) return;
         LV[i + 1].build(WV.dq[i + 1], psi.bond[i + 1], psi0.bond[i + 1], ln.st);
         envp.build_left(WV, i, LV[i], psi.A[i], psi0.A[i], psi.bond[i], psi0.bond[i], psi.bond[i + 1],
                         psi0.bond[i + 1], LV[i + 1], ln.st);
@@ -670,6 +765,7 @@ struct Sweeper {
                          psi.bond[i + 1], RA[i], ln.st);
         envp.run(ln.st);
         env_flops = envp.flops();
+        if (ch.ground) return;
         RV[i].build(WV.dq[i], psi.bond[i], psi0.bond[i], ln.st);
         envp.build_right(WV, i, RV[i + 1], psi.A[i], psi0.A[i], psi.bond[i], psi0.bond[i], psi.bond[i + 1],
                          psi0.bond[i + 1], RV[i], ln.st);
@@ -761,9 +857,16 @@ struct Sweeper {
         }
         std::vector<double> wh(wsz);
         if (wsz) MPSPT_CUDA(cudaMemcpyAsync(wh.data(), wv.get(), wsz * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
+        std::vector<int> eflag(eig.nflags);
+        if (eig.nflags)
+            MPSPT_CUDA(cudaMemcpyAsync(eflag.data(), eig.flags.get(), eig.nflags * sizeof(int), cudaMemcpyDeviceToHost,
+                                       ln.st));
         auto ts = clk::now();
         MPSPT_CUDA(cudaStreamSynchronize(ln.st));
         split_wait += since(ts);
+        for (int f : eflag)
+            require(f != 2, "truncation eigensolver: sweep cap reached before the convergence test",
+                    MPSPT_ERR_NOT_CONVERGED);
         // selection: keep the Mkeep largest (ties at the cut dropped as a group)
         struct Cand { double lam; int ci; int rank; int col; };
         std::vector<Cand> cand;
@@ -782,7 +885,7 @@ struct Sweeper {
             const double* w_ = wh.data() + woff[ci];
             for (int r = 0; r < cl[ci].dim; ++r) {
                 const double lam = w_[order[ci][r]];
-                if (lam > 1e-13 * tr) cand.push_back({lam, (int)ci, r, order[ci][r]});
+                if (lam > keep_rel * tr) cand.push_back({lam, (int)ci, r, order[ci][r]});
             }
         }
         std::sort(cand.begin(), cand.end(), [&](const Cand& a, const Cand& b) {
@@ -960,7 +1063,7 @@ struct Sweeper {
         add_time();
     }
     void check_tc() {
-        if (lo_kind != GEMM_TC) return;
+        if (!is_tc(lo_kind)) return;
         int e = 0;
         MPSPT_CUDA(cudaMemcpyAsync(&e, ln.tcerr.get(), sizeof(int), cudaMemcpyDeviceToHost, ln.st));
         MPSPT_CUDA(cudaStreamSynchronize(ln.st));
@@ -1001,6 +1104,8 @@ struct Sweeper {
         sig.set_skip(nullptr);
         require(!ln.cg_host->not_spd, "CG: p^T A p <= 0 (H0 - E0 not positive on the local space)",
                 MPSPT_ERR_NOT_SPD);
+        require(ln.cg_host->done != 0, "local CG reached cg_max_iter before the residual test",
+                MPSPT_ERR_NOT_CONVERGED);
         res->cg_iters += ln.cg_host->iters;
         res->sigma64_calls -= launched - ln.cg_host->iters;   // skipped launches did no work
         res->sigma64_flops -= (launched - ln.cg_host->iters) * sig.flops();
@@ -1030,7 +1135,13 @@ struct Sweeper {
             MPSPT_CUDA(cudaStreamSynchronize(ln.st));
             add_time();
             const double bb = ln.scal_host[2], rr = ln.scal_host[3];
-            if (rr <= c.opt.cg_tol * c.opt.cg_tol * bb || bb == 0.0 || outer == max_outer) break;
+            if (rr <= c.opt.cg_tol * c.opt.cg_tol * bb || bb == 0.0) break;
+            require(outer < max_outer, "float64 refinement: 12 rounds without meeting cg_tol",
+                    MPSPT_ERR_NOT_CONVERGED);
+            // float16 terms have a narrow exponent range: the inner solve runs
+            // on the residual scaled to unit norm (A is linear, d scales back)
+            const double sc = (lo_kind == GEMM_TC16 && rr > 0.0) ? 1.0 / std::sqrt(rr) : 1.0;
+            if (sc != 1.0) vec_scale_mask(w.r.as<double>(), w.r.as<double>(), sc, n, ln.st);
             // inner solve from d = 0 (the Ap buffer is reused by the inner operator)
             MPSPT_CUDA(cudaMemsetAsync(w.d.get(), 0, n * sizeof(double), ln.st));
             cg_init(w.ri.as<double>(), w.z.as<double>(), w.p.as<double>(), w.r.as<double>(),
@@ -1057,7 +1168,7 @@ struct Sweeper {
             res->cg_iters += ln.cg_host->iters;
             res->sigma_calls -= launched - ln.cg_host->iters;
             res->sigma_flops -= (launched - ln.cg_host->iters) * sig_lo.flops();
-            vec_axpy(x, w.d.as<double>(), 1.0, n, ln.st);
+            vec_axpy(x, w.d.as<double>(), 1.0 / sc, n, ln.st);
         }
         return hylleraas(n);   // w.Ap holds the float64 A x of the final x
     }
@@ -1148,6 +1259,130 @@ struct Sweeper {
         }
     }
 
+    // ---- ground-state DMRG (reference Psi0) ---------------------------------
+    DBuf dvec, davec, dsc;
+    double* dsc_host = nullptr;
+
+    // Lowest eigenpair of A_loc by Davidson with the Jacobi (diagonal)
+    // correction, started from x (the current two-site product); restarts
+    // from the Ritz vector when the basis reaches kmax.  Inner products run
+    // on the device; the kmax x kmax Rayleigh quotient is diagonalised on
+    // the host.  Returns the Ritz value; x holds the unit Ritz vector.
+    double davidson(size_t n) {
+        constexpr int kmax = 16;
+        const int maxit = std::max(8, c.opt.cg_max_iter);
+        dvec.ensure((size_t)kmax * n * sizeof(double) + 16, ln.st);
+        davec.ensure((size_t)kmax * n * sizeof(double) + 16, ln.st);
+        dsc.ensure(64 * sizeof(double), ln.st);
+        if (!dsc_host) MPSPT_CUDA(cudaMallocHost(&dsc_host, 64 * sizeof(double)));
+        double* Vb = dvec.as<double>();
+        double* AVb = davec.as<double>();
+        double* x = w.x.as<double>();
+        auto V = [&](int j) { return Vb + (size_t)j * n; };
+        auto AV = [&](int j) { return AVb + (size_t)j * n; };
+        auto dots = [&](int cnt, const double* const* a, const double* const* b) {
+            for (int q = 0; q < cnt; ++q)
+                vec_dot(a[q], b[q], n, dsc.as<double>() + q, ln.red.as<double>(), ln.cnt.as<unsigned>(), ln.st);
+            MPSPT_CUDA(cudaMemcpyAsync(dsc_host, dsc.get(), cnt * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
+            MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        };
+        {   // v0 = x / |x|
+            const double* a[1] = {x};
+            dots(1, a, a);
+            const double nx = std::sqrt(dsc_host[0]);
+            require(nx > 0.0 && std::isfinite(nx), "Davidson: zero start vector");
+            vec_scale_mask(V(0), x, 1.0 / nx, n, ln.st);
+        }
+        std::vector<double> H((size_t)kmax * kmax, 0.0);
+        int m = 1;
+        bool need_av = true;
+        double theta = 0.0;
+        const double tol = c.opt.cg_tol;
+        for (int it = 0; it < maxit; ++it) {
+            if (need_av) {   // AV[m-1] = A V[m-1] and the new column of H
+                MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), V(m - 1), n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
+                sigma64();
+                MPSPT_CUDA(cudaMemcpyAsync(AV(m - 1), w.Ap.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
+                std::vector<const double*> a(m), b(m, AV(m - 1));
+                for (int j = 0; j < m; ++j) a[j] = V(j);
+                dots(m, a.data(), b.data());
+                for (int j = 0; j < m; ++j) H[(size_t)j * kmax + m - 1] = H[(size_t)(m - 1) * kmax + j] = dsc_host[j];
+            }
+            // Rayleigh-Ritz on span V
+            std::vector<double> Hm((size_t)m * m), ev, U;
+            for (int i2 = 0; i2 < m; ++i2)
+                for (int j = 0; j < m; ++j) Hm[(size_t)i2 * m + j] = H[(size_t)i2 * kmax + j];
+            jacobi_eigh(m, Hm, ev, U);
+            int lo = 0;
+            for (int j = 1; j < m; ++j) if (ev[j] < ev[lo]) lo = j;
+            theta = ev[lo];
+            // u = V y -> x, A u = AV y -> w.r, residual r = A u - theta u -> w.z
+            vec_zero(x, n, ln.st);
+            vec_zero(w.r.as<double>(), n, ln.st);
+            for (int j = 0; j < m; ++j) {
+                const double y = U[(size_t)j * m + lo];
+                vec_axpy(x, V(j), y, n, ln.st);
+                vec_axpy(w.r.as<double>(), AV(j), y, n, ln.st);
+            }
+            MPSPT_CUDA(cudaMemcpyAsync(w.z.get(), w.r.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
+            vec_axpy(w.z.as<double>(), x, -theta, n, ln.st);
+            {
+                const double* a[1] = {w.z.as<double>()};
+                dots(1, a, a);
+            }
+            const double rn = std::sqrt(dsc_host[0]);
+            if (rn <= tol * std::max(1.0, std::fabs(theta))) return theta;
+            if (m == kmax) {   // restart from the Ritz vector
+                MPSPT_CUDA(cudaMemcpyAsync(V(0), x, n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
+                MPSPT_CUDA(cudaMemcpyAsync(AV(0), w.r.get(), n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
+                std::fill(H.begin(), H.end(), 0.0);
+                H[0] = theta;
+                m = 1;
+            }
+            // correction t = r / (theta - diag) on the masked entries, then
+            // orthogonalised against V twice and normalised
+            double* t = V(m);
+            davidson_correction(t, w.z.as<double>(), w.dg.as<double>(), theta, n, ln.st);
+            for (int pass = 0; pass < 2; ++pass) {
+                std::vector<const double*> a(m), b(m, t);
+                for (int j = 0; j < m; ++j) a[j] = V(j);
+                dots(m, a.data(), b.data());
+                for (int j = 0; j < m; ++j) vec_axpy(t, V(j), -dsc_host[j], n, ln.st);
+            }
+            {
+                const double* a[1] = {t};
+                dots(1, a, a);
+            }
+            const double tn = std::sqrt(dsc_host[0]);
+            require(tn > 1e-300, "Davidson: correction vanished before convergence", MPSPT_ERR_NOT_CONVERGED);
+            vec_scale_mask(t, t, 1.0 / tn, n, ln.st);
+            ++m;
+            need_av = true;
+        }
+        throw Error(MPSPT_ERR_NOT_CONVERGED, "Davidson reached its iteration cap (cg_max_iter)");
+    }
+
+    double step_ground(int i, int dir) {
+        const Bond &bL = psi.bond[i], &bR = psi.bond[i + 2];
+        X.build(bL, bR, filt[i + 1]);
+        const size_t n = X.n;
+        w.ensure(n, 1, ln.st);
+        double* x = w.x.as<double>();
+        product(prod, psi, i, X, x);
+        const Omega& oA = omega(omA_c, WA, i);
+        sig.build(oA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
+                  w.Ap.as<double>(), ln.st);
+        dia.build(oA, X, bL, bR, LA[i], RA[i + 2], WA.dq[i], WA.dq[i + 2], w.dg.as<double>(), ln.st);
+        dia.run(ln.st);
+        const double e = davidson(n);
+        const double disc = split(i, dir, M, X, x);
+        res->max_disc = std::max(res->max_disc, disc);
+        res->max_bond = std::max(res->max_bond, psi.bond[i + 1].total);
+        if (dir == 0) update_left(i);
+        else update_right(i + 1);
+        return e;
+    }
+
     // one bond step; returns h_loc
     // host-side phase timers (printed with verbose >= 2)
     double t_plan = 0, t_rhs = 0, t_solve = 0, t_split = 0, t_env = 0;
@@ -1161,6 +1396,7 @@ struct Sweeper {
     static double since(clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); }
 
     double step(int i, int dir) {
+        if (ch.ground) return step_ground(i, dir);
         auto t0 = clk::now();
         const Bond &bL = psi.bond[i], &bR = psi.bond[i + 2];
         auto th = clk::now();
@@ -1224,21 +1460,11 @@ struct Sweeper {
 
 }  // namespace
 
-std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res, Lane* lane) {
-    Lane& ln = lane ? *lane : *c.lane0;
-    require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
-    require(M >= 1, "bond dimension M must be >= 1");
-    require(c.opt.prec == MPSPT_FP64 || c.opt.prec == MPSPT_FP32 || c.opt.prec == MPSPT_MIXED_BF16,
-            "unknown precision mode");
-    const auto t0 = std::chrono::steady_clock::now();
-    const long long l0 = launch_count();
-    // device timeline: an event at entry and one at the end of every sweep
-    cudaEvent_t e_start;
-    std::vector<cudaEvent_t> e_sweep;
-    MPSPT_CUDA(cudaEventCreate(&e_start));
-    MPSPT_CUDA(cudaEventRecord(e_start, ln.st));
+namespace {
+// Initial MPS of a sweep (reading R8): sector dimensions from the counting
+// rule, entries from SplitMix64 keyed by (seed, site, state, row, column).
+MpsHost initial_mps(const Ctx& c, const Chain& ch, int M) {
     const int nsite = ch.nsite;
-    // initial Psi1
     MpsHost ih;
     ih.nsite = nsite;
     ih.bond = initial_bonds(nsite, ch.target, ch.filt, M);
@@ -1257,6 +1483,26 @@ std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res,
                             init_value(c.opt.seed, s, t, sl.off + a, rs.off + b);
             }
     }
+    return ih;
+}
+}  // namespace
+
+std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res, Lane* lane) {
+    Lane& ln = lane ? *lane : *c.lane0;
+    require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
+    require(M >= 1, "bond dimension M must be >= 1");
+    require(c.opt.prec == MPSPT_FP64 || c.opt.prec == MPSPT_FP32 || c.opt.prec == MPSPT_MIXED_BF16 ||
+                c.opt.prec == MPSPT_MIXED_FP16,
+            "unknown precision mode");
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = launch_count();
+    // device timeline: an event at entry and one at the end of every sweep
+    cudaEvent_t e_start;
+    std::vector<cudaEvent_t> e_sweep;
+    MPSPT_CUDA(cudaEventCreate(&e_start));
+    MPSPT_CUDA(cudaEventRecord(e_start, ln.st));
+    const int nsite = ch.nsite;
+    MpsHost ih = initial_mps(c, ch, M);
     std::unique_ptr<MpsD> psi = mps_upload(ih, ln.st);
     Sweeper sw(c, ln, ch, M, *psi);
     sw.res = &res;
@@ -1271,6 +1517,8 @@ std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res,
         for (int i = 0; i <= nsite - 2; ++i) e = sw.step(i, 0);
         for (int i = nsite - 2; i >= 0; --i) e = sw.step(i, 1);
         res.e2_sweep.push_back(e);
+        res.disc_sweep.push_back(res.max_disc);
+        res.sigma_cum.push_back(res.sigma_calls + res.sigma64_calls);
         cudaEvent_t ev;
         MPSPT_CUDA(cudaEventCreate(&ev));
         MPSPT_CUDA(cudaEventRecord(ev, ln.st));
@@ -1295,7 +1543,7 @@ std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res,
         if (c.opt.verbose == 1)
             fprintf(stderr, "[mpspt]   host-only ms: layouts+products %.1f rhs-plan %.1f sigma-plans %.1f split-host %.1f env-plans %.1f\n",
                     sw.h_prod, sw.h_rhs, sw.h_sig, sw.h_split, sw.h_env);
-        if (s > 0 && std::fabs(e - prev) < c.opt.e_tol) break;
+        if (s > 0 && std::fabs(e - prev) < c.opt.e_tol) { res.converged = true; break; }
         prev = e;
     }
     res.e2 = res.e2_sweep.back();
@@ -1311,6 +1559,64 @@ std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res,
         cudaEventDestroy(ev);
     }
     cudaEventDestroy(e_start);
+    res.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return psi;
+}
+
+std::unique_ptr<MpsD> ground_state(Ctx& c, int M0, double s2_penalty, SweepResult& res) {
+    Problem& P = c.P;
+    require(P.have_int, "mpspt_set_integrals must come first", MPSPT_ERR_STATE);
+    require(M0 >= 1, "bond dimension M0 must be >= 1");
+    require(P.ka >= 2, "ground-state DMRG needs k_act >= 2");
+    Lane& ln = *c.lane0;
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = launch_count();
+    const int ka = P.ka;
+    require(s2_penalty >= 0.0 && std::isfinite(s2_penalty), "spin penalty must be >= 0");
+    std::vector<Term> th = active_hamiltonian_terms(P);
+    // lambda S^2 = lambda S- S+ on Sz = 0 (S+ = sum_p c+_pa c_pb): lifts every
+    // state with S > 0 by at least 2 lambda, so the sweep finds the lowest singlet
+    if (s2_penalty > 0.0)
+        for (int q = 0; q < ka; ++q)
+            for (int p = 0; p < ka; ++p)
+                th.push_back(Term{s2_penalty, 4, {FOp{2 * q + 1, true}, FOp{2 * q, false}, FOp{2 * p, true},
+                                                  FOp{2 * p + 1, false}}});
+    const MPO W = build_mpo(th, ka, ka);
+    Chain ch;
+    ch.nsite = ka;
+    ch.ka = ka;
+    ch.target = QN(P.nel, 0);
+    ch.filt.assign(ka + 1, {});
+    ch.WA = &W;
+    ch.WV = &W;
+    ch.ground = true;
+    MpsHost ih = initial_mps(c, ch, M0);
+    std::unique_ptr<MpsD> psi = mps_upload(ih, ln.st);
+    {
+        Sweeper sw(c, ln, ch, M0, *psi);
+        sw.res = &res;
+        sw.right_canonicalize();
+        sw.boundary_envs();
+        for (int i = ka - 1; i >= 1; --i) sw.update_right(i);
+        double prev = 0.0;
+        const int maxs = std::min(64, std::max(1, c.opt.max_sweeps));
+        for (int s = 0; s < maxs; ++s) {
+            res.max_disc = 0.0;
+            double e = 0.0;
+            for (int i = 0; i <= ka - 2; ++i) e = sw.step(i, 0);
+            for (int i = ka - 2; i >= 0; --i) e = sw.step(i, 1);
+            res.e2_sweep.push_back(e);
+            res.disc_sweep.push_back(res.max_disc);
+            if (c.opt.verbose)
+                fprintf(stderr, "[mpspt] DMRG sweep %d  E = %.12f  max discarded %.3e\n", s, e, res.max_disc);
+            if (s > 0 && std::fabs(e - prev) < c.opt.e_tol) { res.converged = true; break; }
+            prev = e;
+        }
+        res.e2 = res.e2_sweep.back();
+    }
+    MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+    set_reference_mps(c, mps_download(*psi, ln.st));
+    res.launches = launch_count() - l0;
     res.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return psi;
 }
@@ -1464,7 +1770,9 @@ double minimize_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int
     for (int i = 0; i < n; ++i) tot += e2_part[i];   // fixed (pair) order
     res = SweepResult();
     res.e2 = tot;
+    res.converged = true;
     for (const auto& r : rs) {
+        res.converged = res.converged && r.converged;
         res.cg_iters += r.cg_iters;
         res.sigma_calls += r.sigma_calls;
         res.sigma_flops += r.sigma_flops;

@@ -83,6 +83,13 @@ struct Ctx {
 
 void set_integrals(Ctx& c, int ka, int kv, int nel, const double* h, const double* L, int nq);
 void set_reference(Ctx& c, const double* ci, long long n);
+// Reference as an active-space MPS (host tensors, any norm): gamma and E_ref
+// by MPO transfers on the device, then finish_reference.
+void set_reference_mps(Ctx& c, MpsHost act);
+// With P.gamma, P.e_ref set and P.h / P.L / P.eri in the input basis: the
+// generalised Fock matrix, semicanonical virtuals, eps and Psi0 on the full
+// chain.
+void finish_reference(Ctx& c, MpsHost& act);
 
 struct SweepResult {
     double e2 = 0.0;
@@ -96,6 +103,9 @@ struct SweepResult {
     long long learned_used = 0, learned_rejected = 0;
     long long sigma64_calls = 0;
     double sigma64_flops = 0.0, sigma64_ms = 0.0;
+    bool converged = false;              // last sweep met e_tol
+    std::vector<long long> sigma_cum;    // sigma applications (all precisions) at each sweep end
+    std::vector<double> disc_sweep;      // max discarded weight of each sweep
 };
 
 // One MPS-PT problem on a chain of sites: the full space (active + all
@@ -108,6 +118,7 @@ struct Chain {
     const MPO* WV = nullptr;              // RHS operator on the chain
     MpsD psi0;                            // reference on the chain (views)
     std::vector<int> orbs;                // full-space orbital of each site
+    bool ground = false;                  // ground-state DMRG of WA (WV, psi0 unused)
 };
 struct PartOps {
     MPO A, V;
@@ -122,6 +133,10 @@ double minimize_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int
                             const std::vector<int>& Ms, int n_lanes, std::vector<double>& e2_part,
                             SweepResult& res);
 std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res);
+// Ground-state DMRG of H_act + s2_penalty S^2 in the (n_elec, Sz = 0) sector
+// at bond dimension <= M0 (two-site sweep, Davidson local solver); installs
+// the result as the reference and returns it (active sites only).
+std::unique_ptr<MpsD> ground_state(Ctx& c, int M0, double s2_penalty, SweepResult& res);
 double expectation(Ctx& c, const MPO& W, const MpsD& bra, const MpsD& ket);
 double third_order(Ctx& c, int h0, const MpsD& psi1);
 void local_apply(Ctx& c, int h0, const MpsD& psi1, int i, int op, const double* x, double* out);

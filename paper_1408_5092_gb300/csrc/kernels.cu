@@ -6,6 +6,9 @@
 
 #include <atomic>
 #include <cstdio>
+#include <mutex>
+#include <set>
+#include <utility>
 
 namespace mpspt {
 namespace {
@@ -491,6 +494,17 @@ __global__ void k_minv(double* y, const double* __restrict__ d, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         y[i] = d[i] > 0.0 ? 1.0 / d[i] : 0.0;
 }
+// Davidson correction t = r / (theta - d), the denominator kept at least
+// 1e-8 max(1, |theta|) away from zero (its sign kept)
+__global__ void k_dav_corr(double* t, const double* __restrict__ r, const double* __restrict__ d, double theta,
+                           size_t n) {
+    const double eps = 1e-8 * fmax(1.0, fabs(theta));
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double den = theta - d[i];
+        if (fabs(den) < eps) den = den < 0.0 ? -eps : eps;
+        t[i] = r[i] / den;
+    }
+}
 __global__ void k_d2f(float* y, const double* __restrict__ x, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         y[i] = (float)x[i];
@@ -511,6 +525,17 @@ inline int ew_grid(size_t n) {
 
 long long launch_count() { return g_launches.load(); }
 void count_launch() { counted(); }
+
+void ensure_smem_attr(const void* func, int bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({func, dev})) return;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+        done.insert({func, dev});
+}
 
 void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                            const int* skip) {
@@ -537,12 +562,8 @@ void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaSt
 }
 void launch_eig(const EigTask* tasks, int ntask, cudaStream_t st) {
     if (ntask <= 0) return;
-    static bool attr = false;
     const int smem = EIG_SMEM_BYTES;
-    if (!attr) {
-        cudaFuncSetAttribute(k_eig<double, EigTask>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    ensure_smem_attr(reinterpret_cast<const void*>(k_eig<double, EigTask>), smem);
     counted();
     k_eig<double, EigTask><<<ntask, 512, smem, st>>>(tasks);
 }
@@ -554,7 +575,9 @@ void launch_ns_prep(const EigTask* tasks, int ntask, cudaStream_t st) {
     if (ntask > 0) { counted(); k_ns_prep<<<ntask, 256, 0, st>>>(tasks); }
 }
 
-void vec_zero(double* x, size_t n, cudaStream_t st) { if (n) k_zero<<<ew_grid(n), 256, 0, st>>>(x, n); }
+void vec_zero(double* x, size_t n, cudaStream_t st) {
+    if (n) { counted(); k_zero<<<ew_grid(n), 256, 0, st>>>(x, n); }
+}
 void vec_scale_mask(double* y, const double* x, double a, size_t n, cudaStream_t st) {
     if (n) { counted(); k_scale<<<ew_grid(n), 256, 0, st>>>(y, x, a, n); }
 }
@@ -570,6 +593,9 @@ void f64_to_f32(float* y, const double* x, size_t n, cudaStream_t st) {
 }
 void f32_to_f64(double* y, const float* x, size_t n, cudaStream_t st) {
     if (n) { counted(); k_f2d<<<ew_grid(n), 256, 0, st>>>(y, x, n); }
+}
+void davidson_correction(double* t, const double* r, const double* diag, double theta, size_t n, cudaStream_t st) {
+    if (n) { counted(); k_dav_corr<<<ew_grid(n), 256, 0, st>>>(t, r, diag, theta, n); }
 }
 void make_minv(double* minv, const double* diag, size_t n, cudaStream_t st) {
     if (n) { counted(); k_minv<<<ew_grid(n), 256, 0, st>>>(minv, diag, n); }

@@ -76,11 +76,10 @@ struct JacTask {
     double* V;         // n x n eigenvectors (columns), row-major; with vinit: the start basis
     double* w;         // n eigenvalues (unsorted), or null
     double* prev;      // scratch: off-norm of the previous sweep
-    int* done;         // scratch: set once the matrix has converged
+    int* done;         // 0 while sweeping; 1 converged; 2 stopped by the sweep cap
     int* nsw;          // scratch: sweeps performed (written when the matrix stops)
     int n, vinit;
-    int sched;         // pair schedule: 0 round robin, 1 large-diagonal indices first
-    int pad;
+    int pad0, pad1;
 };
 struct JacRows {       // rows [r0, r0 + rows) of task's V for one apply block
     int task, r0, rows, pad;
@@ -108,13 +107,19 @@ struct CgState {
 // Number of kernels launched by this library in this process.
 long long launch_count();
 void count_launch();
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device.  The attribute belongs to the device's context, so it is set once
+// per (kernel, device); thread-safe.  A failure is not remembered: the
+// launch that follows then fails and its error check reports it.
+void ensure_smem_attr(const void* func, int bytes);
 
 // Split-bfloat16 tcgen05 variant of the grouped GEMM (tiles 128 x 64; same
-// task format).  *err is set to 1 if a bounded mbarrier wait gave up.
+// task format); f16: split-float16 terms instead.  *err is set to 1 if a
+// bounded mbarrier wait gave up.
 int tc_tile_m();
 int tc_tile_n();
 void launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmOp* ops, int* err, cudaStream_t st,
-                    const int* skip = nullptr);
+                    const int* skip = nullptr, bool f16 = false);
 // Float32-arithmetic variant of the float64 grouped GEMM (float64 in/out).
 void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                            const int* skip = nullptr);
@@ -162,6 +167,8 @@ void cg_init(double* r, double* z, double* p, const double* b, const double* Ax,
 void cg_step(double* x, double* r, double* z, double* p, const double* Ap, const double* minv,
              size_t n, CgState* S, double* scratch, unsigned* counter, cudaStream_t st);
 void make_minv(double* minv, const double* diag, size_t n, cudaStream_t st);
+// t = r / (theta - diag), denominators kept away from zero (Davidson correction)
+void davidson_correction(double* t, const double* r, const double* diag, double theta, size_t n, cudaStream_t st);
 
 // ---- learned preconditioner (kernels_mlp.cu)
 struct BlockRef {      // one QN block of a two-site vector

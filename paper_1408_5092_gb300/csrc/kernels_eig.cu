@@ -62,41 +62,12 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t
 __host__ __device__ inline int jac_max_rounds(int n) { return 2 * n + 4; }
 __host__ __device__ inline size_t jac_rot_head(int n) { return align16((size_t)(1 + jac_max_rounds(n)) * 4); }
 
-// shared-memory head of the sweep kernels: rowoff, Pp, Qq, perm (n ints each),
-// Cc, Ss (n T each), dg (n doubles); the packed triangle follows
+// shared-memory head of the sweep kernels: rowoff, Pp, Qq (n ints each, room
+// for four), Cc, Ss (n T each) and n doubles of headroom; the packed
+// triangle follows
 template <class T>
 __host__ __device__ inline size_t jac_head_bytes(int n) {
     return align16((size_t)n * 16) + align16(2 * (size_t)n * sizeof(T)) + align16((size_t)n * 8);
-}
-
-// perm = indices by decreasing dg (ties by index), *kS = #{dg >= 1e-8 max}
-__device__ void sort_diag(const double* dg, int n, int* perm, int* kS, double* red) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double mx = -1e300;
-    for (int i = tid; i < n; i += blockDim.x) mx = fmax(mx, dg[i]);
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) red[warp] = mx;
-    if (tid == 0) *kS = 0;
-    __syncthreads();
-    if (tid == 0) {
-        double v = red[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
-        red[0] = v;
-    }
-    __syncthreads();
-    const double thr = 1e-8 * red[0];
-    int cnt = 0;
-    for (int i = tid; i < n; i += blockDim.x) {
-        const double d = dg[i];
-        int r = 0;
-        for (int j = 0; j < n; ++j) r += (dg[j] > d) || (dg[j] == d && j < i);
-        perm[r] = i;
-        cnt += d >= thr;
-    }
-    atomicAdd(kS, cnt);
-    __syncthreads();
-    if (tid == 0 && *kS < 1) *kS = 1;
-    __syncthreads();
 }
 
 template <class T>
@@ -104,7 +75,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double red[2][JAC_THREADS / 32];
     __shared__ double thr;
-    __shared__ int stop, cnt, kS;
+    __shared__ int stop, cnt;
     const JacTask t = tasks[blockIdx.x];
     if (sweep > 0 && *(volatile const int*)t.done) return;
     const int n = t.n;
@@ -113,10 +84,8 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
     int* rowoff = reinterpret_cast<int*>(sm);
     int* Pp = rowoff + n;
     int* Qq = Pp + n;
-    int* perm = Qq + n;
     T* Cc = reinterpret_cast<T*>(sm + align16((size_t)n * 16));
     T* Ss = Cc + n;
-    double* dg = reinterpret_cast<double*>(sm + align16((size_t)n * 16) + align16(2 * (size_t)n * sizeof(T)));
     const size_t head = jac_head_bytes<T>(n);
     const bool p_sm = head + np * sizeof(T) <= (size_t)JAC_SMEM;
     T* P = p_sm ? reinterpret_cast<T*>(sm + head) : reinterpret_cast<T*>(t.P);
@@ -156,10 +125,11 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
             for (int w = 0; w < nw; ++w) { so += red[0][w]; sd += red[1][w]; }
             const double sa = so + sd;
             const double prev = sweep == 0 ? 1e300 : *t.prev;
-            const int s = (so <= JacTol<T>::stop * sa) || sa == 0.0 || (so <= JacTol<T>::stall * sa && so > 0.81 * prev) ||
-                          sweep >= maxs || n < 2;
+            const int conv = (so <= JacTol<T>::stop * sa) || sa == 0.0 ||
+                             (so <= JacTol<T>::stall * sa && so > 0.81 * prev) || n < 2;
+            const int s = conv || sweep >= maxs;
             *t.prev = so;
-            *t.done = s;
+            *t.done = s ? (conv ? 1 : 2) : 0;   // 2: stopped by the sweep cap
             if (s) *t.nsw = sweep;
             stop = s;
             thr = JacTol<T>::absf * sqrt(sa);
@@ -171,13 +141,8 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
             for (int i = tid; i < n; i += JAC_THREADS) t.w[i] = (double)P[rowoff[i] + i];
         return;
     }
-    if (t.sched == 1) {
-        for (int i = tid; i < n; i += JAC_THREADS) dg[i] = (double)P[rowoff[i] + i];
-        __syncthreads();
-        sort_diag(dg, n, perm, &kS, &red[0][0]);
-    }
     Sched sc;
-    sc.init(t.sched, n, perm, t.sched == 1 ? kS : 0);
+    sc.init(n);
     const int nr = sc.rounds();
     if (tid == 0) rhead[0] = nr;
     constexpr T SKIP = (T)JacTol<T>::skip;
@@ -260,7 +225,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
     __shared__ double red[2][JAC_THREADS / 32];
     __shared__ double part[2][JC];
     __shared__ double thr;
-    __shared__ int stop, cnt, kS;
+    __shared__ int stop, cnt;
     const int rank = (int)cl.block_rank();
     const JacTask t = tasks[blockIdx.x / JC];
     if (sweep > 0 && *(volatile const int*)t.done) return;   // same value in every CTA of the cluster
@@ -271,10 +236,8 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
     int* rowoff = reinterpret_cast<int*>(sm);
     int* Pp = rowoff + n;
     int* Qq = Pp + n;
-    int* perm = Qq + n;
     T* Cc = reinterpret_cast<T*>(sm + align16((size_t)n * 16));
     T* Ss = Cc + n;
-    double* dg = reinterpret_cast<double*>(sm + align16((size_t)n * 16) + align16(2 * (size_t)n * sizeof(T)));
     T* Ploc = reinterpret_cast<T*>(sm + jac_head_bytes<T>(n));
     T* Pg = reinterpret_cast<T*>(t.P);
     int* rhead = reinterpret_cast<int*>(t.rot);
@@ -329,10 +292,11 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
             for (int r = 0; r < JC; ++r) { so += part[0][r]; sd += part[1][r]; }
             const double sa = so + sd;
             const double prev = sweep == 0 ? 1e300 : *t.prev;
-            const int s = (so <= JacTol<T>::stop * sa) || sa == 0.0 || (so <= JacTol<T>::stall * sa && so > 0.81 * prev) ||
-                          sweep >= maxs || n < 2;
+            const int conv = (so <= JacTol<T>::stop * sa) || sa == 0.0 ||
+                             (so <= JacTol<T>::stall * sa && so > 0.81 * prev) || n < 2;
+            const int s = conv || sweep >= maxs;
             *t.prev = so;
-            *t.done = s;
+            *t.done = s ? (conv ? 1 : 2) : 0;   // 2: stopped by the sweep cap
             if (s) *t.nsw = sweep;
             const double th = JacTol<T>::absf * sqrt(sa);
             for (int r = 0; r < JC; ++r) { *cl.map_shared_rank(&stop, r) = s; *cl.map_shared_rank(&thr, r) = th; }
@@ -347,13 +311,8 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
             }
         return;
     }
-    if (t.sched == 1) {   // every CTA sorts the same diagonal the same way
-        for (int i = tid; i < n; i += JAC_THREADS) dg[i] = (double)S(i, i);
-        __syncthreads();
-        sort_diag(dg, n, perm, &kS, &red[0][0]);
-    }
     Sched sc;
-    sc.init(t.sched, n, perm, t.sched == 1 ? kS : 0);
+    sc.init(n);
     const int nr = sc.rounds();
     if (rank == 0 && tid == 0) rhead[0] = nr;
     constexpr T SKIP = (T)JacTol<T>::skip;
@@ -491,14 +450,10 @@ int jac_rows_per_block(int n, bool f32) {
 }
 
 static void jac_attributes() {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_jac_sweep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, JAC_SMEM);
-        cudaFuncSetAttribute(k_jac_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, JAC_SMEM);
-        cudaFuncSetAttribute(k_jac_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, JAC_SMEM);
-        cudaFuncSetAttribute(k_jac_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, JAC_SMEM);
-        attr = true;
-    }
+    ensure_smem_attr(reinterpret_cast<const void*>(k_jac_sweep<double>), JAC_SMEM);
+    ensure_smem_attr(reinterpret_cast<const void*>(k_jac_sweep<float>), JAC_SMEM);
+    ensure_smem_attr(reinterpret_cast<const void*>(k_jac_apply<double>), JAC_SMEM);
+    ensure_smem_attr(reinterpret_cast<const void*>(k_jac_apply<float>), JAC_SMEM);
 }
 
 void launch_jac_sweep(const JacTask* tasks, int ntask, int sweep, int maxs, bool f32, cudaStream_t st) {
@@ -518,11 +473,7 @@ int jac_cluster_smem(int n) {
 
 void launch_jac_sweep_cluster(const JacTask* tasks, int ntask, int sweep, int maxs, int smem, cudaStream_t st) {
     if (ntask <= 0) return;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_jac_sweep_cl<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, JAC_SMEM);
-        attr = true;
-    }
+    ensure_smem_attr(reinterpret_cast<const void*>(k_jac_sweep_cl<double>), JAC_SMEM);
     count_launch();
     k_jac_sweep_cl<double><<<ntask * JC, JAC_THREADS, smem, st>>>(tasks, sweep, maxs);
 }

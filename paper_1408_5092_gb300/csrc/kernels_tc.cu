@@ -1,9 +1,9 @@
-// Split-bfloat16 grouped block GEMM on the 5th-generation tensor cores
-// (tcgen05, sm_103a).  Same task lists as the float64 kernel: each CTA owns
-// one 128 x 64 output tile and walks its K-list; every float64 operand value
-// v is split into hi = bf16(v), lo = bf16(v - hi) while it is staged into
-// shared memory, and the tile accumulates Ahi*Bhi + Ahi*Blo + Alo*Bhi in
-// float32 in tensor memory (TMEM).  One elected thread issues the MMAs and
+// Split-bfloat16 (or split-float16) grouped block GEMM on the 5th-generation
+// tensor cores (tcgen05, sm_103a).  Same task lists as the float64 kernel:
+// each CTA owns one 128 x 64 output tile and walks its K-list; every float64
+// operand value v is split into hi = bf16(v), lo = bf16(v - hi) (f16 in the
+// float16 variant) while it is staged into shared memory, and the tile
+// accumulates Ahi*Bhi + Ahi*Blo + Alo*Bhi in float32 in tensor memory (TMEM).  One elected thread issues the MMAs and
 // commits them to an mbarrier per shared-memory stage (double buffered).
 // The eight warps stage the operands with 16 independent loads in flight
 // per thread, and read the accumulator back with tcgen05.ld (warp w: TMEM
@@ -15,6 +15,7 @@
 // so the leading-dimension (K) core-matrix stride is 128 B and the
 // stride-dimension (8-row group) stride is 1024 B.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 
@@ -53,9 +54,12 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     return d;                            // base offset 0, layout type 0 (no swizzle)
 }
 
-// Instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major.
+// Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B of the
+// same 16-bit type (bits 7-9 and 10-12: 1 = bf16, 0 = f16), both K-major.
+template <bool F16>
 __host__ __device__ constexpr uint32_t make_idesc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | ((F16 ? 0u : 1u) << 7) | ((F16 ? 0u : 1u) << 10) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -111,13 +115,23 @@ __device__ __forceinline__ float d2f_rn(double v) {
     return __uint_as_float(f);
 }
 
+// hi = round(f), lo = round(f - hi) in the 16-bit type (bf16 or f16)
+template <bool F16>
 __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, uint32_t off, float f) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(f);
-    const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
-    *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
-    *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
+    if constexpr (F16) {
+        const __half h = __float2half_rn(f);
+        const __half l = __float2half_rn(f - __half2float(h));
+        *reinterpret_cast<__half*>(hi + off) = h;
+        *reinterpret_cast<__half*>(lo + off) = l;
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(f);
+        const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
+        *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
+        *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
+    }
 }
 
+template <bool F16>
 __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__ tasks,
                                                     const GemmOp* __restrict__ ops, int* err,
                                                     const int* __restrict__ skip) {
@@ -148,7 +162,7 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base_sh;
-    constexpr uint32_t idesc = make_idesc();
+    constexpr uint32_t idesc = make_idesc<F16>();
 
     int stage = 0;
     bool ok = true;
@@ -186,7 +200,7 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < LCH; ++q) split_store(Ahi, Alo, (uint32_t)off[q], alpha * d2f_rn(v[q]));
+                for (int q = 0; q < LCH; ++q) split_store<F16>(Ahi, Alo, (uint32_t)off[q], alpha * d2f_rn(v[q]));
             }
             for (int e0 = 0; e0 < BN * BK; e0 += NTH * LCH) {
                 double v[LCH];
@@ -204,7 +218,7 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < LCH; ++q) split_store(Bhi, Blo, (uint32_t)off[q], d2f_rn(v[q]));
+                for (int q = 0; q < LCH; ++q) split_store<F16>(Bhi, Blo, (uint32_t)off[q], d2f_rn(v[q]));
             }
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
@@ -286,15 +300,16 @@ int tc_tile_m() { return BM; }
 int tc_tile_n() { return BN; }
 
 void launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmOp* ops, int* err, cudaStream_t st,
-                    const int* skip) {
+                    const int* skip, bool f16) {
     if (ntask <= 0) return;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        attr = true;
-    }
     count_launch();
-    k_gemm_tc<<<ntask, NTH, SMEM_BYTES, st>>>(tasks, ops, err, skip);
+    if (f16) {
+        ensure_smem_attr(reinterpret_cast<const void*>(k_gemm_tc<true>), SMEM_BYTES);
+        k_gemm_tc<true><<<ntask, NTH, SMEM_BYTES, st>>>(tasks, ops, err, skip);
+    } else {
+        ensure_smem_attr(reinterpret_cast<const void*>(k_gemm_tc<false>), SMEM_BYTES);
+        k_gemm_tc<false><<<ntask, NTH, SMEM_BYTES, st>>>(tasks, ops, err, skip);
+    }
 }
 
 }  // namespace mpspt

@@ -1,9 +1,10 @@
 // Allocation-free variant of the batched float64 eigensolver entry point.
 //
-// Some callers cannot allocate device memory while they call us: code that
-// runs inside a CUDA graph being captured (where cudaMalloc is not allowed),
-// real-time or embedded hosts that reserve all memory up front, or callers
-// whose own memory pool owns the device and forbids other allocations.  For
+// Some callers cannot allocate device memory while they call us: hosts that
+// reserve all device memory up front for their own allocator (an
+// allocation here would fail, or would go around the pool that accounts
+// for every byte), and latency-bound callers that cannot afford the device
+// synchronisation and driver round trip a fresh allocation may cost.  For
 // them mpspt_eigh_batched_noalloc keeps its working storage (the task table
 // and the work copy of the input matrices) in one fixed, file-scope device
 // array instead of allocating it per call.
@@ -13,7 +14,8 @@
 // it: calls whose GPU work overlaps (different streams, or several host
 // threads) race on it and must be serialised by the caller.  Each call
 // overwrites all of the storage it uses, so nothing carries over from the
-// previous call.
+// previous call.  The call makes `device` current for its own work and puts
+// the caller's current device back before it returns, on every path.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -46,6 +48,20 @@ mpspt_status scratch_address(int device, double** out) {
     return MPSPT_OK;
 }
 
+// Makes `device` current for the lifetime of the guard and restores the
+// device that was current before.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(device) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
 
 extern "C" mpspt_status mpspt_eigh_batched_noalloc(int device, void* stream, int batch, const int* n,
@@ -57,7 +73,8 @@ extern "C" mpspt_status mpspt_eigh_batched_noalloc(int device, void* stream, int
         tot += (size_t)n[i] * n[i];
     }
     if (tot > kScratchDoubles - kTaskDoubles) return MPSPT_ERR_INVALID;   // beyond the fixed scratch
-    if (cudaSetDevice(device) != cudaSuccess) return MPSPT_ERR_CUDA;
+    DeviceGuard dg(device);
+    if (!dg.ok) return MPSPT_ERR_CUDA;
     double* base = nullptr;
     const mpspt_status s = scratch_address(device, &base);
     if (s != MPSPT_OK) return s;

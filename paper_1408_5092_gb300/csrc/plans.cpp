@@ -59,7 +59,7 @@ void GemmPlan::run(cudaStream_t st) const {
     if (nt == 0) return;
     const GemmTask* t = dtasks.as<GemmTask>();
     const GemmOp* o = dops.as<GemmOp>();
-    if (kind == GEMM_TC) launch_gemm_tc(t, nt, o, err, st, skip);
+    if (is_tc(kind)) launch_gemm_tc(t, nt, o, err, st, skip, kind == GEMM_TC16);
     else if (kind == GEMM_F32) (skinny ? launch_gemm_f64in_f32_skinny : launch_gemm_f64in_f32)(t, nt, o, st, skip);
     else (skinny ? launch_gemm_f64_skinny : launch_gemm_f64)(t, nt, o, st, skip);
 }
@@ -256,7 +256,7 @@ void TwoSitePlan::build(const Omega& om, const TwoT& bra, const TwoT& ket, const
         }
         // g2: out(sl, :) = Lpack(sl) V_stack(sl); TC computes the transpose (rows = panel cols)
         const int dl = braL.sec[sl].dim, K = lp_cols[sl];
-        if (kind == GEMM_TC) {
+        if (is_tc(kind)) {
             const long long co = g2.add_cmap(cm);
             int m0 = g2.mark();
             g2.op(Vp + voff[sl], W, Lpp + lp_off[sl], K, K, 1 | 2, 1.0);

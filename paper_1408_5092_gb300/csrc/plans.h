@@ -7,7 +7,9 @@
 
 namespace mpspt {
 
-enum GemmKind { GEMM_F64 = 0, GEMM_F32 = 1, GEMM_TC = 2 };
+// GEMM_TC: split-bf16 tcgen05; GEMM_TC16: split-f16 tcgen05 (same tiles)
+enum GemmKind { GEMM_F64 = 0, GEMM_F32 = 1, GEMM_TC = 2, GEMM_TC16 = 3 };
+inline bool is_tc(int kind) { return kind == GEMM_TC || kind == GEMM_TC16; }
 
 struct GemmPlan {
     int tm = GEMM_TM, tn = GEMM_TN;   // output tile (TC kernel: 128 x 64; skinny: 16 x 128)
@@ -18,8 +20,8 @@ struct GemmPlan {
     void set_kind(int k, int* e, bool skinny_ = false) {
         kind = k;
         err = e;
-        skinny = skinny_ && k != GEMM_TC;
-        if (k == GEMM_TC) { tm = tc_tile_m(); tn = tc_tile_n(); }
+        skinny = skinny_ && !is_tc(k);
+        if (is_tc(k)) { tm = tc_tile_m(); tn = tc_tile_n(); }
         else if (skinny) { tm = 16; tn = 128; }
         else { tm = GEMM_TM; tn = GEMM_TN; }
     }

@@ -21,7 +21,7 @@ Conventions (shared by every consumer):
   (p0a, p0b, p1a, p1b, ...) applied to the vacuum.
 """
 from .integrals import integrals, config_integrals, partition_bond_dims, CONFIGS, EVAL_SEED, TRAIN_SEED
-from .reference import fci_reference
+from .reference import config_reference, fci_reference
 
 __all__ = ["integrals", "config_integrals", "partition_bond_dims", "CONFIGS", "EVAL_SEED", "TRAIN_SEED",
-           "fci_reference"]
+           "fci_reference", "config_reference"]

@@ -7,6 +7,8 @@ spin-adapted excitation operators E_pq; it shares nothing with the oracle's
 spin-orbital operator code, so the oracle can check it independently.
 """
 import itertools
+import os
+
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
@@ -112,7 +114,10 @@ def fci_reference(h, L, k_act, n_elec, n_roots=8, s2_tol=1e-8):
         w, v = np.linalg.eigh(H.toarray())
     else:
         nr = min(n_roots, dim - 2)
-        w, v = spla.eigsh(H, k=nr, which="SA", tol=1e-14, maxiter=20000)
+        # seeded start vector: ARPACK otherwise draws a random one, and the
+        # converged vector then differs between runs at the 1e-14 level
+        v0 = np.random.Generator(np.random.PCG64(0)).normal(size=dim)
+        w, v = spla.eigsh(H, k=nr, which="SA", tol=1e-14, maxiter=20000, v0=v0)
         order = np.argsort(w)
         w, v = w[order], v[:, order]
     chosen = None
@@ -146,3 +151,32 @@ def fci_reference(h, L, k_act, n_elec, n_roots=8, s2_tol=1e-8):
     if ci[imax] < 0:
         ci = -ci
     return ci, energy
+
+
+_DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+
+
+def stored_reference_path(name, seed):
+    return os.path.join(_DATA, f"{name}_seed{seed}_psi0.npz")
+
+
+def config_reference(name, seed=None):
+    """(h, L, config, ci) of a named workload.
+
+    The reference vector is read from ``synthetic/data`` when a stored copy
+    of (name, seed) exists (written by ``python -m synthetic.store_reference``
+    from fci_reference).  LAPACK/ARPACK round differently on different
+    machines and BLAS builds, and sweep energies at medium size respond to
+    1e-14 changes of Psi0 at the 1e-9 level, so every machine that compares
+    against stored oracle values must start from the same bits."""
+    from .integrals import EVAL_SEED, config_integrals
+    seed = EVAL_SEED if seed is None else seed
+    h, L, c = config_integrals(name, seed=seed)
+    path = stored_reference_path(name, seed)
+    if os.path.exists(path):
+        z = np.load(path)
+        ci = np.zeros(4 ** c["k_act"])
+        ci[z["idx"]] = z["val"]
+    else:
+        ci, _ = fci_reference(h, L, c["k_act"], c["n_elec"])
+    return h, L, c, ci

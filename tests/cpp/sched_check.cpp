@@ -4,8 +4,6 @@
 // rotated exactly once per sweep.  Prints "ok <cases>" or the first failure.
 #include <algorithm>
 #include <cstdio>
-#include <numeric>
-#include <random>
 #include <set>
 #include <utility>
 #include <vector>
@@ -14,57 +12,46 @@
 
 int main() {
     int cases = 0;
-    std::mt19937 gen(7);
     std::vector<int> sizes;
     for (int n = 1; n <= 40; ++n) sizes.push_back(n);
     for (int n : {47, 48, 64, 99, 184, 185, 300}) sizes.push_back(n);
     for (int n : sizes) {
-        std::vector<int> perm(n);
-        std::iota(perm.begin(), perm.end(), 0);
-        std::shuffle(perm.begin(), perm.end(), gen);
-        std::set<int> ks = {1, 2, 3, n / 3, n / 2, n - 1, n};
-        for (int mode = 0; mode < 2; ++mode) {
-            for (int kS : ks) {
-                if (mode == 0 && kS != 1) continue;
-                if (kS < 1 || kS > n) continue;
-                mpspt::Sched sc;
-                sc.init(mode, n, perm.data(), mode == 1 ? kS : 0);
-                std::set<std::pair<int, int>> pairs;
-                if (sc.rounds() > 2 * n + 4) { printf("too many rounds n=%d\n", n); return 1; }
-                for (int r = 0; r < sc.rounds(); ++r) {
-                    const int ns = sc.slots(r);
-                    if (ns > std::max(n, 1)) { printf("slots %d > n=%d\n", ns, n); return 1; }
-                    std::vector<int> seen;
-                    int np = 0;
-                    for (int k = 0; k < ns; ++k) {
-                        int p, q;
-                        sc.slot(r, k, p, q);
-                        seen.push_back(p);
-                        if (q >= 0) {
-                            if (!(p < q)) { printf("order n=%d\n", n); return 1; }
-                            seen.push_back(q);
-                            ++np;
-                            if (!pairs.insert({p, q}).second) {
-                                printf("pair twice n=%d mode=%d kS=%d (%d,%d)\n", n, mode, kS, p, q);
-                                return 1;
-                            }
-                        }
+        mpspt::Sched sc;
+        sc.init(n);
+        std::set<std::pair<int, int>> pairs;
+        if (sc.rounds() > 2 * n + 4) { printf("too many rounds n=%d\n", n); return 1; }
+        for (int r = 0; r < sc.rounds(); ++r) {
+            const int ns = sc.slots(r);
+            if (ns > std::max(n, 1)) { printf("slots %d > n=%d\n", ns, n); return 1; }
+            std::vector<int> seen;
+            int np = 0;
+            for (int k = 0; k < ns; ++k) {
+                int p, q;
+                sc.slot(r, k, p, q);
+                seen.push_back(p);
+                if (q >= 0) {
+                    if (!(p < q)) { printf("order n=%d\n", n); return 1; }
+                    seen.push_back(q);
+                    ++np;
+                    if (!pairs.insert({p, q}).second) {
+                        printf("pair twice n=%d (%d,%d)\n", n, p, q);
+                        return 1;
                     }
-                    std::sort(seen.begin(), seen.end());
-                    for (int i = 0; i < n; ++i)
-                        if ((int)seen.size() != n || seen[i] != i) {
-                            printf("round misses an index n=%d mode=%d kS=%d r=%d\n", n, mode, kS, r);
-                            return 1;
-                        }
-                    if (np > sc.half) { printf("pairs %d > half n=%d\n", np, n); return 1; }
                 }
-                if ((long long)pairs.size() != (long long)n * (n - 1) / 2) {
-                    printf("sweep misses pairs n=%d mode=%d kS=%d: %zu\n", n, mode, kS, pairs.size());
+            }
+            std::sort(seen.begin(), seen.end());
+            for (int i = 0; i < n; ++i)
+                if ((int)seen.size() != n || seen[i] != i) {
+                    printf("round misses an index n=%d r=%d\n", n, r);
                     return 1;
                 }
-                ++cases;
-            }
+            if (np > sc.half) { printf("pairs %d > half n=%d\n", np, n); return 1; }
         }
+        if ((long long)pairs.size() != (long long)n * (n - 1) / 2) {
+            printf("sweep misses pairs n=%d: %zu\n", n, pairs.size());
+            return 1;
+        }
+        ++cases;
     }
     printf("ok %d\n", cases);
     return 0;

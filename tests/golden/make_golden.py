@@ -1,8 +1,13 @@
 """Writes the stored oracle energies used by the GPU parity tests.
 
 Calls only oracle/ (and the seeded inputs of synthetic/).  Run from the repo
-root:  python tests/golden/make_golden.py [tiny|medium_partitions|medium64 [fock|dyall [sweeps]]]
-(medium: the first sweeps of the M = 64 run; the tests compare E2 per sweep).
+root:
+    python tests/golden/make_golden.py [tiny|medium_partitions|medium<M> [fock|dyall [sweeps]]] [--threads T]
+(medium<M>: the sweep history at bond dimension M; the tests compare E2 per
+sweep).  The medium reference vector is the stored one
+(synthetic.config_reference), so the GPU machine starts from the same bits.  The
+BLAS thread count is fixed (default 2) and recorded: it changes the summation
+order of the oracle's matrix products.
 """
 import json
 import os
@@ -42,8 +47,7 @@ def tiny():
 def medium_partitions(M, h0, pairs):
     """Per-partition E2 of a few virtual-pair partitions of the medium system."""
     from oracle.partition import SubProblem
-    h, L, c = synthetic.config_integrals("medium")
-    ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
+    h, L, c, ci = synthetic.config_reference("medium")
     p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
     out = {"config": "medium", "h0": h0, "M": M, "parts": []}
     for a, b in pairs:
@@ -55,21 +59,50 @@ def medium_partitions(M, h0, pairs):
     return out
 
 
-def medium(M, h0, sweeps):
-    h, L, c = synthetic.config_integrals("medium")
-    ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
+def medium(M, h0, sweeps, out_name):
+    """Sweep history at bond dimension M; the file is rewritten after every
+    sweep (with E3 of the state at that point), so a long run leaves usable
+    values while it goes on."""
+    h, L, c, ci = synthetic.config_reference("medium")
     p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
     t = time.time()
-    sw = HylleraasSweep(p, M, tol_e=1e-9, max_sweeps=sweeps, verbose=True)
-    e2 = sw.run()
-    e3 = third_order(sw)
-    print("E3", e3, flush=True)
-    return {"config": "medium", "h0": h0, "M": M, "E_ref": p.E_ref, "E0": p.E0, "E1": p.E1,
-            "E2": e2, "E3": e3, "sweeps": len(sw.history), "history": sw.history, "tol_e": 1e-9,
-            "oracle_s": time.time() - t}
+    sw = HylleraasSweep(p, M, tol_e=1e-10, max_sweeps=sweeps, verbose=True)
+    res = {"config": "medium", "h0": h0, "M": M, "E_ref": p.E_ref, "E0": p.E0, "E1": p.E1,
+           "tol_e": 1e-10, "blas_threads": THREADS, "history": [], "E3_history": [],
+           "max_discarded": [], "cg_iters": [], "sweep_s": []}
+    prev = None
+    for n in range(sweeps):
+        t1 = time.time()
+        sw.discarded = []
+        e = sw.sweep()
+        sw.history.append(e)
+        e3 = third_order(sw)
+        res["history"].append(e)
+        res["E3_history"].append(e3)
+        res["max_discarded"].append(max(sw.discarded))
+        res["cg_iters"].append(sw.cg_iters)
+        res["sweep_s"].append(time.time() - t1)
+        res.update({"E2": e, "E3": e3, "sweeps": len(sw.history), "oracle_s": time.time() - t,
+                    "converged": prev is not None and abs(e - prev) < 1e-10})
+        print(f"sweep {n}: E2 = {e:.12f} E3 = {e3:.12f} max discarded {max(sw.discarded):.3e} "
+              f"({time.time() - t1:.0f} s)", flush=True)
+        with open(os.path.join(HERE, out_name), "w") as f:
+            json.dump(res, f, indent=1)
+        if res["converged"]:
+            break
+        prev = e
+    return res
 
+
+THREADS = 2
 
 if __name__ == "__main__":
+    if "--threads" in sys.argv:
+        k = sys.argv.index("--threads")
+        THREADS = int(sys.argv[k + 1])
+        del sys.argv[k:k + 2]
+    from threadpoolctl import threadpool_limits
+    threadpool_limits(THREADS)
     what = sys.argv[1] if len(sys.argv) > 1 else "tiny"
     if what == "tiny":
         res = tiny()
@@ -80,8 +113,8 @@ if __name__ == "__main__":
     else:
         M = int(what.replace("medium", ""))
         h0 = sys.argv[2] if len(sys.argv) > 2 else "fock"
-        res = medium(M, h0, int(sys.argv[3]) if len(sys.argv) > 3 else 3)
         name = f"oracle_medium_{h0}_M{M}.json"
+        res = medium(M, h0, int(sys.argv[3]) if len(sys.argv) > 3 else 3, name)
     with open(os.path.join(HERE, name), "w") as f:
         json.dump(res, f, indent=1)
     print("wrote", name)

@@ -61,7 +61,7 @@ def test_fp64_roofline_arithmetic():
 def _run_reference(env_extra):
     env = dict(os.environ, **env_extra)
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "0", "--M", "32"],
+                          "--steps", "1", "--warmup", "0", "--M", "16", "--config", "tiny"],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     return [l for l in out.stdout.splitlines() if l.strip()]
@@ -78,7 +78,7 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert "workload" in d["config"] and d["config"]["M"] == 32
+    assert "workload" in d["config"] and d["config"]["M"] == 16
 
 
 def test_reference_arm_other_ranks_exit_quietly():

@@ -46,7 +46,7 @@ def _ctx(L, seed, use_learned=0):
     o.use_learned = use_learned
     ctx = L.mpspt_create(o)
     L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
-    L.mpspt_set_reference(ctx, ci)
+    L.mpspt_set_reference_ci(ctx, ci)
     return ctx
 
 

@@ -18,8 +18,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def medium():
-    h, L, c = synthetic.config_integrals("medium")
-    ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
+    h, L, c, ci = synthetic.config_reference("medium")
     return h, L, c, ci
 
 
@@ -58,7 +57,7 @@ def test_medium_local_operators(medium, h0):
     o = L.mpspt_default_options()
     ctx = L.mpspt_create(o)
     L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
-    L.mpspt_set_reference(ctx, ci)
+    L.mpspt_set_reference_ci(ctx, ci)
     psi = L.mpspt_mps_import(ctx, sw.psi1.A, sw.psi1.q)
     rng = np.random.default_rng(9)
     for i in (5, 7, 20):
@@ -82,42 +81,53 @@ def test_medium_local_operators(medium, h0):
     L.mpspt_destroy(ctx)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 3e-8), ("mixed", 1e-6)])
-def test_medium_e2_per_sweep_matches_oracle(medium, prec, tol):
-    """E2 after each of the first sweeps at M = 64 (Fock H0) against the
-    oracle's sweep history from the same seeded initial Psi1
-    (tests/golden/oracle_medium_fock_M64.json, written by make_golden.py).
-    M = 64 truncates strongly (discarded weight ~6e-2) and converges slowly,
-    so the comparison is per sweep, not on a converged value.
-
-    Tolerance: this case is ill-conditioned.  Truncating at a cut with close
-    density-matrix eigenvalues amplifies rounding-level changes of the
-    inputs.  In the oracle, a 1e-14 relative perturbation of Psi0 moves the
-    first-sweep E2 by 9e-9 (and by 3e-9 / 1e-9 after sweeps 2 / 3).  Psi0
-    itself comes from an iterative eigensolver reproducible to that level
-    across machines, so float64 parity is held at 3e-8 here; the tiny
-    system's converged energies are held at 1e-8."""
+def _gold(name):
     import json
     import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not written yet (tests/golden/make_golden.py)")
+    return json.load(open(path))
+
+
+@pytest.mark.parametrize("h0,M", [("fock", 64), ("dyall", 64), ("dyall", 128)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 1e-6), ("mixed_fp16", 1e-6)])
+def test_medium_e2_per_sweep_matches_oracle(medium, h0, M, prec, tol):
+    """E2 (and E3 of the state after the last compared sweep) per sweep at
+    bond dimension M against the oracle's sweep history from the same seeded
+    initial Psi1 and the same stored Psi0 (tests/golden/, written by
+    make_golden.py, which rewrites the file after every oracle sweep).  M = 64
+    truncates strongly (discarded weight ~5e-2); later sweeps approach the
+    converged value, which does not depend on the starting state.
+
+    Tolerance: the benchmark spec's targets, 1e-8 Eh for float64 and 1e-6 Eh for
+    the mixed paths.  Reading R7's keep threshold (1e-10 tr rho) keeps the
+    truncated basis six decades above float64 eigensolver rounding, so the
+    kept space does not depend on how either side rounds."""
     from paper_1408_5092_gb300 import _lib as L
-    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_medium_fock_M64.json")))
+    gold = _gold(f"oracle_medium_{h0}_M{M}.json")
+    hist_ref = gold["history"]
+    n = len(hist_ref)
     h, Lc, c, ci = medium
     o = L.mpspt_default_options()
     o.prec = L.PREC[prec]
-    o.max_sweeps = 3
-    o.e_tol = 1e-14          # run all three sweeps
+    o.max_sweeps = n
+    o.e_tol = 1e-14          # run all n sweeps
     ctx = L.mpspt_create(o)
     L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
-    L.mpspt_set_reference(ctx, ci)
-    e0, e1, eref = L.mpspt_energies(ctx, "fock")
+    L.mpspt_set_reference_ci(ctx, ci)
+    e0, e1, eref = L.mpspt_energies(ctx, h0)
     assert abs(eref - gold["E_ref"]) < 1e-10 and abs(e0 - gold["E0"]) < 1e-10
-    e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, "fock", 64)
+    e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, h0, M)
     hist = [rep.e2_per_sweep[s] for s in range(rep.n_sweeps)]
-    assert rep.n_sweeps == 3
-    for s in range(3):
-        assert abs(hist[s] - gold["history"][s]) < tol, (s, hist[s], gold["history"][s])
-    # E3 (Eq. 5) of the three-sweep Psi1, conditioned like E2
-    e3 = L.mpspt_third_order(ctx, "fock", psi)
-    assert abs(e3 - gold["E3"]) < (1e-7 if prec == "fp64" else 1e-6), (e3, gold["E3"])
+    assert rep.n_sweeps == n
+    dev = [abs(a - b) for a, b in zip(hist, hist_ref)]
+    print(f"{h0} M={M} {prec}: max |E2 - oracle| per sweep {max(dev):.2e}", dev)
+    assert max(dev) < tol, (hist, hist_ref)
+    # E3 (Eq. 5) of the final Psi1
+    e3 = L.mpspt_third_order(ctx, h0, psi)
+    e3_ref = gold["E3_history"][n - 1] if "E3_history" in gold else gold["E3"]
+    print(f"  E3 {e3:.12f} oracle {e3_ref:.12f} diff {abs(e3 - e3_ref):.2e}")
+    assert abs(e3 - e3_ref) < tol, (e3, e3_ref)
     L.mpspt_mps_free(psi)
     L.mpspt_destroy(ctx)

@@ -22,7 +22,7 @@ def _ctx(L, tiny, prec="fp64"):
     o.prec = L.PREC[prec]
     ctx = L.mpspt_create(o)
     L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
-    L.mpspt_set_reference(ctx, ci)
+    L.mpspt_set_reference_ci(ctx, ci)
     return ctx
 
 
@@ -73,12 +73,11 @@ def test_medium_partitions_match_oracle():
     from paper_1408_5092_gb300 import _lib as L
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
                                        "oracle_medium_partitions_fock_M16.json")))
-    h, Lc, c = synthetic.config_integrals("medium")
-    ci, _ = synthetic.fci_reference(h, Lc, c["k_act"], c["n_elec"])
+    h, Lc, c, ci = synthetic.config_reference("medium")
     o = L.mpspt_default_options()
     ctx = L.mpspt_create(o)
     L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
-    L.mpspt_set_reference(ctx, ci)
+    L.mpspt_set_reference_ci(ctx, ci)
     pairs = [(p["a"], p["b"]) for p in gold["parts"]]
     tot, ep, rep = L.mpspt_minimize_partitioned(ctx, "fock", pairs, [gold["M"]] * len(pairs), n_streams=4)
     ref = np.array([p["E2"] for p in gold["parts"]])

@@ -55,7 +55,9 @@ def test_null_arguments_are_rejected():
     n1 = (ctypes.c_int * 1)(4)
     assert lib.mpspt_create(None, None) == inv
     assert lib.mpspt_set_integrals(None, 2, 2, 2, None, None, 1) == inv
-    assert lib.mpspt_set_reference(None, None, 0) == inv
+    assert lib.mpspt_set_reference_ci(None, None, 0) == inv
+    assert lib.mpspt_set_reference(None, 0, None, None, None) == inv
+    assert lib.mpspt_ground_state(None, 16, 0.0, None, None, None) == inv
     assert lib.mpspt_minimize_hylleraas(None, 0, 16, None, None, None) == inv
     assert lib.mpspt_minimize_partitioned(None, 0, 1, None, None, 1, None, None, None) == inv
     assert lib.mpspt_third_order(None, 0, None, None) == inv

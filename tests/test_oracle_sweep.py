@@ -24,9 +24,19 @@ def tiny():
 @pytest.mark.parametrize("h0", ["fock", "dyall"])
 def test_exact_at_full_bond_dimension(tiny, h0):
     p, ex, m_exact = tiny[h0]
-    sw = HylleraasSweep(p, m_exact)
+    # keep threshold at the rounding level: the sweep reproduces the
+    # uncontracted E2* and E3* (the large-M limit of the paper)
+    sw = HylleraasSweep(p, m_exact, keep_rel=1e-13)
     assert abs(sw.run() - ex.e2()) < 1e-9
     assert abs(third_order(sw) - ex.e3()) < 1e-9
+    # reading R7's threshold (1e-10 tr rho) drops Schmidt states of weight
+    # below it: E2 stays an upper bound and moves by O(weight) (Eq. 1 is
+    # quadratic about its minimum), E3 by O(sqrt(weight)) (Eq. 5 is not
+    # stationary)
+    sw = HylleraasSweep(p, m_exact)
+    e2 = sw.run()
+    assert -1e-12 <= e2 - ex.e2() < 1e-9
+    assert abs(third_order(sw) - ex.e3()) < 1e-7
 
 
 def test_upper_bound_and_monotone_in_m(tiny):
@@ -40,7 +50,7 @@ def test_upper_bound_and_monotone_in_m(tiny):
 
 def test_initial_state_canonicalisation():
     """Reading R8: the seeded random MPS is made right-canonical by
-    right-to-left density-matrix splits (no M cap, states above 1e-13 tr rho
+    right-to-left density-matrix splits (no M cap, states above 1e-10 tr rho
     kept).  The state changes only by the dropped directions (relative norm
     below sqrt of their weight), every site but the first is right-
     orthonormal, and no bond grows."""

@@ -1,5 +1,5 @@
 """The renormalisation step of the oracle sweep: state selection by reading
-R7 (M largest density-matrix eigenvalues above 1e-13 tr rho, a tied group at
+R7 (M largest density-matrix eigenvalues above 1e-10 tr rho, a tied group at
 the cut dropped whole) and the split of a two-site tensor, checked against
 the Eckart-Young identity: the squared error of the kept projection equals
 the discarded eigenvalue sum exactly."""
@@ -22,7 +22,7 @@ def test_select_keeps_the_m_largest_above_the_threshold():
     kept, disc = _kept(ev, 3)
     assert kept == [((3, -1), 0), ((3, 1), 0), ((3, 1), 1)]
     assert disc == pytest.approx((0.05 + 1e-15) / tr, rel=1e-12)
-    # M above the number of states: everything above 1e-13 tr rho, nothing else
+    # M above the number of states: everything above 1e-10 tr rho, nothing else
     kept, disc = _kept(ev, 10)
     assert len(kept) == 4 and ((3, 1), 2) not in kept
     assert disc == pytest.approx(1e-15 / tr, rel=1e-6)

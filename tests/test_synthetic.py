@@ -49,3 +49,14 @@ def test_seeded_and_deterministic():
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     assert not np.array_equal(a[0], c[0])
     assert synthetic.EVAL_SEED != synthetic.TRAIN_SEED
+
+
+def test_stored_medium_reference_is_the_fci_singlet():
+    """The stored medium Psi0 (read by config_reference so that every machine
+    starts from the same bits) is the string-based FCI singlet: same vector
+    to 1e-10, unit norm, Sz = 0 / N = 8 strings only."""
+    import numpy as np
+    h, L, c, ci = synthetic.config_reference("medium")
+    ref, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
+    assert abs(np.linalg.norm(ci) - 1.0) < 1e-14
+    assert np.abs(ci - ref).max() < 1e-10
