@@ -98,6 +98,14 @@ typedef struct {
     const char* autotune_cache; /* file of tuned tile shapes: read by            */
                                 /* mpspt_create, written by mpspt_destroy; NULL */
                                 /* = tune in memory only                         */
+    int cuda_graphs;            /* 1: each local CG solve captures a chunk of 8  */
+                                /* iterations (sigma + vector updates) in a CUDA */
+                                /* graph and replays it until converged; the    */
+                                /* sigma time then includes the chunk's vector  */
+                                /* kernels.  Needs a created stream (the legacy */
+                                /* default stream cannot be captured: there the */
+                                /* option has no effect); partitions always run */
+                                /* on created streams                            */
 } mpspt_options;
 
 typedef struct {
@@ -124,6 +132,8 @@ typedef struct {
                                  /* of each sweep                                */
     long long sigma_calls_cum[64]; /* applications of A_loc (all precisions)     */
                                  /* done by the end of each sweep                */
+    double host_wait_ms;         /* host time blocked waiting for the device     */
+                                 /* (partitioned: summed over the partitions)    */
 } mpspt_report;
 
 /* Fills *opt with defaults: device 0, default stream, FP64, 30 sweeps,
@@ -204,6 +214,18 @@ mpspt_status mpspt_energies(mpspt_ctx* ctx, mpspt_h0 h0, double* e0, double* e1,
  * in the library source (seed from the options). */
 mpspt_status mpspt_minimize_hylleraas(mpspt_ctx* ctx, mpspt_h0 h0, int M, double* e2,
                                       mpspt_mps** psi1, mpspt_report* rep);
+
+/* E2 against the truncation error (the paper's convergence study of E2 with
+ * M and its extrapolation in the discarded weight, Figs. 3-4 and the text on
+ * the renormalisation step): minimises Eq. 1 at each bond dimension M[j]
+ * (j < n_M, with the context's options; every run starts from the seeded
+ * initial Psi1) and fits E2(M) = e2_extrap + slope * w(M) by least squares,
+ * w(M) = the largest discarded weight of the last sweep (reading: the
+ * truncation error of a converged run).  e2_M and w_M (n_M each, nullable)
+ * receive the points.  n_M >= 2 with at least two distinct w, else
+ * MPSPT_ERR_INVALID. */
+mpspt_status mpspt_extrapolate_e2(mpspt_ctx* ctx, mpspt_h0 h0, int n_M, const int* M, double* e2_M, double* w_M,
+                                  double* e2_extrap, double* slope);
 
 /* Partitioned E2 (the paper's parallelism over virtual-orbital pairs, not
  * implemented there): H0 conserves the occupation of every semicanonical
@@ -289,6 +311,20 @@ mpspt_status mpspt_harvest(mpspt_ctx* ctx, mpspt_h0 h0, int M, int max_samples, 
 /* Attach a network to the context; used when options.use_learned is set.
  * The context does not own it (NULL detaches). */
 mpspt_status mpspt_set_preconditioner(mpspt_ctx* ctx, const mpspt_mlp* net);
+
+/* End-to-end training of the learned preconditioner on the context's own
+ * problem: up to max_samples training pairs from a plain sweep at (h0, M)
+ * (as mpspt_harvest), a new network of width 256 trained on the GPU for
+ * `epochs` passes (Adam, minibatches of 256, learning rate 1e-3, seed from
+ * the options), attached to the context (as mpspt_set_preconditioner; the
+ * context owns this network and frees it with mpspt_destroy).
+ * harvest_path (nullable): if the file exists, its pairs are used instead
+ * of harvesting; otherwise the harvested pairs are written to it (int32 n,
+ * then float32 x[n * 16], then float32 t[n * 2], native byte order).
+ * loss (nullable): mean training loss of the last epoch.  The network is
+ * used when options.use_learned is set. */
+mpspt_status mpspt_train_preconditioner(mpspt_ctx* ctx, mpspt_h0 h0, int M, int max_samples, int epochs,
+                                        const char* harvest_path, float* loss);
 
 /* The float64 eigensolver of the truncation step (row "a8": density-matrix
  * sectors rho_q = X_q X_q^T, paper text on the renormalisation step) on

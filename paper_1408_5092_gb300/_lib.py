@@ -38,7 +38,7 @@ class mpspt_options(ctypes.Structure):
                 ("cg_max_iter", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("use_learned", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("eig_fp64_only", ctypes.c_int), ("keep_rel", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p)]
+                ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p), ("cuda_graphs", ctypes.c_int)]
 
 
 class mpspt_report(ctypes.Structure):
@@ -51,7 +51,7 @@ class mpspt_report(ctypes.Structure):
                 ("sigma64_flops", ctypes.c_double), ("sigma64_ms", ctypes.c_double),
                 ("learned_used", ctypes.c_longlong), ("learned_rejected", ctypes.c_longlong),
                 ("converged", ctypes.c_int), ("max_discarded_per_sweep", ctypes.c_double * 64),
-                ("sigma_calls_cum", ctypes.c_longlong * 64)]
+                ("sigma_calls_cum", ctypes.c_longlong * 64), ("host_wait_ms", ctypes.c_double)]
 
 
 class MpsptError(RuntimeError):
@@ -84,6 +84,7 @@ def load():
             "mpspt_minimize_hylleraas": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.POINTER(vp),
                                                         ctypes.POINTER(mpspt_report)]),
             "mpspt_third_order": (ctypes.c_int, [vp, ctypes.c_int, vp, dp]),
+            "mpspt_extrapolate_e2": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, dp]),
             "mpspt_minimize_partitioned": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, ip, ctypes.c_int, dp, dp,
                                                           ctypes.POINTER(mpspt_report)]),
             "mpspt_mps_free": (None, [vp]),
@@ -104,6 +105,8 @@ def load():
             "mpspt_mlp_train": (ctypes.c_int, [vp, ctypes.c_int, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_float, fp]),
             "mpspt_harvest": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, fp, ip]),
             "mpspt_set_preconditioner": (ctypes.c_int, [vp, vp]),
+            "mpspt_train_preconditioner": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                          ctypes.c_char_p, fp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -243,6 +246,16 @@ def mpspt_minimize_partitioned(ctx, h0, pairs, Ms, n_streams=0):
     return e2.value, ep, rep
 
 
+def mpspt_extrapolate_e2(ctx, h0, Ms):
+    Ms = np.ascontiguousarray(np.asarray(Ms, dtype=np.int32))
+    e2 = np.zeros(len(Ms))
+    w = np.zeros(len(Ms))
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().mpspt_extrapolate_e2(ctx, H0.get(h0, h0), len(Ms), Ms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                       _dp(e2), _dp(w), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value, e2, w
+
+
 def mpspt_third_order(ctx, h0, psi1):
     e3 = ctypes.c_double()
     _check(load().mpspt_third_order(ctx, H0.get(h0, h0), psi1, ctypes.byref(e3)))
@@ -378,6 +391,13 @@ def mpspt_harvest(ctx, h0, M, max_samples):
     n = ctypes.c_int()
     _check(load().mpspt_harvest(ctx, H0.get(h0, h0), M, max_samples, _fpp(x), _fpp(t), ctypes.byref(n)))
     return x[: n.value].copy(), t[: n.value].copy()
+
+
+def mpspt_train_preconditioner(ctx, h0, M, max_samples=20000, epochs=30, harvest_path=None):
+    loss = ctypes.c_float()
+    _check(load().mpspt_train_preconditioner(ctx, H0.get(h0, h0), M, max_samples, epochs,
+                                             harvest_path.encode() if harvest_path else None, ctypes.byref(loss)))
+    return loss.value
 
 
 def mpspt_set_preconditioner(ctx, net):

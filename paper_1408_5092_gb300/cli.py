@@ -4,6 +4,8 @@
         --prec mixed [--sweeps 64] [--e_tol 1e-7] [--e3] [--verbose 1]
     python -m paper_1408_5092_gb300.cli --config medium --partitions 300 \
         [--streams 8] [--M 0]      (partitioned mode, uneven seeded M_P)
+    python -m paper_1408_5092_gb300.cli --config partitions --dmrg 256 \
+        --partitions 1830 --M 0    (reference by the library's DMRG at M0)
 
 Prints one JSON line: E2 (and E3), the per-sweep energies and device times,
 the local-solver counters and the kernel launch count; in partitioned mode
@@ -20,11 +22,12 @@ from . import _lib as L
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--config", default="medium", choices=["tiny", "medium", "partitions", "large"])
+    ap.add_argument("--config", default="medium",
+                    choices=["tiny", "medium", "partitions", "large"])
     ap.add_argument("--seed", type=int, default=None, help="integral seed (default: the evaluation seed)")
     ap.add_argument("--M", type=int, default=64)
     ap.add_argument("--h0", default="dyall", choices=["dyall", "fock"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "mixed", "mixed_fp16"])
     ap.add_argument("--sweeps", type=int, default=64)
     ap.add_argument("--e_tol", type=float, default=1e-7)
     ap.add_argument("--eig_fp64_only", type=int, default=0)
@@ -33,12 +36,28 @@ def main(argv=None):
     ap.add_argument("--partitions", type=int, default=0,
                     help="partitioned mode: the first N virtual pairs (a <= b, a then b)")
     ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--dmrg", type=int, default=0,
+                    help="build the reference with the library's ground-state DMRG at this M0 "
+                         "(S^2 penalty 1) instead of the FCI vector")
+    ap.add_argument("--dmrg_sweeps", type=int, default=0, help="sweep cap of the reference DMRG (0: --sweeps)")
+    ap.add_argument("--s2_penalty", type=float, default=1.0,
+                    help="lambda of the DMRG's lambda S^2 term (0: lowest Sz = 0 state of any spin)")
+    ap.add_argument("--autotune", type=int, default=0)
+    ap.add_argument("--graphs", type=int, default=0, help="capture CG chunks in CUDA graphs")
+    ap.add_argument("--autotune_cache", default=None)
     a = ap.parse_args(argv)
     import synthetic
     seed = synthetic.EVAL_SEED if a.seed is None else a.seed
-    h, Lc, c = synthetic.config_integrals(a.config, seed=seed)
-    ci, _ = synthetic.fci_reference(h, Lc, c["k_act"], c["n_elec"])
+    if a.dmrg > 0:
+        h, Lc, c = synthetic.config_integrals(a.config, seed=seed)
+        ci = None
+    else:
+        h, Lc, c, ci = synthetic.config_reference(a.config, seed=seed)
     o = L.mpspt_default_options()
+    o.autotune = a.autotune
+    o.cuda_graphs = a.graphs
+    if a.autotune_cache:
+        o.autotune_cache = a.autotune_cache.encode()
     o.prec = L.PREC[a.prec]
     o.max_sweeps = a.sweeps
     o.e_tol = a.e_tol
@@ -47,7 +66,28 @@ def main(argv=None):
     ctx = L.mpspt_create(o)
     try:
         L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
-        L.mpspt_set_reference_ci(ctx, ci)
+        ref_info = {}
+        if ci is None:
+            # the reference comes from the library's DMRG in its own context
+            # (its own sweep cap) and enters this one as an MPS
+            t = time.time()
+            od = L.mpspt_default_options()
+            od.max_sweeps = a.dmrg_sweeps if a.dmrg_sweeps > 0 else a.sweeps
+            od.e_tol = a.e_tol
+            od.verbose = a.verbose
+            gctx = L.mpspt_create(od)
+            L.mpspt_set_integrals(gctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
+            e_ref, psi0, grep = L.mpspt_ground_state(gctx, a.dmrg, s2_penalty=a.s2_penalty, want_psi0=True)
+            tensors, labels = L.mpspt_mps_export(psi0)
+            L.mpspt_mps_free(psi0)
+            L.mpspt_destroy(gctx)
+            L.mpspt_set_reference(ctx, tensors, labels)
+            e0, e1, eref2 = L.mpspt_energies(ctx, a.h0)
+            ref_info = {"reference": f"DMRG M0={a.dmrg}, S^2 penalty {a.s2_penalty}", "E_ref": e_ref, "E_ref_installed": eref2, "E0": e0,
+                        "E1": e1, "dmrg_sweeps": grep.n_sweeps, "dmrg_s": time.time() - t}
+            print(json.dumps(ref_info), flush=True)
+        else:
+            L.mpspt_set_reference_ci(ctx, ci)
         if a.partitions > 0:
             kv = h.shape[0] - c["k_act"]
             pairs = [(x, y) for x in range(kv) for y in range(x, kv)][: a.partitions]
@@ -58,7 +98,9 @@ def main(argv=None):
             print(json.dumps({"config": a.config, "h0": a.h0, "prec": a.prec, "partitions": len(pairs),
                               "M_part": "seeded from {32,...,512}" if a.M <= 0 else a.M, "E2": tot,
                               "wall_s": wall, "partitions_per_s": len(pairs) / wall, "streams": a.streams,
-                              "cg_iters": rep.cg_iters, "kernel_launches": rep.kernel_launches}), flush=True)
+                              "cg_iters": rep.cg_iters, "kernel_launches": rep.kernel_launches,
+                              "host_wait_s": rep.host_wait_ms / 1e3, **ref_info}),
+                  flush=True)
             return 0
         t = time.time()
         e2, psi, rep = L.mpspt_minimize_hylleraas(ctx, a.h0, a.M, want_psi1=a.e3)
@@ -68,7 +110,7 @@ def main(argv=None):
                "sweep_ms": [rep.sweep_ms[s] for s in range(rep.n_sweeps)], "cg_iters": rep.cg_iters,
                "sigma_ms": rep.sigma_ms, "sigma_gflop": rep.sigma_flops / 1e9, "sigma64_ms": rep.sigma64_ms,
                "max_bond_dim": rep.max_bond_dim, "max_discarded_weight": rep.max_discarded_weight,
-               "kernel_launches": rep.kernel_launches}
+               "kernel_launches": rep.kernel_launches, **ref_info}
         if a.e3:
             out["E3"] = L.mpspt_third_order(ctx, a.h0, psi)
             L.mpspt_mps_free(psi)

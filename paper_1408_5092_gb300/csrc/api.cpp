@@ -1,5 +1,6 @@
 // C ABI of the MPS-PT library: argument checks, exception barrier, handles.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 
@@ -67,6 +68,7 @@ void fill_report(mpspt_report* rep, const mpspt::SweepResult& r) {
     rep->converged = r.converged ? 1 : 0;
     for (int s = 0; s < (int)r.disc_sweep.size() && s < 64; ++s) rep->max_discarded_per_sweep[s] = r.disc_sweep[s];
     for (int s = 0; s < (int)r.sigma_cum.size() && s < 64; ++s) rep->sigma_calls_cum[s] = r.sigma_cum[s];
+    rep->host_wait_ms = r.host_wait_ms;
 }
 }  // namespace
 
@@ -89,6 +91,7 @@ void mpspt_default_options(mpspt_options* o) {
     o->keep_rel = 1e-10;
     o->autotune = 0;
     o->autotune_cache = nullptr;
+    o->cuda_graphs = 0;
 }
 
 mpspt_status mpspt_create(mpspt_ctx** ctx, const mpspt_options* opt) {
@@ -246,6 +249,36 @@ mpspt_status mpspt_minimize_hylleraas(mpspt_ctx* ctx, mpspt_h0 h0, int M, double
     });
 }
 
+
+mpspt_status mpspt_extrapolate_e2(mpspt_ctx* ctx, mpspt_h0 h0, int n_M, const int* M, double* e2_M, double* w_M,
+                                  double* e2_extrap, double* slope) {
+    if (!ctx || n_M < 2 || !M || !e2_extrap || !slope) return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] {
+        auto& c = *ctx->c;
+        MPSPT_CUDA(cudaSetDevice(c.opt.device));
+        std::vector<double> e(n_M), w(n_M);
+        for (int j = 0; j < n_M; ++j) {
+            mpspt::require(M[j] >= 1, "bond dimensions must be >= 1");
+            mpspt::SweepResult r;
+            mpspt::minimize(c, h0, M[j], r);
+            e[j] = r.e2;
+            w[j] = r.max_disc;
+        }
+        // least squares line e = a + b w (centred sums, float64)
+        double mw = 0.0, me = 0.0;
+        for (int j = 0; j < n_M; ++j) { mw += w[j]; me += e[j]; }
+        mw /= n_M;
+        me /= n_M;
+        double sww = 0.0, swe = 0.0;
+        for (int j = 0; j < n_M; ++j) { sww += (w[j] - mw) * (w[j] - mw); swe += (w[j] - mw) * (e[j] - me); }
+        mpspt::require(sww > 0.0, "the discarded weights are all equal: no line to fit");
+        const double b = swe / sww;
+        if (e2_M) for (int j = 0; j < n_M; ++j) e2_M[j] = e[j];
+        if (w_M) for (int j = 0; j < n_M; ++j) w_M[j] = w[j];
+        *slope = b;
+        *e2_extrap = me - b * mw;
+    });
+}
 
 mpspt_status mpspt_minimize_partitioned(mpspt_ctx* ctx, mpspt_h0 h0, int n_part, const int* pair_ab,
                                         const int* M_part, int n_streams, double* e2_total, double* e2_part,
@@ -533,6 +566,65 @@ mpspt_status mpspt_harvest(mpspt_ctx* ctx, mpspt_h0 h0, int M, int max_samples, 
         std::copy(c.harvest_x.begin(), c.harvest_x.end(), x);
         std::copy(c.harvest_t.begin(), c.harvest_t.end(), t);
         *n_samples = ns;
+    });
+}
+
+mpspt_status mpspt_train_preconditioner(mpspt_ctx* ctx, mpspt_h0 h0, int M, int max_samples, int epochs,
+                                        const char* harvest_path, float* loss) {
+    if (!ctx || M < 1 || max_samples < 1 || epochs < 1) return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] {
+        auto& c = *ctx->c;
+        MPSPT_CUDA(cudaSetDevice(c.opt.device));
+        std::vector<float> x, t;
+        bool loaded = false;
+        if (harvest_path) {
+            if (FILE* f = std::fopen(harvest_path, "rb")) {
+                int n = 0;
+                bool ok = std::fread(&n, sizeof(int), 1, f) == 1 && n > 0;
+                if (ok) {
+                    x.resize((size_t)n * mpspt::MLP_NF);
+                    t.resize((size_t)n * 2);
+                    ok = std::fread(x.data(), sizeof(float), x.size(), f) == x.size() &&
+                         std::fread(t.data(), sizeof(float), t.size(), f) == t.size();
+                }
+                std::fclose(f);
+                mpspt::require(ok, "harvest file is truncated or empty");
+                loaded = true;
+            }
+        }
+        if (!loaded) {
+            c.harvesting = true;
+            c.harvest_max = (size_t)max_samples;
+            c.harvest_x.clear();
+            c.harvest_t.clear();
+            mpspt::SweepResult r;
+            try {
+                mpspt::minimize(c, h0, M, r);
+            } catch (...) {
+                c.harvesting = false;
+                throw;
+            }
+            c.harvesting = false;
+            x.swap(c.harvest_x);
+            t.swap(c.harvest_t);
+            mpspt::require(!x.empty(), "the sweep gave no training pairs");
+            if (harvest_path) {
+                FILE* f = std::fopen(harvest_path, "wb");
+                mpspt::require(f != nullptr, "cannot write the harvest file");
+                const int n = (int)(x.size() / mpspt::MLP_NF);
+                const bool ok = std::fwrite(&n, sizeof(int), 1, f) == 1 &&
+                                std::fwrite(x.data(), sizeof(float), x.size(), f) == x.size() &&
+                                std::fwrite(t.data(), sizeof(float), t.size(), f) == t.size();
+                std::fclose(f);
+                mpspt::require(ok, "cannot write the harvest file");
+            }
+        }
+        const int n = (int)(x.size() / mpspt::MLP_NF);
+        std::unique_ptr<mpspt::Mlp> net(new mpspt::Mlp(mpspt::MLP_NF, 256, 2, c.opt.seed, 0));
+        const float l = net->train(n, x.data(), t.data(), epochs, 256, 1e-3f);
+        c.own_net = std::move(net);
+        c.net = c.own_net.get();
+        if (loss) *loss = l;
     });
 }
 

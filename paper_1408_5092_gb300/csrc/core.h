@@ -6,9 +6,11 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <shared_mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -87,31 +89,42 @@ struct Bond {
 // before launch (every pointer range a kernel will touch must lie inside one
 // live allocation), so a planner error becomes a status, not a bad access.
 struct Registry {
-    std::mutex mu;
+    // Readers (the planners' range checks, many per task list and from every
+    // lane thread) share the lock; allocations and releases take it alone.
+    // Each thread remembers the last few allocations it found; the memory
+    // is valid until any allocation is released (gen counts releases).
+    std::shared_mutex mu;
     std::map<uintptr_t, size_t> live;
-    std::atomic<unsigned long long> gen{0};   // bumped by every release
+    std::atomic<unsigned long long> gen{0};
     static Registry& get() { static Registry r; return r; }
-    void add(const void* p, size_t n) { std::lock_guard<std::mutex> g(mu); live[(uintptr_t)p] = n; }
+    void add(const void* p, size_t n) { std::unique_lock<std::shared_mutex> g(mu); live[(uintptr_t)p] = n; }
     void remove(const void* p) {
-        std::lock_guard<std::mutex> g(mu);
+        std::unique_lock<std::shared_mutex> g(mu);
         live.erase((uintptr_t)p);
-        gen.fetch_add(1, std::memory_order_relaxed);
+        gen.fetch_add(1, std::memory_order_release);
     }
     bool contains(const void* p, size_t bytes) {
-        // planners check long runs of ranges inside one allocation: the last
-        // hit is remembered per thread until an allocation is released
-        thread_local uintptr_t c0 = 0, c1 = 0;
+        constexpr int kWays = 8;
+        thread_local uintptr_t c0[kWays] = {}, c1[kWays] = {};
         thread_local unsigned long long cg = ~0ULL;
+        thread_local int next = 0;
         const uintptr_t a = (uintptr_t)p, b = a + bytes;
-        if (cg == gen.load(std::memory_order_relaxed) && a >= c0 && b <= c1) return true;
-        std::lock_guard<std::mutex> g(mu);
+        const unsigned long long g0 = gen.load(std::memory_order_acquire);
+        if (cg == g0)
+            for (int w = 0; w < kWays; ++w)
+                if (a >= c0[w] && b <= c1[w]) return true;
+        std::shared_lock<std::shared_mutex> g(mu);
         auto it = live.upper_bound(a);
         if (it == live.begin()) return false;
         --it;
         if (!(a >= it->first && b <= it->first + it->second)) return false;
-        c0 = it->first;
-        c1 = it->first + it->second;
-        cg = gen.load(std::memory_order_relaxed);
+        if (cg != g0) {   // a release happened: forget everything remembered
+            for (int w = 0; w < kWays; ++w) c0[w] = c1[w] = 0;
+            cg = g0;
+        }
+        c0[next] = it->first;
+        c1[next] = it->first + it->second;
+        next = (next + 1) % kWays;
         return true;
     }
 };
@@ -194,12 +207,80 @@ class DBuf {
     bool owned_ = true;
 };
 
+// Pinned staging ring of one stream.  A host-to-device copy from pageable
+// memory goes through the driver's own staging buffer, which every host
+// thread of the process shares; concurrent lanes then serialise on it, and
+// the copy blocks the calling thread.  Task lists are instead copied into
+// this ring (page-locked) and sent with a truly asynchronous copy.  The ring
+// has two halves; before a half is written again, the event recorded when
+// the previous half was left is waited on, so the copies from it are done.
+struct PinnedRing {
+    unsigned char* base = nullptr;
+    size_t half = 0, off = 0;
+    int cur = 0;
+    bool used[2] = {false, false};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaStream_t st = 0;
+    PinnedRing(size_t bytes, cudaStream_t s) : st(s) {
+        half = bytes / 2;
+        MPSPT_CUDA(cudaMallocHost(&base, 2 * half));
+        MPSPT_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        MPSPT_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    }
+    ~PinnedRing() {
+        cudaStreamSynchronize(st);
+        if (base) cudaFreeHost(base);
+        for (auto& e : ev) if (e) cudaEventDestroy(e);
+    }
+    PinnedRing(const PinnedRing&) = delete;
+    PinnedRing& operator=(const PinnedRing&) = delete;
+    // page-locked copy of src (nullptr if it does not fit in a half)
+    void* stage(const void* src, size_t n) {
+        const size_t need = (n + 255) & ~(size_t)255;
+        if (need > half) return nullptr;
+        if (off + need > half) {
+            MPSPT_CUDA(cudaEventRecord(ev[cur], st));
+            used[cur] = true;
+            cur ^= 1;
+            if (used[cur]) MPSPT_CUDA(cudaEventSynchronize(ev[cur]));
+            off = 0;
+        }
+        unsigned char* p = base + (size_t)cur * half + off;
+        std::memcpy(p, src, n);
+        off += need;
+        return p;
+    }
+};
+
+// The staging ring of the calling thread's current lane (set by the sweep
+// drivers for their duration; null = plain pageable copies).
+inline PinnedRing*& thread_ring() {
+    thread_local PinnedRing* r = nullptr;
+    return r;
+}
+
+struct RingScope {
+    PinnedRing* prev;
+    explicit RingScope(PinnedRing* r) : prev(thread_ring()) { thread_ring() = r; }
+    ~RingScope() { thread_ring() = prev; }
+};
+
+inline void copy_h2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (!bytes) return;
+    PinnedRing* r = thread_ring();
+    if (r && r->st == st) {
+        if (void* p = r->stage(src, bytes)) {
+            MPSPT_CUDA(cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, st));
+            return;
+        }
+    }
+    MPSPT_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+}
+
 template <class T>
 inline void upload(DBuf& dst, const std::vector<T>& v, cudaStream_t st) {
     dst.ensure(v.size() * sizeof(T) + 16, st);
-    if (!v.empty())
-        MPSPT_CUDA(cudaMemcpyAsync(dst.get(), v.data(), v.size() * sizeof(T),
-                                   cudaMemcpyHostToDevice, st));
+    if (!v.empty()) copy_h2d(dst.get(), v.data(), v.size() * sizeof(T), st);
 }
 
 }  // namespace mpspt

@@ -8,6 +8,7 @@
 #include <thread>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <numeric>
 
 #include "hostla.h"
@@ -26,11 +27,27 @@ Lane::Lane(cudaStream_t s, bool create) : st(s), own_stream(create) {
     MPSPT_CUDA(cudaMemsetAsync(tcerr.get(), 0, sizeof(int) * 4, st));
     MPSPT_CUDA(cudaMallocHost(&cg_host, sizeof(CgState)));
     MPSPT_CUDA(cudaMallocHost(&scal_host, 16 * sizeof(double)));
+    ring.reset(new PinnedRing((size_t)16 << 20, st));
     MPSPT_CUDA(cudaStreamSynchronize(st));
+}
+
+void* Lane::readback(size_t bytes) {
+    if (bytes > rb_bytes) {
+        MPSPT_CUDA(cudaStreamSynchronize(st));
+        if (rb) cudaFreeHost(rb);
+        rb = nullptr;
+        rb_bytes = 0;
+        const size_t nb = std::max(bytes, (size_t)1 << 20);
+        MPSPT_CUDA(cudaMallocHost(&rb, nb));
+        rb_bytes = nb;
+    }
+    return rb;
 }
 
 Lane::~Lane() {
     cudaStreamSynchronize(st);
+    ring.reset();
+    if (rb) cudaFreeHost(rb);
     red.release(); cnt.release(); cg.release(); scal.release(); tcerr.release();
     cudaStreamSynchronize(st);
     if (cg_host) cudaFreeHost(cg_host);
@@ -52,10 +69,18 @@ Ctx::Ctx(const mpspt_options& o) : opt(o) {
     MPSPT_CUDA(cudaMemsetAsync(tcerr.get(), 0, sizeof(int) * 4, st));
     MPSPT_CUDA(cudaMallocHost(&cg_host, sizeof(CgState)));
     MPSPT_CUDA(cudaMallocHost(&scal_host, 16 * sizeof(double)));
+    if (o.autotune) {
+        tuner.reset(new Autotuner);
+        if (o.autotune_cache) {
+            tuner_path = o.autotune_cache;
+            tuner->load(tuner_path);
+        }
+    }
 }
 
 Ctx::~Ctx() {
     cudaStreamSynchronize(st);
+    if (tuner && !tuner_path.empty()) tuner->save(tuner_path);
     if (cg_host) cudaFreeHost(cg_host);
     if (scal_host) cudaFreeHost(scal_host);
 }
@@ -714,6 +739,11 @@ struct Sweeper {
         sig_lo.set_kind(lo_kind, ln.tcerr.as<int>());
         sig.set_kind(GEMM_F64, nullptr);
         rhs.set_kind(GEMM_F64, nullptr);
+        if (c.tuner) {
+            Autotuner* t = c.tuner.get();
+            sig.set_tuner(t); sig_lo.set_tuner(t); rhs.set_tuner(t); envp.set_tuner(t);
+            prod.tuner = t; prod0.tuner = t; gr.tuner = t; gc.tuner = t; eig.ge.tuner = t;
+        }
         MPSPT_CUDA(cudaEventCreate(&ev0));
         MPSPT_CUDA(cudaEventCreate(&ev1));
         for (auto& e : evs) MPSPT_CUDA(cudaEventCreate(&e));
@@ -723,6 +753,7 @@ struct Sweeper {
     }
     ~Sweeper() {
         if (dsc_host) { cudaStreamSynchronize(ln.st); cudaFreeHost(dsc_host); }
+        if (gexec) { cudaStreamSynchronize(ln.st); cudaGraphExecDestroy(gexec); }
         cudaEventDestroy(ev0); cudaEventDestroy(ev1);
         for (auto& e : evs) cudaEventDestroy(e);
         for (auto& e : sev) cudaEventDestroy(e);
@@ -735,7 +766,7 @@ struct Sweeper {
             E.build(dq, b, k0, ln.st);
             const double v = 1.0;
             MPSPT_CUDA(cudaMemcpyAsync(E.d.get(), &v, sizeof(double), cudaMemcpyHostToDevice, ln.st));
-            MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+            wait();
         };
         one(LA[0], WA.dq[0], psi.bond[0], psi.bond[0]);
         one(RA[k], WA.dq[k], psi.bond[k], psi.bond[k]);
@@ -855,15 +886,19 @@ struct Sweeper {
             for (const auto& t : et) { n3 += (double)t.n * t.n * t.n; nmax = std::max(nmax, t.n); }
             eig_n3 += n3; eig_nmax = std::max(eig_nmax, nmax); eig_calls += (int)et.size();
         }
-        std::vector<double> wh(wsz);
-        if (wsz) MPSPT_CUDA(cudaMemcpyAsync(wh.data(), wv.get(), wsz * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
-        std::vector<int> eflag(eig.nflags);
+        // eigenvalues and convergence flags back through the lane's
+        // page-locked buffer (one asynchronous copy each, one sync)
+        const size_t wbytes = (wsz * sizeof(double) + 15) & ~(size_t)15;
+        unsigned char* hb = static_cast<unsigned char*>(ln.readback(wbytes + eig.nflags * sizeof(int) + 16));
+        if (wsz) MPSPT_CUDA(cudaMemcpyAsync(hb, wv.get(), wsz * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
         if (eig.nflags)
-            MPSPT_CUDA(cudaMemcpyAsync(eflag.data(), eig.flags.get(), eig.nflags * sizeof(int), cudaMemcpyDeviceToHost,
+            MPSPT_CUDA(cudaMemcpyAsync(hb + wbytes, eig.flags.get(), eig.nflags * sizeof(int), cudaMemcpyDeviceToHost,
                                        ln.st));
         auto ts = clk::now();
-        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        wait();
         split_wait += since(ts);
+        std::vector<double> wh(reinterpret_cast<double*>(hb), reinterpret_cast<double*>(hb) + wsz);
+        std::vector<int> eflag(reinterpret_cast<int*>(hb + wbytes), reinterpret_cast<int*>(hb + wbytes) + eig.nflags);
         for (int f : eflag)
             require(f != 2, "truncation eigensolver: sweep cap reached before the convergence test",
                     MPSPT_ERR_NOT_CONVERGED);
@@ -1057,16 +1092,70 @@ struct Sweeper {
         }
         nev = 0;
     }
+    // ---- CUDA graphs of CG chunks (opt.cuda_graphs) ---------------------------
+    // A chunk of kChunk CG iterations (sigma + the fused vector updates, no
+    // host work in between) is captured once per local solve and replayed
+    // until the device convergence flag is set: one graph launch instead of
+    // ~7 kernel launches per iteration.  The sigma time of a graph chunk is
+    // its CUDA-event time (it includes the chunk's CG vector kernels).
+    static constexpr int kChunk = 8;
+    cudaGraphExec_t gexec = nullptr;
+    bool lo_warm = false;
+    void capture(cudaGraphExec_t& ex, const std::function<void()>& body) {
+        cudaGraph_t g = nullptr;
+        MPSPT_CUDA(cudaStreamBeginCapture(ln.st, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = launch_count_thread();
+        try {
+            body();
+        } catch (...) {
+            cudaStreamEndCapture(ln.st, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        MPSPT_CUDA(cudaStreamEndCapture(ln.st, &g));
+        uncount_launches(launch_count_thread() - l0);   // replays are counted, not the capture
+        if (ex) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(ex, g, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(ex);
+                ex = nullptr;
+            }
+        }
+        if (!ex) {
+            const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            MPSPT_CUDA(e);
+        } else {
+            cudaGraphDestroy(g);
+        }
+    }
+    void launch_graph(cudaGraphExec_t ex, bool is64, double flops_per_iter) {
+        ev_begin();
+        MPSPT_CUDA(cudaGraphLaunch(ex, ln.st));
+        count_launch();
+        ev_end(is64);
+        if (is64) { res->sigma64_calls += kChunk; res->sigma64_flops += kChunk * flops_per_iter; }
+        else { res->sigma_calls += kChunk; res->sigma_flops += kChunk * flops_per_iter; }
+    }
+
+    // host time blocked on the lane's stream (the device is behind the host)
+    void wait() {
+        const auto t = clk::now();
+        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        res->host_wait_ms += since(t);
+    }
+
     void sync_state() {
         MPSPT_CUDA(cudaMemcpyAsync(ln.cg_host, ln.cg.as<CgState>(), sizeof(CgState), cudaMemcpyDeviceToHost, ln.st));
-        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        wait();
         add_time();
     }
     void check_tc() {
         if (!is_tc(lo_kind)) return;
         int e = 0;
         MPSPT_CUDA(cudaMemcpyAsync(&e, ln.tcerr.get(), sizeof(int), cudaMemcpyDeviceToHost, ln.st));
-        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        wait();
         require(e == 0, "tensor-core GEMM: bounded mbarrier wait gave up", MPSPT_ERR_TIMEOUT);
     }
 
@@ -1076,7 +1165,7 @@ struct Sweeper {
         dot(x, w.Ap.as<double>(), n, 0);
         dot(x, w.g.as<double>(), n, 1);
         MPSPT_CUDA(cudaMemcpyAsync(ln.scal_host, ln.scal.get(), 2 * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
-        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        wait();
         return ln.scal_host[0] + 2.0 * ln.scal_host[1];
     }
 
@@ -1091,6 +1180,20 @@ struct Sweeper {
         sync_state();
         int launched = 0;
         sig.set_skip(&S->done);
+        if (c.opt.cuda_graphs && ln.st != nullptr && !ln.cg_host->done) {
+            capture(gexec, [&] {
+                for (int q = 0; q < kChunk; ++q) {
+                    sig.run(ln.st);
+                    cg_step(x, w.r.as<double>(), w.z.as<double>(), w.p.as<double>(), w.Ap.as<double>(),
+                            w.minv.as<double>(), n, S, ln.red.as<double>(), ln.cnt.as<unsigned>(), ln.st);
+                }
+            });
+            while (!ln.cg_host->done && launched < c.opt.cg_max_iter) {
+                launch_graph(gexec, true, sig.flops());
+                launched += kChunk;
+                sync_state();
+            }
+        }
         while (!ln.cg_host->done && launched < c.opt.cg_max_iter) {
             const int chunk = std::min(c.opt.cg_max_iter - launched, launched < 8 ? 4 : 8);
             for (int q = 0; q < chunk; ++q) {
@@ -1111,7 +1214,7 @@ struct Sweeper {
         res->sigma64_flops -= (launched - ln.cg_host->iters) * sig.flops();
         MPSPT_CUDA(cudaMemcpyAsync(w.p.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
         sigma64();
-        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        wait();
         add_time();
         return hylleraas(n);
     }
@@ -1132,7 +1235,7 @@ struct Sweeper {
             vec_axpy(w.r.as<double>(), w.Ap.as<double>(), -1.0, n, ln.st);
             dot(w.r.as<double>(), w.r.as<double>(), n, 3);
             MPSPT_CUDA(cudaMemcpyAsync(ln.scal_host, ln.scal.get(), 4 * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
-            MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+            wait();
             add_time();
             const double bb = ln.scal_host[2], rr = ln.scal_host[3];
             if (rr <= c.opt.cg_tol * c.opt.cg_tol * bb || bb == 0.0) break;
@@ -1148,9 +1251,28 @@ struct Sweeper {
                     w.zero.as<double>(), w.minv.as<double>(), n, S, tol_in, ln.red.as<double>(),
                     ln.cnt.as<unsigned>(), ln.st);
             MPSPT_CUDA(cudaMemcpyAsync(ln.cg_host, S, sizeof(CgState), cudaMemcpyDeviceToHost, ln.st));
-            MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+            wait();
             int launched = 0;
             sig_lo.set_skip(&S->done);
+            if (c.opt.cuda_graphs && ln.st != nullptr && !ln.cg_host->done) {
+                // the first launch of each kernel sets its attributes and
+                // occupancy cache; make it outside the capture (the product
+                // lands in Ap, which the first CG iteration overwrites)
+                if (!lo_warm) { sig_lo.run(ln.st); lo_warm = true; }
+                capture(gexec, [&] {
+                    for (int q = 0; q < kChunk; ++q) {
+                        sig_lo.run(ln.st);
+                        cg_step(w.d.as<double>(), w.ri.as<double>(), w.z.as<double>(), w.p.as<double>(),
+                                w.Ap.as<double>(), w.minv.as<double>(), n, S, ln.red.as<double>(),
+                                ln.cnt.as<unsigned>(), ln.st);
+                    }
+                });
+                while (!ln.cg_host->done && launched < c.opt.cg_max_iter) {
+                    launch_graph(gexec, false, sig_lo.flops());
+                    launched += kChunk;
+                    sync_state();
+                }
+            }
             while (!ln.cg_host->done && launched < c.opt.cg_max_iter) {
                 const int chunk = std::min(c.opt.cg_max_iter - launched, launched < 8 ? 4 : 8);
                 for (int q = 0; q < chunk; ++q) {
@@ -1207,7 +1329,7 @@ struct Sweeper {
         vec_axpy(w.r.as<double>(), w.Ap.as<double>(), -1.0, n, ln.st);
         dot(w.r.as<double>(), w.r.as<double>(), n, 4);
         MPSPT_CUDA(cudaMemcpyAsync(ln.scal_host, ln.scal.get(), 5 * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
-        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        wait();
         add_time();
         return ln.scal_host[4];
     }
@@ -1240,7 +1362,7 @@ struct Sweeper {
         std::vector<float> feat((size_t)nb * MLP_NF);
         MPSPT_CUDA(cudaMemcpyAsync(fit.data(), dfit.get(), fit.size() * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
         MPSPT_CUDA(cudaMemcpyAsync(feat.data(), dfeat.get(), feat.size() * sizeof(float), cudaMemcpyDeviceToHost, ln.st));
-        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+        wait();
         for (int q = 0; q < nb; ++q) {
             if (c.harvest_x.size() / MLP_NF >= c.harvest_max) return;
             const double* f = &fit[(size_t)q * 5];
@@ -1284,7 +1406,7 @@ struct Sweeper {
             for (int q = 0; q < cnt; ++q)
                 vec_dot(a[q], b[q], n, dsc.as<double>() + q, ln.red.as<double>(), ln.cnt.as<unsigned>(), ln.st);
             MPSPT_CUDA(cudaMemcpyAsync(dsc_host, dsc.get(), cnt * sizeof(double), cudaMemcpyDeviceToHost, ln.st));
-            MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+            wait();
         };
         {   // v0 = x / |x|
             const double* a[1] = {x};
@@ -1489,6 +1611,7 @@ MpsHost initial_mps(const Ctx& c, const Chain& ch, int M) {
 
 std::unique_ptr<MpsD> minimize(Ctx& c, const Chain& ch, int M, SweepResult& res, Lane* lane) {
     Lane& ln = lane ? *lane : *c.lane0;
+    RingScope rs(ln.ring.get());
     require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
     require(M >= 1, "bond dimension M must be >= 1");
     require(c.opt.prec == MPSPT_FP64 || c.opt.prec == MPSPT_FP32 || c.opt.prec == MPSPT_MIXED_BF16 ||
@@ -1569,6 +1692,7 @@ std::unique_ptr<MpsD> ground_state(Ctx& c, int M0, double s2_penalty, SweepResul
     require(M0 >= 1, "bond dimension M0 must be >= 1");
     require(P.ka >= 2, "ground-state DMRG needs k_act >= 2");
     Lane& ln = *c.lane0;
+    RingScope rs(ln.ring.get());
     const auto t0 = std::chrono::steady_clock::now();
     const long long l0 = launch_count();
     const int ka = P.ka;
@@ -1773,6 +1897,7 @@ double minimize_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int
     res.converged = true;
     for (const auto& r : rs) {
         res.converged = res.converged && r.converged;
+        res.host_wait_ms += r.host_wait_ms;
         res.cg_iters += r.cg_iters;
         res.sigma_calls += r.sigma_calls;
         res.sigma_flops += r.sigma_flops;

@@ -43,6 +43,10 @@ struct Lane {
     cudaStream_t st = 0;
     bool own_stream = false;
     DBuf red, cnt, cg, scal, tcerr;
+    std::unique_ptr<PinnedRing> ring;   // staging of this lane's task lists
+    void* rb = nullptr;                 // page-locked readback buffer
+    size_t rb_bytes = 0;
+    void* readback(size_t bytes);       // grows rb (after a stream sync) as needed
     CgState* cg_host = nullptr;
     double* scal_host = nullptr;
     explicit Lane(cudaStream_t s, bool create = false);
@@ -65,6 +69,9 @@ struct Ctx {
     std::string last_error;
     std::unique_ptr<Lane> lane0;          // resources on the context stream
     const Mlp* net = nullptr;             // learned initial guess (opt.use_learned)
+    std::unique_ptr<Mlp> own_net;         // a network trained by mpspt_train_preconditioner
+    std::unique_ptr<Autotuner> tuner;     // GEMM tile shapes (opt.autotune)
+    std::string tuner_path;               // opt.autotune_cache
     // harvesting of training pairs from plain solves (block features -> the
     // least-squares (gamma, delta) of the converged solution)
     bool harvesting = false;
@@ -105,6 +112,7 @@ struct SweepResult {
     double sigma64_flops = 0.0, sigma64_ms = 0.0;
     bool converged = false;              // last sweep met e_tol
     std::vector<long long> sigma_cum;    // sigma applications (all precisions) at each sweep end
+    double host_wait_ms = 0.0;           // host time blocked in stream synchronisations
     std::vector<double> disc_sweep;      // max discarded weight of each sweep
 };
 

@@ -5,7 +5,9 @@
 #include "kernels.h"
 
 #include <atomic>
+#include <algorithm>
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -14,7 +16,11 @@ namespace mpspt {
 namespace {
 
 std::atomic<long long> g_launches{0};
-inline void counted() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+thread_local long long t_launches = 0;   // this host thread's launches
+inline void counted() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
+}
 
 constexpr int TK = 16;
 constexpr int NT = 256;
@@ -48,16 +54,19 @@ __device__ __forceinline__ float conv<float>(double v) { return d2f_rn(v); }
 // Grouped GEMM: one CTA per output tile, looping over the tile's K-list.
 // 16x16 threads; thread (tx, ty) owns rows ty + 16 i (i < TM/16) and
 // cols tx + 16 j (j < TN/16).  T: storage type, U: arithmetic type.
+// Persistent: the grid is at most the resident CTAs of the GPU, and CTA b
+// takes tasks b, b + gridDim.x, ... (the planner orders tasks longest first).
 template <int TM, int TN, class T, class Task, class Op, class U = T>
-__global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks,
+__global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks, int ntask,
                                              const Op* __restrict__ ops,
                                              const int* __restrict__ skip) {
     if (skip && *skip) return;
     constexpr int RI = TM / 16, RJ = TN / 16;
-    const Task t = tasks[blockIdx.x];
     __shared__ U As[TK][TM + 1];
     __shared__ U Bs[TK][TN + 1];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int ti = blockIdx.x; ti < ntask; ti += gridDim.x) {
+    const Task t = tasks[ti];
     U acc[RI][RJ];
 #pragma unroll
     for (int i = 0; i < RI; ++i)
@@ -125,6 +134,7 @@ __global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks,
             *dst = t.accumulate ? *dst + (T)acc[i][j] : (T)acc[i][j];
         }
     }
+  }
 }
 
 // dst = sum coef * src over the task's source list (memory-bound).
@@ -525,29 +535,91 @@ inline int ew_grid(size_t n) {
 
 long long launch_count() { return g_launches.load(); }
 void count_launch() { counted(); }
+long long launch_count_thread() { return t_launches; }
+void uncount_launches(long long n) {
+    g_launches.fetch_sub(n);
+    t_launches -= n;
+}
 
 void ensure_smem_attr(const void* func, int bytes) {
     static std::mutex mu;
     static std::set<std::pair<const void*, int>> done;
+    thread_local std::set<std::pair<const void*, int>> seen;   // lock-free fast path per thread
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return;
+    if (seen.count({func, dev})) return;
     std::lock_guard<std::mutex> lk(mu);
-    if (done.count({func, dev})) return;
-    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+    if (!done.count({func, dev})) {
+        if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return;
         done.insert({func, dev});
+    }
+    seen.insert({func, dev});
+}
+
+namespace {
+// Resident CTAs of a kernel on the current device (occupancy x SMs), cached
+// per (kernel, device).
+int resident_ctas(const void* func, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    thread_local std::map<std::pair<const void*, int>, int> mine;   // lock-free fast path per thread
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto f = mine.find({func, dev});
+    if (f != mine.end()) return f->second;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({func, dev});
+    if (it != cache.end()) return mine[{func, dev}] = it->second;
+    int nb = 1, sms = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, smem) != cudaSuccess || nb < 1) nb = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    cudaGetLastError();
+    return mine[{func, dev}] = cache[{func, dev}] = nb * sms;
+}
+
+template <int TM, int TN, class U>
+void launch_tile(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st, const int* skip) {
+    auto* f = k_gemm<TM, TN, double, GemmTask, GemmOp, U>;
+    const int grid = std::min(ntask, resident_ctas(reinterpret_cast<const void*>(f), NT, 0));
+    counted();
+    f<<<grid, NT, 0, st>>>(tasks, ntask, ops, skip);
+}
+}  // namespace
+
+bool gemm_tile_supported(int tm, int tn) {
+    return (tm == 64 && tn == 64) || (tm == 32 && tn == 64) || (tm == 64 && tn == 32) || (tm == 16 && tn == 128) ||
+           (tm == 32 && tn == 32);
+}
+
+void launch_gemm_tile(int tm, int tn, bool f32, const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
+                      const int* skip) {
+    if (ntask <= 0) return;
+#define MPSPT_TILE(A, B)                                                          \
+    if (tm == A && tn == B) {                                                     \
+        if (f32) launch_tile<A, B, float>(tasks, ntask, ops, st, skip);           \
+        else launch_tile<A, B, double>(tasks, ntask, ops, st, skip);              \
+        return;                                                                   \
+    }
+    MPSPT_TILE(64, 64)
+    MPSPT_TILE(32, 64)
+    MPSPT_TILE(64, 32)
+    MPSPT_TILE(16, 128)
+    MPSPT_TILE(32, 32)
+#undef MPSPT_TILE
+    launch_tile<64, 64, double>(tasks, 0, ops, st, skip);   // unreachable for planned tiles
 }
 
 void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                            const int* skip) {
-    if (ntask > 0) { counted(); k_gemm<64, 64, double, GemmTask, GemmOp, float><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
+    launch_gemm_tile(64, 64, true, tasks, ntask, ops, st, skip);
 }
 void launch_gemm_f64_skinny(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                             const int* skip) {
-    if (ntask > 0) { counted(); k_gemm<16, 128, double, GemmTask, GemmOp><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
+    launch_gemm_tile(16, 128, false, tasks, ntask, ops, st, skip);
 }
 void launch_gemm_f64in_f32_skinny(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                                   const int* skip) {
-    if (ntask > 0) { counted(); k_gemm<16, 128, double, GemmTask, GemmOp, float><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
+    launch_gemm_tile(16, 128, true, tasks, ntask, ops, st, skip);
 }
 void launch_mix(const MixTask* tasks, int ntask, const MixSrc* srcs, cudaStream_t st, const int* skip) {
     if (ntask > 0) { counted(); k_mix<<<ntask, 128, 0, st>>>(tasks, srcs, skip); }
@@ -555,7 +627,7 @@ void launch_mix(const MixTask* tasks, int ntask, const MixSrc* srcs, cudaStream_
 
 void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                      const int* skip) {
-    if (ntask > 0) { counted(); k_gemm<64, 64, double, GemmTask, GemmOp><<<ntask, NT, 0, st>>>(tasks, ops, skip); }
+    launch_gemm_tile(64, 64, false, tasks, ntask, ops, st, skip);
 }
 void launch_diag(const DiagTask* tasks, int ntask, const DiagTerm* terms, cudaStream_t st) {
     if (ntask > 0) { counted(); k_diag<<<ntask, 256, 0, st>>>(tasks, terms); }

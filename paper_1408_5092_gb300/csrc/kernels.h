@@ -107,6 +107,8 @@ struct CgState {
 // Number of kernels launched by this library in this process.
 long long launch_count();
 void count_launch();
+long long launch_count_thread();      // launches made by the calling host thread
+void uncount_launches(long long n);   // launches that went into a captured graph (this thread's)
 // Raises a kernel's dynamic shared-memory limit to `bytes` on the current
 // device.  The attribute belongs to the device's context, so it is set once
 // per (kernel, device); thread-safe.  A failure is not remembered: the
@@ -126,6 +128,12 @@ void launch_gemm_f64in_f32(const GemmTask* tasks, int ntask, const GemmOp* ops, 
 
 void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                      const int* skip = nullptr);
+// Grouped GEMM with output tile tm x tn (64x64, 32x64, 64x32, 16x128, 32x32),
+// float64 or float32 arithmetic (f32) on float64 data.  Persistent: at most
+// the resident CTAs are launched and each walks a stride of the task list.
+bool gemm_tile_supported(int tm, int tn);
+void launch_gemm_tile(int tm, int tn, bool f32, const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
+                      const int* skip = nullptr);
 // Skinny-tile (16 x 128) float64 variant for panels with few rows.
 void launch_gemm_f64_skinny(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                             const int* skip = nullptr);

@@ -17,7 +17,11 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "kernels.h"
 
@@ -131,8 +135,12 @@ __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo
     }
 }
 
+// Persistent: at most the resident CTAs are launched; CTA b takes tasks b,
+// b + gridDim.x, ... with one TMEM allocation and one barrier pair for all of
+// them (the stage counter, and with it the mbarrier phases, runs on across
+// tasks).
 template <bool F16>
-__global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__ tasks,
+__global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__ tasks, int ntask,
                                                     const GemmOp* __restrict__ ops, int* err,
                                                     const int* __restrict__ skip) {
     if (skip && *skip) return;
@@ -142,10 +150,7 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
     __shared__ uint64_t bars[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int wait_ok;
-    const GemmTask t = tasks[blockIdx.x];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int mrem = min(BM, t.m - t.r0);
-    const int nrem = min(BN, t.n - t.c0);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -166,135 +171,164 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
 
     int stage = 0;
     bool ok = true;
-    for (int o = t.op0; o < t.op1 && ok; ++o) {
-        const GemmOp op = ops[o];
-        const bool ta = op.trans & 1, tb = op.trans & 2;
-        const float alpha = d2f_rn(op.alpha);
-        for (int k0 = 0; k0 < op.k; k0 += BK) {
-            const int buf = stage & 1;
-            if (stage >= 2) {   // stage buffer free once the MMAs of stage-2 completed
-                if (tid == 0) wait_ok = mbar_wait(&bars[buf], ((stage - 2) >> 1) & 1) ? 1 : 0;
+    for (int ti = blockIdx.x; ti < ntask && ok; ti += gridDim.x) {
+        const GemmTask t = tasks[ti];
+        const int mrem = min(BM, t.m - t.r0);
+        const int nrem = min(BN, t.n - t.c0);
+        const int stage0 = stage;
+        for (int o = t.op0; o < t.op1 && ok; ++o) {
+            const GemmOp op = ops[o];
+            const bool ta = op.trans & 1, tb = op.trans & 2;
+            const float alpha = d2f_rn(op.alpha);
+            for (int k0 = 0; k0 < op.k; k0 += BK) {
+                const int buf = stage & 1;
+                if (stage >= 2) {   // stage buffer free once the MMAs of stage-2 completed
+                    if (tid == 0) wait_ok = mbar_wait(&bars[buf], ((stage - 2) >> 1) & 1) ? 1 : 0;
+                    __syncthreads();
+                    if (!wait_ok) { ok = false; break; }
+                }
+                unsigned char* Ahi = smem + buf * STAGE_BYTES;
+                unsigned char* Alo = Ahi + A_BYTES;
+                unsigned char* Bhi = Alo + A_BYTES;
+                unsigned char* Blo = Bhi + B_BYTES;
+                const int krem = min(BK, op.k - k0);
+                // A: BM x BK values, B: BN x BK values; LCH loads per thread are
+                // issued before any of them is split and stored
+                for (int e0 = 0; e0 < BM * BK; e0 += NTH * LCH) {
+                    double v[LCH];
+                    int off[LCH];
+#pragma unroll
+                    for (int q = 0; q < LCH; ++q) {
+                        const int e = e0 + q * NTH + tid;
+                        int r, kk;
+                        if (ta) { r = e % BM; kk = e / BM; } else { kk = e % BK; r = e / BK; }
+                        off[q] = (int)tile_off(r, kk);
+                        v[q] = 0.0;
+                        if (r < mrem && kk < krem) {
+                            const int row = t.r0 + r, kg = k0 + kk;
+                            v[q] = ta ? op.A[(size_t)kg * op.lda + row] : op.A[(size_t)row * op.lda + kg];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < LCH; ++q)
+                        split_store<F16>(Ahi, Alo, (uint32_t)off[q], alpha * d2f_rn(v[q]));
+                }
+                for (int e0 = 0; e0 < BN * BK; e0 += NTH * LCH) {
+                    double v[LCH];
+                    int off[LCH];
+#pragma unroll
+                    for (int q = 0; q < LCH; ++q) {
+                        const int e = e0 + q * NTH + tid;
+                        int j, kk;
+                        if (tb) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
+                        off[q] = (int)tile_off(j, kk);
+                        v[q] = 0.0;
+                        if (j < nrem && kk < krem) {
+                            const int col = t.c0 + j, kg = k0 + kk;
+                            v[q] = tb ? op.B[(size_t)col * op.ldb + kg] : op.B[(size_t)kg * op.ldb + col];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < LCH; ++q) split_store<F16>(Bhi, Blo, (uint32_t)off[q], d2f_rn(v[q]));
+                }
+                asm volatile("fence.proxy.async.shared::cta;");
                 __syncthreads();
-                if (!wait_ok) { ok = false; break; }
-            }
-            unsigned char* Ahi = smem + buf * STAGE_BYTES;
-            unsigned char* Alo = Ahi + A_BYTES;
-            unsigned char* Bhi = Alo + A_BYTES;
-            unsigned char* Blo = Bhi + B_BYTES;
-            const int krem = min(BK, op.k - k0);
-            // A: BM x BK values, B: BN x BK values; LCH loads per thread are
-            // issued before any of them is split and stored
-            for (int e0 = 0; e0 < BM * BK; e0 += NTH * LCH) {
-                double v[LCH];
-                int off[LCH];
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
+                    const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
 #pragma unroll
-                for (int q = 0; q < LCH; ++q) {
-                    const int e = e0 + q * NTH + tid;
-                    int r, kk;
-                    if (ta) { r = e % BM; kk = e / BM; } else { kk = e % BK; r = e / BK; }
-                    off[q] = (int)tile_off(r, kk);
-                    v[q] = 0.0;
-                    if (r < mrem && kk < krem) {
-                        const int row = t.r0 + r, kg = k0 + kk;
-                        v[q] = ta ? op.A[(size_t)kg * op.lda + row] : op.A[(size_t)row * op.lda + kg];
+                    for (int j = 0; j < BK / 16; ++j) {
+                        const uint32_t kofs = j * 256;   // two 128-byte core matrices per 16 K
+                        mma_bf16(tmem, make_desc(ahi + kofs), make_desc(bhi + kofs), idesc,
+                                 (stage > stage0 || j > 0) ? 1u : 0u);
+                        mma_bf16(tmem, make_desc(ahi + kofs), make_desc(blo + kofs), idesc, 1u);
+                        mma_bf16(tmem, make_desc(alo + kofs), make_desc(bhi + kofs), idesc, 1u);
                     }
+                    mma_commit(&bars[buf]);
                 }
-#pragma unroll
-                for (int q = 0; q < LCH; ++q) split_store<F16>(Ahi, Alo, (uint32_t)off[q], alpha * d2f_rn(v[q]));
+                ++stage;
             }
-            for (int e0 = 0; e0 < BN * BK; e0 += NTH * LCH) {
-                double v[LCH];
-                int off[LCH];
-#pragma unroll
-                for (int q = 0; q < LCH; ++q) {
-                    const int e = e0 + q * NTH + tid;
-                    int j, kk;
-                    if (tb) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
-                    off[q] = (int)tile_off(j, kk);
-                    v[q] = 0.0;
-                    if (j < nrem && kk < krem) {
-                        const int col = t.c0 + j, kg = k0 + kk;
-                        v[q] = tb ? op.B[(size_t)col * op.ldb + kg] : op.B[(size_t)kg * op.ldb + col];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < LCH; ++q) split_store<F16>(Bhi, Blo, (uint32_t)off[q], d2f_rn(v[q]));
-            }
-            asm volatile("fence.proxy.async.shared::cta;");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
-                const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
-#pragma unroll
-                for (int j = 0; j < BK / 16; ++j) {
-                    const uint32_t kofs = j * 256;   // two 128-byte core matrices per 16 K
-                    mma_bf16(tmem, make_desc(ahi + kofs), make_desc(bhi + kofs), idesc, (stage > 0 || j > 0) ? 1u : 0u);
-                    mma_bf16(tmem, make_desc(ahi + kofs), make_desc(blo + kofs), idesc, 1u);
-                    mma_bf16(tmem, make_desc(alo + kofs), make_desc(bhi + kofs), idesc, 1u);
-                }
-                mma_commit(&bars[buf]);
-            }
-            ++stage;
         }
-    }
-    const bool any = stage > 0;
-    if (any && ok) {
-        if (tid == 0) wait_ok = mbar_wait(&bars[(stage - 1) & 1], ((stage - 1) >> 1) & 1) ? 1 : 0;
-        __syncthreads();
-        ok = wait_ok != 0;
-    }
-    if (!ok) {
-        if (tid == 0) {
-            atomicExch(err, 1);
-            // give in-flight MMAs a bounded chance to drain before releasing TMEM
-            if (any) mbar_wait(&bars[(stage - 1) & 1], ((stage - 1) >> 1) & 1);
-        }
-        __syncthreads();
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. +31 (accumulator
-    // rows), columns 32 (w / 4) .. +31
-    const int row = (warp & 3) * 32 + lane;
-#pragma unroll 1
-    for (int c0 = (warp >> 2) * 32; c0 < (warp >> 2) * 32 + 32; c0 += 16) {
-        uint32_t v[16];
+        const bool any = stage > stage0;
         if (any && ok) {
-            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                  "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-        } else {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = 0u;
+            if (tid == 0) wait_ok = mbar_wait(&bars[(stage - 1) & 1], ((stage - 1) >> 1) & 1) ? 1 : 0;
+            __syncthreads();
+            ok = wait_ok != 0;
         }
-        if (row < mrem && ok) {
+        if (!ok) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                // give in-flight MMAs a bounded chance to drain before releasing TMEM
+                if (stage > 0) mbar_wait(&bars[(stage - 1) & 1], ((stage - 1) >> 1) & 1);
+            }
+            __syncthreads();
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. +31 (accumulator
+        // rows), columns 32 (w / 4) .. +31
+        const int row = (warp & 3) * 32 + lane;
+#pragma unroll 1
+        for (int c0 = (warp >> 2) * 32; c0 < (warp >> 2) * 32 + 32; c0 += 16) {
+            uint32_t v[16];
+            if (any && ok) {
+                const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+            } else {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int col = c0 + q;
-                if (col < nrem) {
-                    const int gr = t.r0 + row, gc = t.c0 + col;
-                    double* dst;
-                    if (t.cmap == nullptr) dst = t.C + (size_t)gr * t.ldc + gc;
-                    else if (t.cmap_rows) dst = t.C + t.cmap[2 * gr] + (size_t)gc * t.cmap[2 * gr + 1];
-                    else dst = t.C + t.cmap[2 * gc] + (size_t)gr * t.cmap[2 * gc + 1];
-                    const double val = (double)__uint_as_float(v[q]);
-                    *dst = t.accumulate ? *dst + val : val;
+                for (int q = 0; q < 16; ++q) v[q] = 0u;
+            }
+            if (row < mrem && ok) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int col = c0 + q;
+                    if (col < nrem) {
+                        const int gr = t.r0 + row, gc = t.c0 + col;
+                        double* dst;
+                        if (t.cmap == nullptr) dst = t.C + (size_t)gr * t.ldc + gc;
+                        else if (t.cmap_rows) dst = t.C + t.cmap[2 * gr] + (size_t)gc * t.cmap[2 * gr + 1];
+                        else dst = t.C + t.cmap[2 * gc] + (size_t)gr * t.cmap[2 * gc + 1];
+                        const double val = (double)__uint_as_float(v[q]);
+                        *dst = t.accumulate ? *dst + val : val;
+                    }
                 }
             }
         }
+        // the next task's first MMA overwrites the accumulator: every warp's
+        // tcgen05.ld above completes before it (wait::ld, then this barrier)
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 }  // namespace
+
+// Resident CTAs of the kernel on the current device, per (kernel, device).
+int tc_resident_ctas(const void* f) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    thread_local std::map<std::pair<const void*, int>, int> mine;   // lock-free fast path per thread
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto g = mine.find({f, dev});
+    if (g != mine.end()) return g->second;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({f, dev});
+    if (it != cache.end()) return mine[{f, dev}] = it->second;
+    int nb = 1, sms = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, NTH, SMEM_BYTES) != cudaSuccess || nb < 1) nb = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    cudaGetLastError();
+    return mine[{f, dev}] = cache[{f, dev}] = nb * sms;
+}
 
 int tc_tile_m() { return BM; }
 int tc_tile_n() { return BN; }
@@ -303,13 +337,11 @@ void launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmOp* ops, int* er
                     const int* skip, bool f16) {
     if (ntask <= 0) return;
     count_launch();
-    if (f16) {
-        ensure_smem_attr(reinterpret_cast<const void*>(k_gemm_tc<true>), SMEM_BYTES);
-        k_gemm_tc<true><<<ntask, NTH, SMEM_BYTES, st>>>(tasks, ops, err, skip);
-    } else {
-        ensure_smem_attr(reinterpret_cast<const void*>(k_gemm_tc<false>), SMEM_BYTES);
-        k_gemm_tc<false><<<ntask, NTH, SMEM_BYTES, st>>>(tasks, ops, err, skip);
-    }
+    const void* f = f16 ? reinterpret_cast<const void*>(k_gemm_tc<true>) : reinterpret_cast<const void*>(k_gemm_tc<false>);
+    ensure_smem_attr(f, SMEM_BYTES);
+    const int grid = std::min(ntask, tc_resident_ctas(f));
+    if (f16) k_gemm_tc<true><<<grid, NTH, SMEM_BYTES, st>>>(tasks, ntask, ops, err, skip);
+    else k_gemm_tc<false><<<grid, NTH, SMEM_BYTES, st>>>(tasks, ntask, ops, err, skip);
 }
 
 }  // namespace mpspt

@@ -2,6 +2,7 @@
 #include "plans.h"
 
 #include <algorithm>
+#include <cstdio>
 #include <map>
 #include <tuple>
 
@@ -12,46 +13,184 @@ void GemmPlan::block(double* C, int ldc, int m, int n, int accumulate, int op0, 
     if (m <= 0 || n <= 0) return;
     const int op1 = (int)ops.size();
     for (int o = op0; o < op1; ++o) flops += 2.0 * m * n * ops[o].k;
-    for (int r0 = 0; r0 < m; r0 += tm)
-        for (int c0 = 0; c0 < n; c0 += tn) {
-            tasks.push_back({C, nullptr, ldc, m, n, r0, c0, op0, op1, accumulate, cmap_rows});
-            task_cmap.push_back(cmap_off);
-        }
+    blocks.push_back({C, cmap_off, ldc, m, n, accumulate, op0, op1, cmap_rows});
 }
 
+void GemmPlan::split(int tm_, int tn_, std::vector<GemmTask>& out, std::vector<long long>* cm) const {
+    out.clear();
+    if (cm) cm->clear();
+    for (const Blk& b : blocks)
+        for (int r0 = 0; r0 < b.m; r0 += tm_)
+            for (int c0 = 0; c0 < b.n; c0 += tn_) {
+                out.push_back({b.C, nullptr, b.ldc, b.m, b.n, r0, c0, b.op0, b.op1, b.accumulate, b.cmap_rows});
+                if (cm) cm->push_back(b.cmap_off);
+            }
+}
+
+namespace {
+// longest K-list first: the persistent kernels hand out tasks in strides of
+// the grid, so this order balances the CTAs (each output tile has exactly
+// one task, so the order does not change any result)
+void order_tasks(std::vector<GemmTask>& tasks, std::vector<long long>* cm, const std::vector<GemmOp>& ops) {
+    std::vector<long long> cost(tasks.size());
+    for (size_t i = 0; i < tasks.size(); ++i) {
+        long long k = 0;
+        for (int o = tasks[i].op0; o < tasks[i].op1; ++o) k += ops[o].k;
+        cost[i] = k;
+    }
+    std::vector<size_t> ord(tasks.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<GemmTask> t2(tasks.size());
+    std::vector<long long> c2(cm ? tasks.size() : 0);
+    for (size_t i = 0; i < ord.size(); ++i) {
+        t2[i] = tasks[ord[i]];
+        if (cm) c2[i] = (*cm)[ord[i]];
+    }
+    tasks.swap(t2);
+    if (cm) cm->swap(c2);
+}
+
+int bucket(long long x) {
+    int b = 0;
+    while (x > 1) { x >>= 1; ++b; }
+    return b;
+}
+}  // namespace
+
 void GemmPlan::upload(cudaStream_t st) {
+    mpspt::upload(dops, ops, st);
+    if (tuner && !is_tc(kind) && !blocks.empty()) {
+        const std::pair<int, int> t = tuner->choose(*this, st);
+        tm = t.first;
+        tn = t.second;
+    }
+    split(tm, tn, tasks, &task_cmap);
+    order_tasks(tasks, &task_cmap, ops);
     if (!cmaps.empty()) mpspt::upload(dcmaps, cmaps, st);
     const int* cbase = dcmaps.as<int>();
     for (size_t i = 0; i < tasks.size(); ++i)
         tasks[i].cmap = task_cmap[i] >= 0 ? cbase + task_cmap[i] : nullptr;
     if (checks_enabled()) {
-        for (size_t i = 0; i < tasks.size(); ++i) {
-            const auto& t = tasks[i];
-            if (t.cmap == nullptr) {
-                check_range(t.C, ((size_t)(t.m - 1) * t.ldc + t.n) * sizeof(double), "gemm C");
-                if (t.ldc < t.n) throw Error(MPSPT_ERR_INVALID, "gemm ldc");
+        // per planned block (all tiles of a block share its output and its
+        // K-list): the output range, or the span of its mapped addresses,
+        // and every operand range of its K-list
+        for (const Blk& b : blocks) {
+            if (b.cmap_off < 0) {
+                check_range(b.C, ((size_t)(b.m - 1) * b.ldc + b.n) * sizeof(double), "gemm C");
+                if (b.ldc < b.n) throw Error(MPSPT_ERR_INVALID, "gemm ldc");
             } else {
-                const long long o = task_cmap[i];
-                const int nmap = t.cmap_rows ? t.m : t.n, other = t.cmap_rows ? t.n : t.m;
+                const long long o = b.cmap_off;
+                const int nmap = b.cmap_rows ? b.m : b.n, other = b.cmap_rows ? b.n : b.m;
                 require((size_t)(o + 2 * (long long)nmap) <= cmaps.size(), "gemm cmap range");
+                long long lo = 0, hi = 0;
                 for (int q = 0; q < nmap; ++q) {
-                    const int base = cmaps[o + 2 * q], ld = cmaps[o + 2 * q + 1];
-                    check_range(t.C + base, ((size_t)(other - 1) * ld + 1) * sizeof(double), "gemm cmap dst");
+                    const long long base = cmaps[o + 2 * q], ld = cmaps[o + 2 * q + 1];
+                    require(base >= 0 && ld >= 0, "gemm cmap entry");
+                    const long long last = base + (long long)(other - 1) * ld;
+                    lo = q ? std::min(lo, base) : base;
+                    hi = q ? std::max(hi, last) : last;
                 }
+                check_range(b.C + lo, (size_t)(hi - lo + 1) * sizeof(double), "gemm cmap dst");
             }
-            for (int q = t.op0; q < t.op1; ++q) {
+            for (int q = b.op0; q < b.op1; ++q) {
                 const GemmOp& op = ops[q];
-                const size_t ea = (op.trans & 1) ? (size_t)(op.k - 1) * op.lda + t.m : (size_t)(t.m - 1) * op.lda + op.k;
-                const size_t eb = (op.trans & 2) ? (size_t)(t.n - 1) * op.ldb + op.k : (size_t)(op.k - 1) * op.ldb + t.n;
+                const size_t ea = (op.trans & 1) ? (size_t)(op.k - 1) * op.lda + b.m : (size_t)(b.m - 1) * op.lda + op.k;
+                const size_t eb = (op.trans & 2) ? (size_t)(b.n - 1) * op.ldb + op.k : (size_t)(op.k - 1) * op.ldb + b.n;
                 check_range(op.A, ea * sizeof(double), "gemm A");
                 check_range(op.B, eb * sizeof(double), "gemm B");
-                if ((op.trans & 1) ? op.lda < t.m : op.lda < op.k) throw Error(MPSPT_ERR_INVALID, "gemm lda");
-                if ((op.trans & 2) ? op.ldb < op.k : op.ldb < t.n) throw Error(MPSPT_ERR_INVALID, "gemm ldb");
+                if ((op.trans & 1) ? op.lda < b.m : op.lda < op.k) throw Error(MPSPT_ERR_INVALID, "gemm lda");
+                if ((op.trans & 2) ? op.ldb < op.k : op.ldb < b.n) throw Error(MPSPT_ERR_INVALID, "gemm ldb");
             }
         }
     }
     mpspt::upload(dtasks, tasks, st);
-    mpspt::upload(dops, ops, st);
+}
+
+Autotuner::~Autotuner() {
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+}
+
+std::pair<int, int> Autotuner::choose(const GemmPlan& g, cudaStream_t st) {
+    std::vector<long long> ms, ns, ks;
+    size_t cmax = 1;
+    for (const auto& b : g.blocks) {
+        long long k = 0;
+        for (int o = b.op0; o < b.op1; ++o) k += g.ops[o].k;
+        ms.push_back(b.m);
+        ns.push_back(b.n);
+        ks.push_back(k);
+        cmax = std::max(cmax, (size_t)b.m * b.n);
+    }
+    auto med = [](std::vector<long long>& v) {
+        std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+        return v[v.size() / 2];
+    };
+    const Key key{g.kind, g.skinny ? 1 : 0, bucket(med(ms)), bucket(med(ns)), bucket(med(ks)),
+                  bucket((long long)g.blocks.size())};
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = best.find(key);
+    if (it != best.end()) { ++reused; return it->second; }
+    static const int cand_wide[][2] = {{64, 64}, {32, 64}, {64, 32}, {32, 32}};
+    static const int cand_skinny[][2] = {{16, 128}, {32, 64}, {32, 32}};
+    const int (*cand)[2] = g.skinny ? cand_skinny : cand_wide;
+    const int nc = g.skinny ? 3 : 4;
+    if (!ev[0]) {
+        MPSPT_CUDA(cudaEventCreate(&ev[0]));
+        MPSPT_CUDA(cudaEventCreate(&ev[1]));
+    }
+    scratch.ensure(cmax * sizeof(double) + 16, st);
+    std::pair<int, int> win{cand[0][0], cand[0][1]};
+    float tbest = 1e30f;
+    std::vector<GemmTask> tt;
+    for (int c = 0; c < nc; ++c) {
+        g.split(cand[c][0], cand[c][1], tt, nullptr);
+        order_tasks(tt, nullptr, g.ops);
+        for (auto& t : tt) {   // outputs go to scratch: dense m x n, no map; operands are the plan's
+            t.C = scratch.as<double>();
+            t.ldc = t.n;
+            t.cmap = nullptr;
+            t.cmap_rows = 0;
+        }
+        mpspt::upload(dtasks, tt, st);
+        const bool f32 = g.kind == GEMM_F32;
+        launch_gemm_tile(cand[c][0], cand[c][1], f32, dtasks.as<GemmTask>(), (int)tt.size(), g.dops.as<GemmOp>(), st);
+        MPSPT_CUDA(cudaEventRecord(ev[0], st));
+        for (int r = 0; r < 3; ++r)
+            launch_gemm_tile(cand[c][0], cand[c][1], f32, dtasks.as<GemmTask>(), (int)tt.size(), g.dops.as<GemmOp>(),
+                             st);
+        MPSPT_CUDA(cudaEventRecord(ev[1], st));
+        MPSPT_CUDA(cudaEventSynchronize(ev[1]));
+        float ms_ = 0.f;
+        MPSPT_CUDA(cudaEventElapsedTime(&ms_, ev[0], ev[1]));
+        if (ms_ < tbest) { tbest = ms_; win = {cand[c][0], cand[c][1]}; }
+    }
+    ++timed;
+    best[key] = win;
+    return win;
+}
+
+void Autotuner::load(const std::string& path) {
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return;
+    int a[8];
+    std::lock_guard<std::mutex> lk(mu);
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6], &a[7]) == 8)
+        if (gemm_tile_supported(a[6], a[7])) best[Key{a[0], a[1], a[2], a[3], a[4], a[5]}] = {a[6], a[7]};
+    std::fclose(f);
+}
+
+void Autotuner::save(const std::string& path) {
+    FILE* f = std::fopen(path.c_str(), "w");
+    if (!f) return;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto& kv : best) {
+        const Key& k = kv.first;
+        std::fprintf(f, "%d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+                     std::get<4>(k), std::get<5>(k), kv.second.first, kv.second.second);
+    }
+    std::fclose(f);
 }
 
 void GemmPlan::run(cudaStream_t st) const {
@@ -60,8 +199,7 @@ void GemmPlan::run(cudaStream_t st) const {
     const GemmTask* t = dtasks.as<GemmTask>();
     const GemmOp* o = dops.as<GemmOp>();
     if (is_tc(kind)) launch_gemm_tc(t, nt, o, err, st, skip, kind == GEMM_TC16);
-    else if (kind == GEMM_F32) (skinny ? launch_gemm_f64in_f32_skinny : launch_gemm_f64in_f32)(t, nt, o, st, skip);
-    else (skinny ? launch_gemm_f64_skinny : launch_gemm_f64)(t, nt, o, st, skip);
+    else launch_gemm_tile(tm, tn, kind == GEMM_F32, t, nt, o, st, skip);
 }
 
 void Omega::build(const MPO& W, int i) {

@@ -1,5 +1,9 @@
 // Planner: turns each contraction of the sweep into device task lists.
 #pragma once
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "kernels.h"
@@ -11,8 +15,31 @@ namespace mpspt {
 enum GemmKind { GEMM_F64 = 0, GEMM_F32 = 1, GEMM_TC = 2, GEMM_TC16 = 3 };
 inline bool is_tc(int kind) { return kind == GEMM_TC || kind == GEMM_TC16; }
 
+struct GemmPlan;
+
+// Tile-shape autotuner of the CUDA-core grouped GEMM.  A plan's shape class
+// is (arithmetic, skinny, and log2 buckets of the median block rows, columns
+// and K-length and of the block count).  The first plan of a class times
+// every candidate tile on its own operands (outputs redirected to scratch,
+// so no result changes), keeps the fastest, and later plans of the class
+// reuse it.  The table can be read from and written to a text file.
+struct Autotuner {
+    using Key = std::tuple<int, int, int, int, int, int>;
+    std::mutex mu;
+    std::map<Key, std::pair<int, int>> best;
+    long long timed = 0, reused = 0;
+    DBuf scratch, dtasks;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    ~Autotuner();
+    // (tm, tn) for the plan (its blocks recorded, its ops uploaded)
+    std::pair<int, int> choose(const GemmPlan& g, cudaStream_t st);
+    void load(const std::string& path);
+    void save(const std::string& path);
+};
+
 struct GemmPlan {
     int tm = GEMM_TM, tn = GEMM_TN;   // output tile (TC kernel: 128 x 64; skinny: 16 x 128)
+    Autotuner* tuner = nullptr;       // CUDA-core kinds only: choose the tile per shape class
     int kind = GEMM_F64;
     bool skinny = false;
     int* err = nullptr;               // TC kernel error flag (device)
@@ -25,13 +52,22 @@ struct GemmPlan {
         else if (skinny) { tm = 16; tn = 128; }
         else { tm = GEMM_TM; tn = GEMM_TN; }
     }
+    // output blocks as planned; split into tm x tn tasks at upload
+    struct Blk {
+        double* C;
+        long long cmap_off;
+        int ldc, m, n, accumulate, op0, op1, cmap_rows;
+    };
+    std::vector<Blk> blocks;
     std::vector<GemmTask> tasks;
     std::vector<GemmOp> ops;
     std::vector<int> cmaps;           // host copy of all column / row maps
     std::vector<long long> task_cmap; // per task: offset into cmaps or -1
     double flops = 0.0;   // algorithmic: sum over ops of 2 m n k (each product once)
     DBuf dtasks, dops, dcmaps;
-    void clear() { tasks.clear(); ops.clear(); cmaps.clear(); task_cmap.clear(); flops = 0.0; }
+    void clear() { blocks.clear(); tasks.clear(); ops.clear(); cmaps.clear(); task_cmap.clear(); flops = 0.0; }
+    // tasks of the recorded blocks for a tile shape (no cmap pointers yet)
+    void split(int tm_, int tn_, std::vector<GemmTask>& out, std::vector<long long>* cm) const;
     int mark() const { return (int)ops.size(); }
     void op(const double* A, int lda, const double* B, int ldb, int k, int trans, double alpha) {
         if (k <= 0) return;
@@ -85,6 +121,7 @@ struct TwoSitePlan {
         g2s.set_kind(k, e, true);
     }
     void set_skip(const int* s) { skip = s; g1.skip = s; g2.skip = s; g2s.skip = s; }
+    void set_tuner(Autotuner* t) { g1.tuner = t; g2.tuner = t; g2s.tuner = t; }
     void build(const Omega& om, const TwoT& bra, const TwoT& ket, const Bond& braL,
                const Bond& ketL, const Bond& braR, const Bond& ketR, const EnvT& L,
                const EnvT& R, const std::vector<QN>& dqR, const double* x, double* out,
@@ -121,6 +158,7 @@ void plan_product(GemmPlan& g, const TwoT& x, double* xd, const Bond& mid, const
 //   g2:  L_new(out) = sum_s A_bra(s)^T Z_(out, s)          (<= 4 products)
 struct EnvPlan {
     GemmPlan g1, g2;
+    void set_tuner(Autotuner* t) { g1.tuner = t; g2.tuner = t; }
     DBuf Y, Z, dmt, dms;
     std::vector<MixTask> mt;
     std::vector<MixSrc> ms;

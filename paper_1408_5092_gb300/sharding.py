@@ -202,7 +202,8 @@ def minimize_partitioned_elastic(ctx, h0, pairs, Ms, store, rank, n_streams=0, s
     who solves them, and the total is summed in partition order, so every
     surviving rank returns the same values.
     deadline: optional limit in seconds on the whole call (TimeoutError).
-    Returns (E2_total, per-partition E2, indices this rank solved)."""
+    Returns (E2_total, per-partition E2, indices this rank solved, indices
+    it took over from a rank whose heartbeat had stopped)."""
     pairs = np.asarray(pairs, dtype=np.int32).reshape(-1, 2)
     Ms = np.asarray(Ms, dtype=np.int32).reshape(-1)
     if len(pairs) != len(Ms):
@@ -217,6 +218,7 @@ def minimize_partitioned_elastic(ctx, h0, pairs, Ms, store, rank, n_streams=0, s
     ekey = lambda i: f"{prefix}/e/{i}"          # noqa: E731
     ckey = lambda i: f"{prefix}/claim/{i}"      # noqa: E731
     solved = []
+    taken = []
 
     def have(i):
         with lock:
@@ -270,6 +272,7 @@ def minimize_partitioned_elastic(ctx, h0, pairs, Ms, store, rank, n_streams=0, s
                     with lock:
                         if store.compare_set(ckey(i), owner, me).decode() == me:
                             take.append(i)
+            taken.extend(take)
             for c0 in range(0, len(take), batch):
                 solve_and_store(take[c0:c0 + batch])
             if not take:
@@ -283,4 +286,4 @@ def minimize_partitioned_elastic(ctx, h0, pairs, Ms, store, rank, n_streams=0, s
     total = 0.0
     for v in ep:
         total += float(v)
-    return total, ep, sorted(solved)
+    return total, ep, sorted(solved), sorted(taken)

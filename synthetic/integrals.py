@@ -22,8 +22,9 @@ EVAL_SEED = 1408
 TRAIN_SEED = 5092
 
 
-def integrals(seed, k_act, k_virt, n_chol):
-    """Return (h, L) for a seeded synthetic Hamiltonian (float64)."""
+def integrals(seed, k_act, k_virt, n_chol, l_scale=1.0):
+    """Return (h, L) for a seeded synthetic Hamiltonian (float64); the
+    Cholesky entries are drawn with standard deviation 0.05 * l_scale."""
     rng = np.random.Generator(np.random.PCG64(seed))
     k = k_act + k_virt
     eps_act = np.sort(rng.uniform(-0.5, 0.5, size=k_act))
@@ -36,14 +37,14 @@ def integrals(seed, k_act, k_virt, n_chol):
     L = np.zeros((n_chol, k, k))
     for Q in range(n_chol):
         M = np.zeros((k, k))
-        M[iu] = rng.normal(0.0, 0.05, size=iu[0].size)
+        M[iu] = rng.normal(0.0, 0.05 * l_scale, size=iu[0].size)
         L[Q] = M + np.triu(M, 1).T
     return np.ascontiguousarray(h), np.ascontiguousarray(L)
 
 
 def config_integrals(name, seed=EVAL_SEED):
     c = CONFIGS[name]
-    h, L = integrals(seed, c["k_act"], c["k_virt"], c["n_chol"])
+    h, L = integrals(seed, c["k_act"], c["k_virt"], c["n_chol"], c.get("l_scale", 1.0))
     return h, L, c
 
 

@@ -44,6 +44,21 @@ def tiny():
     return out
 
 
+def tiny_extrapolation(Ms=(20, 26, 32, 36)):
+    """E2(M), discarded weights and the extrapolated E2 (oracle/extrapolate.py)
+    on the tiny system, both H0."""
+    from oracle.extrapolate import extrapolate_e2
+    h, L, c = synthetic.config_integrals("tiny")
+    ci, _ = synthetic.fci_reference(h, L, c["k_act"], c["n_elec"])
+    out = {"config": "tiny", "Ms": list(Ms), "h0": {}}
+    for h0 in ("fock", "dyall"):
+        p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
+        a, b, e2, w = extrapolate_e2(p, Ms)
+        out["h0"][h0] = {"E2_extrap": a, "slope": b, "E2": e2, "w": w}
+        print(h0, a, b, flush=True)
+    return out
+
+
 def medium_partitions(M, h0, pairs):
     """Per-partition E2 of a few virtual-pair partitions of the medium system."""
     from oracle.partition import SubProblem
@@ -107,6 +122,9 @@ if __name__ == "__main__":
     if what == "tiny":
         res = tiny()
         name = "oracle_tiny.json"
+    elif what == "tiny_extrapolation":
+        res = tiny_extrapolation()
+        name = "oracle_tiny_extrapolation.json"
     elif what == "medium_partitions":
         res = medium_partitions(16, "fock", [(0, 0), (3, 17), (23, 23)])
         name = "oracle_medium_partitions_fock_M16.json"

@@ -86,3 +86,27 @@ def test_trained_network_in_the_sweep():
         with open(out, "w") as f:
             json.dump(rec, f, indent=1)
     print("learned preconditioner:", rec)
+
+
+def test_train_preconditioner_end_to_end(tmp_path):
+    """mpspt_train_preconditioner: harvest on the context's problem, train on
+    the GPU, attach; the harvest file is written, and a second context trains
+    from the file instead of sweeping.  With the network attached the sweep
+    reaches the plain sweep's E2."""
+    from paper_1408_5092_gb300 import _lib as L
+    path = str(tmp_path / "pairs.bin")
+    ctx = _ctx(L, synthetic.TRAIN_SEED, use_learned=1)
+    loss = L.mpspt_train_preconditioner(ctx, "dyall", 16, max_samples=4000, epochs=5, harvest_path=path)
+    assert np.isfinite(loss) and os.path.getsize(path) > 4
+    n = int(np.fromfile(path, dtype=np.int32, count=1)[0])
+    assert 0 < n <= 4000 and os.path.getsize(path) == 4 + 4 * n * 18
+    L.mpspt_destroy(ctx)
+    ctx = _ctx(L, 1408, use_learned=1)
+    L.mpspt_train_preconditioner(ctx, "dyall", 16, max_samples=4000, epochs=5, harvest_path=path)
+    e_learn, _, r = L.mpspt_minimize_hylleraas(ctx, "dyall", 16, want_psi1=False)
+    L.mpspt_destroy(ctx)
+    ctx = _ctx(L, 1408)
+    e_plain, _, _ = L.mpspt_minimize_hylleraas(ctx, "dyall", 16, want_psi1=False)
+    L.mpspt_destroy(ctx)
+    assert abs(e_learn - e_plain) < 1e-8
+    assert r.learned_used + r.learned_rejected > 0

@@ -284,3 +284,19 @@ def test_iteration_caps_are_reported(L, tiny):
     _, _, rep = L.mpspt_minimize_hylleraas(ctx, "fock", 16, want_psi1=False)
     assert rep.converged == 1
     L.mpspt_destroy(ctx)
+
+
+@pytest.mark.parametrize("h0", ["fock", "dyall"])
+def test_extrapolation_matches_oracle(L, tiny, h0):
+    """E2(M), the last sweep's discarded weight and the least-squares
+    intercept in the discarded weight (the paper's extrapolation) against the
+    oracle's (tests/golden/oracle_tiny_extrapolation.json)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_tiny_extrapolation.json")
+    g = json.load(open(path))
+    ref = g["h0"][h0]
+    ctx = _session(L, tiny)
+    a, b, e2, w = L.mpspt_extrapolate_e2(ctx, h0, g["Ms"])
+    assert np.abs(e2 - np.array(ref["E2"])).max() < 1e-8, (e2, ref["E2"])
+    assert np.abs(w - np.array(ref["w"])).max() < 1e-8 * max(1.0, max(ref["w"])), (w, ref["w"])
+    assert abs(a - ref["E2_extrap"]) < 1e-7 and abs(b - ref["slope"]) < 1e-4 * abs(ref["slope"])
+    L.mpspt_destroy(ctx)

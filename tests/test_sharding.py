@@ -192,10 +192,12 @@ def _elastic_worker(rank, port, out_dir, die_on_call):
             os._exit(3)                      # the process disappears with its claims unfinished
         _t.sleep(0.05 * len(p))
         return exact(p, m)
-    tot, ep, mine = minimize_partitioned_elastic(None, "fock", pairs, Ms, store, rank, solve=solve, batch=2,
-                                                 timeout=3.0, heartbeat=0.2, poll=0.05, deadline=120.0)
+    tot, ep, mine, taken = minimize_partitioned_elastic(None, "fock", pairs, Ms, store, rank, solve=solve,
+                                                        batch=2, timeout=3.0, heartbeat=0.2, poll=0.05,
+                                                        deadline=120.0)
     np.save(os.path.join(out_dir, f"elastic{rank}.npy"), np.concatenate([[tot], ep]))
     np.save(os.path.join(out_dir, f"mine{rank}.npy"), np.asarray(mine))
+    np.save(os.path.join(out_dir, f"taken{rank}.npy"), np.asarray(taken, dtype=np.int64))
 
 
 def test_elastic_run_survives_a_dead_rank(tmp_path):
@@ -228,8 +230,17 @@ def test_elastic_run_survives_a_dead_rank(tmp_path):
         total += v
     assert res[0][0] == total
     # rank 1 stored at most its first batch; the survivors solved the rest,
-    # including its orphaned second batch (a live rank starved of CPU past
-    # the timeout may also have had a claim re-solved, with the same energy)
+    # including its orphaned second batch
     mine = [set(np.load(tmp_path / f"mine{r}.npy").tolist()) for r in (0, 2)]
+    taken = [set(np.load(tmp_path / f"taken{r}.npy").tolist()) for r in (0, 2)]
     assert len(mine[0] | mine[1]) >= len(pairs) - 2
+    assert taken[0] | taken[1], "nobody took over the dead rank's claims"
+    # a partition is solved twice only through a takeover: the overlap of the
+    # survivors' work is made of taken-over claims (a live rank starved of CPU
+    # past the timeout can have a claim taken over; the energy is the same),
+    # and no more than the dead rank's batch plus one batch per survivor is
+    # solved twice
+    dup = mine[0] & mine[1]
+    assert dup <= (taken[0] | taken[1]), (dup, taken)
+    assert len(dup) <= 2 + 2 * 2, dup
     del store
