@@ -36,6 +36,7 @@ def main(argv=None):
     ap.add_argument("--partitions", type=int, default=0,
                     help="partitioned mode: the first N virtual pairs (a <= b, a then b)")
     ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--chunk", type=int, default=0, help="partitions per call (progress lines between calls)")
     ap.add_argument("--dmrg", type=int, default=0,
                     help="build the reference with the library's ground-state DMRG at this M0 "
                          "(S^2 penalty 1) instead of the FCI vector")
@@ -93,10 +94,28 @@ def main(argv=None):
             pairs = [(x, y) for x in range(kv) for y in range(x, kv)][: a.partitions]
             Ms = synthetic.partition_bond_dims(len(pairs)) if a.M <= 0 else [a.M] * len(pairs)
             t = time.time()
-            tot, ep, rep = L.mpspt_minimize_partitioned(ctx, a.h0, pairs, Ms, n_streams=a.streams)
+            step = a.chunk if a.chunk > 0 else len(pairs)
+            eps, cg, launches, wait = [], 0, 0, 0.0
+            for c0 in range(0, len(pairs), step):   # chunks: a progress line after each
+                _, ep_c, rep = L.mpspt_minimize_partitioned(ctx, a.h0, pairs[c0:c0 + step], Ms[c0:c0 + step],
+                                                            n_streams=a.streams)
+                eps.extend(float(v) for v in ep_c)
+                cg += rep.cg_iters
+                launches += rep.kernel_launches
+                wait += rep.host_wait_ms / 1e3
+                if step < len(pairs):
+                    print(json.dumps({"done": len(eps), "of": len(pairs), "wall_s": time.time() - t}), flush=True)
             wall = time.time() - t
+            tot = 0.0
+            for v in eps:       # pair order
+                tot += v
+            rep.cg_iters, rep.kernel_launches, rep.host_wait_ms = cg, launches, wait * 1e3
+            hist = {}
+            for m in Ms:
+                hist[m] = hist.get(m, 0) + 1
             print(json.dumps({"config": a.config, "h0": a.h0, "prec": a.prec, "partitions": len(pairs),
-                              "M_part": "seeded from {32,...,512}" if a.M <= 0 else a.M, "E2": tot,
+                              "M_part": "seeded from {32,...,512}" if a.M <= 0 else a.M,
+                              "M_part_counts": {str(k): v for k, v in sorted(hist.items())}, "E2": tot,
                               "wall_s": wall, "partitions_per_s": len(pairs) / wall, "streams": a.streams,
                               "cg_iters": rep.cg_iters, "kernel_launches": rep.kernel_launches,
                               "host_wait_s": rep.host_wait_ms / 1e3, **ref_info}),

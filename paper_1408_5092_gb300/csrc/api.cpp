@@ -639,8 +639,8 @@ const char* mpspt_status_string(mpspt_status s) {
         case MPSPT_OK: return "ok";
         case MPSPT_ERR_INVALID: return g_last.empty() ? "invalid argument" : g_last.c_str();
         case MPSPT_ERR_OOM: return "out of memory";
-        case MPSPT_ERR_NOT_SPD: return "H0 - E0 not positive definite on the local space";
-        case MPSPT_ERR_NOT_CONVERGED: return "iteration limit reached";
+        case MPSPT_ERR_NOT_SPD: return g_last.empty() ? "H0 - E0 not positive definite on the local space" : g_last.c_str();
+        case MPSPT_ERR_NOT_CONVERGED: return g_last.empty() ? "iteration limit reached" : g_last.c_str();
         case MPSPT_ERR_TIMEOUT: return "bounded device wait timed out";
         case MPSPT_ERR_CUDA: return g_last.empty() ? "CUDA error" : g_last.c_str();
         case MPSPT_ERR_STATE: return g_last.empty() ? "call out of order" : g_last.c_str();

@@ -5,9 +5,9 @@
 namespace mpspt {
 
 namespace {
-constexpr int kMaxSweepsF64 = 40;      // float64 Jacobi from the identity
-constexpr int kMaxSweepsF32 = 12;      // float32 start
-constexpr int kMaxSweepsPolish = 16;   // float64 polish of V^T A V
+constexpr int kMaxSweepsF64 = 60;      // float64 Jacobi from the identity
+constexpr int kMaxSweepsF32 = 12;      // float32 start (a cap is not an error: the polish follows)
+constexpr int kMaxSweepsPolish = 30;   // float64 polish of V^T A V
 constexpr int kClusterMinN = 48;       // float64 sweeps on CTA clusters from this size
 size_t a16(size_t b) { return (b + 15) & ~(size_t)15; }
 }  // namespace

@@ -47,12 +47,20 @@ template <class T>
 struct JacTol;
 template <>
 struct JacTol<double> {
-    static constexpr double stop = 1e-30, skip = 1e-18, absf = 0.0, stall = 1e-8;
+    static constexpr double stop = 1e-30, skip = 1e-18, absf = 0.0, stall = 1e-8, null = 1e-14;
 };
 template <>
 struct JacTol<float> {
-    static constexpr double stop = 1e-11, skip = 1e-9, absf = 0.0, stall = 1e-8;
+    static constexpr double stop = 1e-11, skip = 1e-9, absf = 0.0, stall = 1e-8, null = 0.0;
 };
+// Null pairs: a pair (p, q) whose 2x2 block has every entry below
+// null * |A|_F is neither rotated nor counted in the off-diagonal norm.  Its
+// eigenvalues are below 2 null |A|_F, so inside such a cluster the vectors
+// are set by rounding anyway; every coupling of a null index to a larger
+// entry is still rotated away.  For the density matrices of the truncation
+// (positive semidefinite) these are the exactly rank-deficient directions,
+// far below the keep threshold; skipping them saves the sweeps the polish
+// spent circulating rounding noise inside the null cluster.
 
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -105,19 +113,42 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
     }
     __syncthreads();
     auto S = [&](int a, int b) -> T& { return a <= b ? P[rowoff[a] + b] : P[rowoff[b] + a]; };
-    // convergence test
+    // convergence test: |A|_F first (it sets the null level), then the
+    // off-diagonal norm without null pairs
+    __shared__ double nullv;
     {
-        double off = 0.0, all = 0.0;
+        double all = 0.0;
         for (int i = warp; i < n; i += nw)
             for (int j = i + lane; j < n; j += 32) {
                 const double v = (double)P[rowoff[i] + j];
-                if (j == i) all += v * v;
+                all += (j == i ? 1.0 : 2.0) * v * v;
+            }
+        for (int o = 16; o > 0; o >>= 1) all += __shfl_xor_sync(0xffffffffu, all, o);
+        if (lane == 0) red[1][warp] = all;
+        __syncthreads();
+        if (tid == 0) {
+            double sa = 0.0;
+            for (int w = 0; w < nw; ++w) sa += red[1][w];
+            nullv = JacTol<T>::null * sqrt(sa);
+        }
+        __syncthreads();
+        const double nv = nullv;
+        double off = 0.0;
+        all = 0.0;
+        for (int i = warp; i < n; i += nw) {
+            const double di = fabs((double)P[rowoff[i] + i]);
+            for (int j = i + lane; j < n; j += 32) {
+                const double v = (double)P[rowoff[i] + j];
+                if (j == i) { all += v * v; continue; }
+                if (fabs(v) < nv && di < nv && fabs((double)P[rowoff[j] + j]) < nv) all += 2.0 * v * v;
                 else off += 2.0 * v * v;
             }
+        }
         for (int o = 16; o > 0; o >>= 1) {
             off += __shfl_xor_sync(0xffffffffu, off, o);
             all += __shfl_xor_sync(0xffffffffu, all, o);
         }
+        __syncthreads();
         if (lane == 0) { red[0][warp] = off; red[1][warp] = all; }
         __syncthreads();
         if (tid == 0) {
@@ -157,7 +188,10 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jac_sweep(const JacTask* __rest
             if (q >= 0) {
                 const T apq = P[rowoff[p] + q];
                 const T app = P[rowoff[p] + p], aqq = P[rowoff[q] + q];
-                if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && (double)fabs(apq) > thr && apq != T(0)) {
+                const bool null_pair = (double)fabs(apq) < nullv && (double)fabs(app) < nullv &&
+                                       (double)fabs(aqq) < nullv;
+                if (!null_pair && fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && (double)fabs(apq) > thr &&
+                    apq != T(0)) {
                     const T th = (aqq - app) / (T(2) * apq);
                     const T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
                     c = T(1) / sqrt(tt * tt + T(1));
@@ -262,21 +296,58 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
         const size_t e = a <= b ? (size_t)rowoff[a] + b : (size_t)rowoff[b] + a;
         return cl.map_shared_rank(Ploc, (int)(e % JC))[e / JC];
     };
-    // convergence test over the whole matrix (partial sums gathered in rank 0)
+    // convergence test over the whole matrix (partial sums gathered in rank
+    // 0): |A|_F first (it sets the null level, broadcast to every CTA), then
+    // the off-diagonal norm without null pairs; the diagonal is copied into
+    // the head's spare space so the null test reads it locally
+    __shared__ double nullv;
+    double* dg = reinterpret_cast<double*>(sm + align16((size_t)n * 16) + align16(2 * (size_t)n * sizeof(T)));
     {
-        double off = 0.0, all = 0.0;
+        double all = 0.0;
         for (int i = warp; i < n; i += nw)
             for (int j = i + lane; j < n; j += 32) {
                 const size_t e = (size_t)rowoff[i] + j;
                 if ((int)(e % JC) != rank) continue;
                 const double v = (double)Ploc[e / JC];
-                if (j == i) all += v * v;
+                all += (j == i ? 1.0 : 2.0) * v * v;
+            }
+        for (int o = 16; o > 0; o >>= 1) all += __shfl_xor_sync(0xffffffffu, all, o);
+        if (lane == 0) red[1][warp] = all;
+        __syncthreads();
+        if (tid == 0) {
+            double sd = 0.0;
+            for (int w = 0; w < nw; ++w) sd += red[1][w];
+            cl.map_shared_rank(&part[0][0], 0)[rank] = sd;
+        }
+        for (int i = tid; i < n; i += JAC_THREADS) {
+            const size_t e = (size_t)rowoff[i] + i;
+            dg[i] = (double)cl.map_shared_rank(Ploc, (int)(e % JC))[e / JC];
+        }
+        cl.sync();
+        if (rank == 0 && tid == 0) {
+            double sa = 0.0;
+            for (int r = 0; r < JC; ++r) sa += part[0][r];
+            const double nvv = JacTol<T>::null * sqrt(sa);
+            for (int r = 0; r < JC; ++r) *cl.map_shared_rank(&nullv, r) = nvv;
+        }
+        cl.sync();
+        const double nv = nullv;
+        double off = 0.0;
+        all = 0.0;
+        for (int i = warp; i < n; i += nw)
+            for (int j = i + lane; j < n; j += 32) {
+                const size_t e = (size_t)rowoff[i] + j;
+                if ((int)(e % JC) != rank) continue;
+                const double v = (double)Ploc[e / JC];
+                if (j == i) { all += v * v; continue; }
+                if (fabs(v) < nv && fabs(dg[i]) < nv && fabs(dg[j]) < nv) all += 2.0 * v * v;
                 else off += 2.0 * v * v;
             }
         for (int o = 16; o > 0; o >>= 1) {
             off += __shfl_xor_sync(0xffffffffu, off, o);
             all += __shfl_xor_sync(0xffffffffu, all, o);
         }
+        __syncthreads();
         if (lane == 0) { red[0][warp] = off; red[1][warp] = all; }
         __syncthreads();
         if (tid == 0) {
@@ -326,7 +397,10 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(JAC_THREADS)
             T c = T(1), s = T(0);
             if (q >= 0) {
                 const T apq = S(p, q), app = S(p, p), aqq = S(q, q);
-                if (fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && (double)fabs(apq) > thr && apq != T(0)) {
+                const bool null_pair = (double)fabs(apq) < nullv && (double)fabs(app) < nullv &&
+                                       (double)fabs(aqq) < nullv;
+                if (!null_pair && fabs(apq) > SKIP * sqrt(fabs(app * aqq)) && (double)fabs(apq) > thr &&
+                    apq != T(0)) {
                     const T th = (aqq - app) / (T(2) * apq);
                     const T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
                     c = T(1) / sqrt(tt * tt + T(1));

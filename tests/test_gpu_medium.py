@@ -90,7 +90,7 @@ def _gold(name):
     return json.load(open(path))
 
 
-@pytest.mark.parametrize("h0,M", [("fock", 64), ("dyall", 64), ("dyall", 128)])
+@pytest.mark.parametrize("h0,M", [("fock", 64), ("dyall", 64), ("dyall", 128), ("dyall", 256)])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 1e-6), ("mixed_fp16", 1e-6)])
 def test_medium_e2_per_sweep_matches_oracle(medium, h0, M, prec, tol):
     """E2 (and E3 of the state after the last compared sweep) per sweep at

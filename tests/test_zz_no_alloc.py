@@ -27,7 +27,9 @@ def _run(fn, sizes, A):
     Ad = torch.tensor(A, device="cuda", dtype=torch.float64)
     V = torch.zeros_like(Ad)
     w = torch.zeros(sum(sizes), device="cuda", dtype=torch.float64)
+    dev = torch.cuda.current_device()
     fn(0, torch.cuda.current_stream().cuda_stream, sizes, Ad.data_ptr(), V.data_ptr(), w.data_ptr())
+    assert torch.cuda.current_device() == dev      # the caller's current device is left as it was
     torch.cuda.synchronize()
     return V.cpu().numpy(), w.cpu().numpy()
 
