@@ -74,12 +74,16 @@ __global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks, int
         for (int j = 0; j < RJ; ++j) acc[i][j] = U(0);
     const int mrem = min(TM, t.m - t.r0);
     const int nrem = min(TN, t.n - t.c0);
+    int kbase = 0;   // position of op o's first K index in the concatenated K-list
     for (int o = t.op0; o < t.op1; ++o) {
         const Op op = ops[o];
+        const int kb = max(0, t.kb - kbase), ke = min(op.k, t.ke - kbase);
+        kbase += op.k;
+        if (kb >= ke) continue;
         const bool ta = op.trans & 1, tb = op.trans & 2;
         const U alpha = conv<U>(op.alpha);
-        for (int k0 = 0; k0 < op.k; k0 += TK) {
-            const int krem = min(TK, op.k - k0);
+        for (int k0 = kb; k0 < ke; k0 += TK) {
+            const int krem = min(TK, ke - k0);
             for (int e = threadIdx.x; e < TM * TK; e += NT) {
                 int i, kk;
                 if (ta) { i = e % TM; kk = e / TM; }
@@ -126,6 +130,7 @@ __global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks, int
         for (int j = 0; j < RJ; ++j) {
             const int c = tx + 16 * j;
             if (c >= nrem) continue;
+            if (t.part) { t.part[r * TN + c] = (T)acc[i][j]; continue; }
             const int gr = t.r0 + r, gc = t.c0 + c;
             T* dst;
             if (t.cmap == nullptr) dst = t.C + (size_t)gr * t.ldc + gc;
@@ -135,6 +140,25 @@ __global__ void __launch_bounds__(NT) k_gemm(const Task* __restrict__ tasks, int
         }
     }
   }
+}
+
+// Split-K reduction: partial tiles summed in ascending order (deterministic).
+__global__ void k_splitk_reduce(const SplitRed* __restrict__ tasks, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const SplitRed t = tasks[blockIdx.x];
+    const int mrem = min(t.tm, t.m - t.r0), nrem = min(t.tn, t.n - t.c0);
+    const size_t tile = (size_t)t.tm * t.tn;
+    for (int e = threadIdx.x; e < mrem * nrem; e += blockDim.x) {
+        const int r = e / nrem, c = e % nrem;
+        double v = 0.0;
+        for (int q = 0; q < t.nparts; ++q) v += t.part[q * tile + (size_t)r * t.tn + c];
+        const int gr = t.r0 + r, gc = t.c0 + c;
+        double* dst;
+        if (t.cmap == nullptr) dst = t.C + (size_t)gr * t.ldc + gc;
+        else if (t.cmap_rows) dst = t.C + t.cmap[2 * gr] + (size_t)gc * t.cmap[2 * gr + 1];
+        else dst = t.C + t.cmap[2 * gc] + (size_t)gr * t.cmap[2 * gc + 1];
+        *dst = t.accumulate ? *dst + v : v;
+    }
 }
 
 // dst = sum coef * src over the task's source list (memory-bound).
@@ -589,6 +613,10 @@ void launch_tile(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream
 bool gemm_tile_supported(int tm, int tn) {
     return (tm == 64 && tn == 64) || (tm == 32 && tn == 64) || (tm == 64 && tn == 32) || (tm == 16 && tn == 128) ||
            (tm == 32 && tn == 32);
+}
+
+void launch_splitk_reduce(const SplitRed* tasks, int ntask, cudaStream_t st, const int* skip) {
+    if (ntask > 0) { counted(); k_splitk_reduce<<<ntask, 256, 0, st>>>(tasks, skip); }
 }
 
 void launch_gemm_tile(int tm, int tn, bool f32, const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,

@@ -28,6 +28,22 @@ struct GemmTask {
     int op0, op1;      // range of GemmOp
     int accumulate;    // 1: C += sum, 0: C = sum
     int cmap_rows;
+    // split-K (CUDA-core kernels only): the task sums the positions
+    // [kb, ke) of the concatenated K-list of its ops and, with part set,
+    // writes its tm x tn partial tile there (dense, row-major) instead of C;
+    // a reduction task then adds the partials in order
+    double* part;
+    int kb, ke;
+};
+// Sum of the nparts partial tiles at part + q * tm * tn (q ascending) into
+// the tile (r0, c0) of C, with the GemmTask addressing (cmap, accumulate).
+struct SplitRed {
+    const double* part;
+    double* C;
+    const int* cmap;
+    int nparts, tm, tn;
+    int ldc, m, n, r0, c0;
+    int accumulate, cmap_rows;
 };
 
 constexpr int GEMM_TM = 64;
@@ -132,6 +148,7 @@ void launch_gemm_f64(const GemmTask* tasks, int ntask, const GemmOp* ops, cudaSt
 // float64 or float32 arithmetic (f32) on float64 data.  Persistent: at most
 // the resident CTAs are launched and each walks a stride of the task list.
 bool gemm_tile_supported(int tm, int tn);
+void launch_splitk_reduce(const SplitRed* tasks, int ntask, cudaStream_t st, const int* skip = nullptr);
 void launch_gemm_tile(int tm, int tn, bool f32, const GemmTask* tasks, int ntask, const GemmOp* ops, cudaStream_t st,
                       const int* skip = nullptr);
 // Skinny-tile (16 x 128) float64 variant for panels with few rows.

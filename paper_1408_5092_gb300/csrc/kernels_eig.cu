@@ -58,9 +58,11 @@ struct JacTol<float> {
 // eigenvalues are below 2 null |A|_F, so inside such a cluster the vectors
 // are set by rounding anyway; every coupling of a null index to a larger
 // entry is still rotated away.  For the density matrices of the truncation
-// (positive semidefinite) these are the exactly rank-deficient directions,
-// far below the keep threshold; skipping them saves the sweeps the polish
-// spent circulating rounding noise inside the null cluster.
+// (positive semidefinite) in float64 these are the exactly rank-deficient
+// directions, far below the keep threshold; skipping them saves the sweeps
+// the polish spent circulating rounding noise inside the null cluster.  The
+// float32 start sweeps every pair (a null level at float32 resolution,
+// 1e-6, saved float32 sweeps but cost as many float64 polish sweeps).
 
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }

@@ -16,15 +16,46 @@ void GemmPlan::block(double* C, int ldc, int m, int n, int accumulate, int op0, 
     blocks.push_back({C, cmap_off, ldc, m, n, accumulate, op0, op1, cmap_rows});
 }
 
-void GemmPlan::split(int tm_, int tn_, std::vector<GemmTask>& out, std::vector<long long>* cm) const {
+int GemmPlan::kchunks(long long m, long long n, long long K) {
+    if (K < 2048 || m * n > 128LL * 256) return 1;
+    return (int)std::min<long long>(8, K / 1024);
+}
+
+void GemmPlan::split(int tm_, int tn_, std::vector<GemmTask>& out, std::vector<long long>* cm,
+                     std::vector<SplitRed>* rd, std::vector<long long>* rcm, size_t* part_elems) const {
     out.clear();
     if (cm) cm->clear();
-    for (const Blk& b : blocks)
+    if (rd) rd->clear();
+    if (rcm) rcm->clear();
+    size_t pe = 0;
+    for (const Blk& b : blocks) {
+        long long K = 0;
+        for (int o = b.op0; o < b.op1; ++o) K += ops[o].k;
+        const int S = (rd && !is_tc(kind)) ? kchunks(b.m, b.n, K) : 1;
+        const int step = (int)((K + S - 1) / S + 31) / 32 * 32;
         for (int r0 = 0; r0 < b.m; r0 += tm_)
             for (int c0 = 0; c0 < b.n; c0 += tn_) {
-                out.push_back({b.C, nullptr, b.ldc, b.m, b.n, r0, c0, b.op0, b.op1, b.accumulate, b.cmap_rows});
-                if (cm) cm->push_back(b.cmap_off);
+                if (S == 1) {
+                    out.push_back({b.C, nullptr, b.ldc, b.m, b.n, r0, c0, b.op0, b.op1, b.accumulate, b.cmap_rows,
+                                   nullptr, 0, 1 << 30});
+                    if (cm) cm->push_back(b.cmap_off);
+                    continue;
+                }
+                int np = 0;
+                for (long long k0 = 0; k0 < K; k0 += step, ++np) {
+                    // the partial pointer holds an element offset until upload
+                    out.push_back({b.C, nullptr, b.ldc, b.m, b.n, r0, c0, b.op0, b.op1, 0, b.cmap_rows,
+                                   reinterpret_cast<double*>((pe + (size_t)np * tm_ * tn_) * sizeof(double) + 8),
+                                   (int)k0, (int)std::min<long long>(K, k0 + step)});
+                    if (cm) cm->push_back(-1);
+                }
+                rd->push_back({reinterpret_cast<const double*>(pe * sizeof(double) + 8), b.C, nullptr, np, tm_, tn_,
+                               b.ldc, b.m, b.n, r0, c0, b.accumulate, b.cmap_rows});
+                if (rcm) rcm->push_back(b.cmap_off);
+                pe += (size_t)np * tm_ * tn_;
             }
+    }
+    if (part_elems) *part_elems = pe;
 }
 
 namespace {
@@ -65,12 +96,20 @@ void GemmPlan::upload(cudaStream_t st) {
         tm = t.first;
         tn = t.second;
     }
-    split(tm, tn, tasks, &task_cmap);
+    size_t pe = 0;
+    split(tm, tn, tasks, &task_cmap, &reds, &red_cmap, &pe);
+    if (pe) dpart.ensure(pe * sizeof(double) + 16, st);
+    double* pbase = dpart.as<double>();
+    for (auto& t : tasks)   // partial offsets (stored as byte offsets + 8) become pointers
+        if (t.part) t.part = pbase + ((reinterpret_cast<uintptr_t>(t.part) - 8) / sizeof(double));
+    for (auto& r : reds) r.part = pbase + ((reinterpret_cast<uintptr_t>(r.part) - 8) / sizeof(double));
     order_tasks(tasks, &task_cmap, ops);
     if (!cmaps.empty()) mpspt::upload(dcmaps, cmaps, st);
     const int* cbase = dcmaps.as<int>();
     for (size_t i = 0; i < tasks.size(); ++i)
         tasks[i].cmap = task_cmap[i] >= 0 ? cbase + task_cmap[i] : nullptr;
+    for (size_t i = 0; i < reds.size(); ++i) reds[i].cmap = red_cmap[i] >= 0 ? cbase + red_cmap[i] : nullptr;
+    if (!reds.empty()) mpspt::upload(dreds, reds, st);
     if (checks_enabled()) {
         // per planned block (all tiles of a block share its output and its
         // K-list): the output range, or the span of its mapped addresses,
@@ -200,6 +239,7 @@ void GemmPlan::run(cudaStream_t st) const {
     const GemmOp* o = dops.as<GemmOp>();
     if (is_tc(kind)) launch_gemm_tc(t, nt, o, err, st, skip, kind == GEMM_TC16);
     else launch_gemm_tile(tm, tn, kind == GEMM_F32, t, nt, o, st, skip);
+    if (!reds.empty()) launch_splitk_reduce(dreds.as<SplitRed>(), (int)reds.size(), st, skip);
 }
 
 void Omega::build(const MPO& W, int i) {

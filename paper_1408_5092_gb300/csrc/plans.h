@@ -65,9 +65,24 @@ struct GemmPlan {
     std::vector<long long> task_cmap; // per task: offset into cmaps or -1
     double flops = 0.0;   // algorithmic: sum over ops of 2 m n k (each product once)
     DBuf dtasks, dops, dcmaps;
-    void clear() { blocks.clear(); tasks.clear(); ops.clear(); cmaps.clear(); task_cmap.clear(); flops = 0.0; }
-    // tasks of the recorded blocks for a tile shape (no cmap pointers yet)
-    void split(int tm_, int tn_, std::vector<GemmTask>& out, std::vector<long long>* cm) const;
+    // split-K (CUDA-core kinds): partial tiles and their ordered reductions
+    std::vector<SplitRed> reds;
+    std::vector<long long> red_cmap;
+    DBuf dreds, dpart;
+    void clear() {
+        blocks.clear(); tasks.clear(); ops.clear(); cmaps.clear(); task_cmap.clear(); reds.clear(); red_cmap.clear();
+        flops = 0.0;
+    }
+    // K-chunks of a block: blocks with a small output and a long K-list are
+    // summed by several CTAs (the chunking depends only on the block, not on
+    // the tile shape, so every tile gives the same rounding)
+    static int kchunks(long long m, long long n, long long K);
+    // tasks of the recorded blocks for a tile shape (no cmap pointers yet);
+    // with rd, split-K chunk tasks get partial-tile offsets (in doubles, from
+    // the partial buffer's start) and rd receives the reductions
+    void split(int tm_, int tn_, std::vector<GemmTask>& out, std::vector<long long>* cm,
+               std::vector<SplitRed>* rd = nullptr, std::vector<long long>* rcm = nullptr,
+               size_t* part_elems = nullptr) const;
     int mark() const { return (int)ops.size(); }
     void op(const double* A, int lda, const double* B, int ldb, int k, int trans, double alpha) {
         if (k <= 0) return;
