@@ -8,12 +8,13 @@ namespace {
 constexpr int kMaxSweepsF64 = 60;      // float64 Jacobi from the identity
 constexpr int kMaxSweepsF32 = 12;      // float32 start (a cap is not an error: the polish follows)
 constexpr int kMaxSweepsPolish = 30;   // float64 polish of V^T A V
+constexpr int kPolishBatch = 6;        // sweeps launched before the host looks at the stop flags
 constexpr int kClusterMinN = 48;       // float64 sweeps on CTA clusters from this size
 size_t a16(size_t b) { return (b + 15) & ~(size_t)15; }
 }  // namespace
 
 void EigSolver::jacobi(const std::vector<EigTask>& et, const std::vector<const double*>& in, int vinit, bool f32,
-                       int maxs, bool want_w, cudaStream_t st) {
+                       int maxs, bool want_w, cudaStream_t st, int batch) {
     const int nt = (int)et.size();
     std::vector<size_t> off(nt);
     size_t tot = 0;
@@ -65,10 +66,28 @@ void EigSolver::jacobi(const std::vector<EigTask>& et, const std::vector<const d
     upload(drows, rows, st);
     if (!one.empty()) upload(djt1, one, st);
     if (!clu.empty()) upload(djtc, clu, st);
-    for (int s = 0; s <= maxs; ++s) {
-        if (!one.empty()) launch_jac_sweep(djt1.as<JacTask>(), (int)one.size(), s, maxs, f32, st);
-        if (!clu.empty()) launch_jac_sweep_cluster(djtc.as<JacTask>(), (int)clu.size(), s, maxs, csm, st);
-        if (s < maxs) launch_jac_apply(djt.as<JacTask>(), drows.as<JacRows>(), (int)rows.size(), smem, s, f32, st);
+    // Sweeps are launched in batches; a matrix that has stopped turns its
+    // later launches into no-ops, and between batches the host reads the
+    // stop flags (one small copy and a sync) so that the tail of a long cap
+    // is only launched when some matrix still needs it.
+    if (batch <= 0) batch = maxs + 1;
+    for (int s0 = 0; s0 <= maxs; s0 += batch) {
+        if (s0 > 0) {
+            if (!flag_host) MPSPT_CUDA(cudaMallocHost(&flag_host, 4096 * sizeof(int)));
+            bool all = true;
+            for (int c0 = 0; c0 < nt && all; c0 += 4096) {
+                const int nc = std::min(4096, nt - c0);
+                MPSPT_CUDA(cudaMemcpyAsync(flag_host, flags.as<int>() + c0, nc * sizeof(int), cudaMemcpyDeviceToHost, st));
+                MPSPT_CUDA(cudaStreamSynchronize(st));
+                for (int i = 0; i < nc; ++i) all = all && flag_host[i] != 0;
+            }
+            if (all) break;
+        }
+        for (int s = s0; s <= maxs && s < s0 + batch; ++s) {
+            if (!one.empty()) launch_jac_sweep(djt1.as<JacTask>(), (int)one.size(), s, maxs, f32, st);
+            if (!clu.empty()) launch_jac_sweep_cluster(djtc.as<JacTask>(), (int)clu.size(), s, maxs, csm, st);
+            if (s < maxs) launch_jac_apply(djt.as<JacTask>(), drows.as<JacRows>(), (int)rows.size(), smem, s, f32, st);
+        }
     }
     if (stats) {   // sweeps per matrix (diagnostics; synchronises)
         for (int i = 0; i < nt; ++i) {
@@ -96,7 +115,7 @@ void EigSolver::run(const std::vector<EigTask>& et, bool fp64_only, cudaStream_t
         jacobi(et, in, 0, false, kMaxSweepsF64, true, st);
         return;
     }
-    jacobi(et, in, 0, true, kMaxSweepsF32, false, st);
+    jacobi(et, in, 0, true, kMaxSweepsF32, false, st, kPolishBatch);
     size_t tot = 0;
     std::vector<size_t> off;
     for (const auto& t : et) { off.push_back(tot); tot += (size_t)t.n * t.n; }
@@ -136,7 +155,7 @@ void EigSolver::run(const std::vector<EigTask>& et, bool fp64_only, cudaStream_t
     batched(TV, 1, TVT, TG);       // G = B = V^T A V
     std::vector<const double*> bin;
     for (size_t i = 0; i < et.size(); ++i) bin.push_back(g.as<double>() + off[i]);
-    jacobi(et, bin, 1, false, kMaxSweepsPolish, true, st);
+    jacobi(et, bin, 1, false, kMaxSweepsPolish, true, st, kPolishBatch);
 }
 
 }  // namespace mpspt

@@ -15,6 +15,8 @@ struct EigSolver {
     // cap (device ints, valid once the stream has reached them)
     DBuf flags;
     int nflags = 0;
+    int* flag_host = nullptr;   // page-locked copy of the flags between sweep batches
+    ~EigSolver() { if (flag_host) cudaFreeHost(flag_host); }
     GemmPlan ge;   // batched square GEMMs of the float64 stage
     bool stats = false;   // count sweeps per matrix (sum, matrices, max)
     long long sweeps32[3] = {0, 0, 0}, sweeps_polish[3] = {0, 0, 0}, sweeps64[3] = {0, 0, 0};
@@ -34,7 +36,7 @@ struct EigSolver {
   private:
     // Jacobi from the given inputs (one per task) into the tasks' V (and w)
     void jacobi(const std::vector<EigTask>& et, const std::vector<const double*>& in, int vinit, bool f32, int maxs,
-                bool want_w, cudaStream_t st);
+                bool want_w, cudaStream_t st, int batch = 0);
 };
 
 }  // namespace mpspt

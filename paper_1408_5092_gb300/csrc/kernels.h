@@ -28,7 +28,7 @@ struct GemmTask {
     int op0, op1;      // range of GemmOp
     int accumulate;    // 1: C += sum, 0: C = sum
     int cmap_rows;
-    // split-K (CUDA-core kernels only): the task sums the positions
+    // split-K: the task sums the positions
     // [kb, ke) of the concatenated K-list of its ops and, with part set,
     // writes its tm x tn partial tile there (dense, row-major) instead of C;
     // a reduction task then adds the partials in order

@@ -176,11 +176,15 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
         const int mrem = min(BM, t.m - t.r0);
         const int nrem = min(BN, t.n - t.c0);
         const int stage0 = stage;
+        int kbase = 0;   // position of op o's first K index in the task's concatenated K-list
         for (int o = t.op0; o < t.op1 && ok; ++o) {
             const GemmOp op = ops[o];
+            const int kb = max(0, t.kb - kbase), ke = min(op.k, t.ke - kbase);
+            kbase += op.k;
+            if (kb >= ke) continue;
             const bool ta = op.trans & 1, tb = op.trans & 2;
             const float alpha = d2f_rn(op.alpha);
-            for (int k0 = 0; k0 < op.k; k0 += BK) {
+            for (int k0 = kb; k0 < ke; k0 += BK) {
                 const int buf = stage & 1;
                 if (stage >= 2) {   // stage buffer free once the MMAs of stage-2 completed
                     if (tid == 0) wait_ok = mbar_wait(&bars[buf], ((stage - 2) >> 1) & 1) ? 1 : 0;
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
                 unsigned char* Alo = Ahi + A_BYTES;
                 unsigned char* Bhi = Alo + A_BYTES;
                 unsigned char* Blo = Bhi + B_BYTES;
-                const int krem = min(BK, op.k - k0);
+                const int krem = min(BK, ke - k0);
                 // A: BM x BK values, B: BN x BK values; LCH loads per thread are
                 // issued before any of them is split and stored
                 for (int e0 = 0; e0 < BM * BK; e0 += NTH * LCH) {
@@ -288,7 +292,9 @@ __global__ void __launch_bounds__(NTH, 1) k_gemm_tc(const GemmTask* __restrict__
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int col = c0 + q;
-                    if (col < nrem) {
+                    if (col < nrem && t.part) {   // split-K partial tile (BM x BN, row-major)
+                        t.part[row * BN + col] = (double)__uint_as_float(v[q]);
+                    } else if (col < nrem) {
                         const int gr = t.r0 + row, gc = t.c0 + col;
                         double* dst;
                         if (t.cmap == nullptr) dst = t.C + (size_t)gr * t.ldc + gc;

@@ -31,8 +31,8 @@ void GemmPlan::split(int tm_, int tn_, std::vector<GemmTask>& out, std::vector<l
     for (const Blk& b : blocks) {
         long long K = 0;
         for (int o = b.op0; o < b.op1; ++o) K += ops[o].k;
-        const int S = (rd && !is_tc(kind)) ? kchunks(b.m, b.n, K) : 1;
-        const int step = (int)((K + S - 1) / S + 31) / 32 * 32;
+        const int S = rd ? kchunks(b.m, b.n, K) : 1;
+        const int step = (int)((K + S - 1) / S + 63) / 64 * 64;   // whole K-stages of either kernel
         for (int r0 = 0; r0 < b.m; r0 += tm_)
             for (int c0 = 0; c0 < b.n; c0 += tn_) {
                 if (S == 1) {

@@ -65,7 +65,7 @@ struct GemmPlan {
     std::vector<long long> task_cmap; // per task: offset into cmaps or -1
     double flops = 0.0;   // algorithmic: sum over ops of 2 m n k (each product once)
     DBuf dtasks, dops, dcmaps;
-    // split-K (CUDA-core kinds): partial tiles and their ordered reductions
+    // split-K: partial tiles and their ordered reductions
     std::vector<SplitRed> reds;
     std::vector<long long> red_cmap;
     DBuf dreds, dpart;
