@@ -470,37 +470,48 @@ __global__ void __launch_bounds__(32) k_jac_apply(const JacTask* __restrict__ ta
         R[i * ld + j] = (sweep == 0 && !t.vinit) ? T(b.r0 + i == j ? 1 : 0) : (T)t.V[(size_t)(b.r0 + i) * n + j];
     }
     __syncwarp();
-    if (!done && lane < b.rows) {
+    if (!done) {   // the whole warp takes part (shuffles); lanes >= rows only relay rotations
         const int m = n + (n & 1), half = m / 2;
         const int* rhead = reinterpret_cast<const int*>(t.rot);
         const RotE<T>* rlist =
             reinterpret_cast<const RotE<T>*>(reinterpret_cast<const unsigned char*>(t.rot) + jac_rot_head(n));
-        T* row = R + lane * ld;
         const int nr = __ldg(rhead);
         for (int r = 0; r < nr; ++r) {
             const int c = __ldg(rhead + 1 + r);
             const RotE<T>* L = rlist + (size_t)r * half;
-            // the rotations of one round act on disjoint columns: eight at a
-            // time, all loads before all stores
-            int j = 0;
-            for (; j + 8 <= c; j += 8) {
-                RotE<T> e[8];
-                T x[8], y[8];
+            // the rotations of one round act on disjoint columns.  The warp
+            // reads 32 of them at a time, one per lane (coalesced), and hands
+            // them round by shuffles; each lane then runs them on its own row
+            // eight at a time, all loads before all stores.
+            for (int j0 = 0; j0 < c; j0 += 32) {
+                const int cnt = min(32, c - j0);
+                RotE<T> mine{};
+                if (lane < cnt) mine = L[j0 + lane];
+                for (int q0 = 0; q0 < cnt; q0 += 8) {
+                    const int nq = min(8, cnt - q0);
+                    T cs[8], sn[8], x[8], y[8];
+                    int pp[8], qq[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) e[q] = L[j + q];
+                    for (int q = 0; q < 8; ++q) {
+                        const int src = q0 + (q < nq ? q : 0);
+                        cs[q] = __shfl_sync(0xffffffffu, mine.c, src);
+                        sn[q] = __shfl_sync(0xffffffffu, mine.s, src);
+                        pp[q] = __shfl_sync(0xffffffffu, mine.p, src);
+                        qq[q] = __shfl_sync(0xffffffffu, mine.q, src);
+                    }
+                    if (lane < b.rows) {
+                        T* row = R + lane * ld;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) { x[q] = row[e[q].p]; y[q] = row[e[q].q]; }
+                        for (int q = 0; q < 8; ++q)
+                            if (q < nq) { x[q] = row[pp[q]]; y[q] = row[qq[q]]; }
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    row[e[q].p] = e[q].c * x[q] - e[q].s * y[q];
-                    row[e[q].q] = e[q].s * x[q] + e[q].c * y[q];
+                        for (int q = 0; q < 8; ++q)
+                            if (q < nq) {
+                                row[pp[q]] = cs[q] * x[q] - sn[q] * y[q];
+                                row[qq[q]] = sn[q] * x[q] + cs[q] * y[q];
+                            }
+                    }
                 }
-            }
-            for (; j < c; ++j) {
-                const RotE<T> e = L[j];
-                const T x = row[e.p], y = row[e.q];
-                row[e.p] = e.c * x - e.s * y;
-                row[e.q] = e.s * x + e.c * y;
             }
         }
     }

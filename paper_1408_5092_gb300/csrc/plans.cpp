@@ -17,8 +17,8 @@ void GemmPlan::block(double* C, int ldc, int m, int n, int accumulate, int op0, 
 }
 
 int GemmPlan::kchunks(long long m, long long n, long long K) {
-    if (K < 2048 || m * n > 128LL * 256) return 1;
-    return (int)std::min<long long>(8, K / 1024);
+    if (K < 1024 || m * n > 128LL * 512) return 1;
+    return (int)std::min<long long>(8, K / 512);
 }
 
 void GemmPlan::split(int tm_, int tn_, std::vector<GemmTask>& out, std::vector<long long>* cm,
