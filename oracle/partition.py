@@ -19,6 +19,19 @@ orbital order, so Jordan-Wigner signs agree with the full chain).
 Pinned by tests/test_oracle_partition.py: sum of partition E2* equals the
 full brute-force E2*, and the MPS sweep of each partition at its exact bond
 dimension reproduces its E2*_P.
+
+E3 over partitions (Eq. 5 for Psi1 = sum_P Psi1^P).  Partitions live on
+disjoint virtual-occupation patterns and H0 keeps every pattern, so for
+P != P' both <Psi1^P|Psi1^P'> and <Psi1^P|H0|Psi1^P'> vanish, while V (which
+moves up to two electrons between orbitals) does not:
+  E3 = sum_P E3(Psi1^P) + sum_{P != P'} <Psi1^P|H|Psi1^P'>.
+Two routes: the plain definition (every Psi1^P written as a vector on the
+full determinant space X and Eq. 5 applied to the sum; small systems), and
+transfers of embedded MPSs (every Psi1^P written on the full chain, empty
+virtual sites passing the bond through).  Pinned by
+tests/test_oracle_partition.py: at exact partitions the sum of the embedded
+vectors is the full-space Psi1* and the E3 of the sum is the full-space E3*;
+the two routes agree on truncated MPSs.
 """
 import numpy as np
 
@@ -105,11 +118,16 @@ class ExactPartition:
         self.A = operator_matrix(sub.h0_terms(), self.X)
         self.g = apply_terms(sub.rhs_terms(), ref, c0[order], self.X)
 
+    def solve(self):
+        """Exact Psi1*_P on X_P (Eq. 2 restricted to the partition)."""
+        if len(self.X) == 0:
+            return np.zeros(0)
+        return -np.linalg.solve(self.A.toarray(), self.g)
+
     def e2(self):
         if len(self.X) == 0:
             return 0.0
-        x = np.linalg.solve(self.A.toarray(), self.g)
-        return -float(self.g @ x)
+        return float(self.g @ self.solve())
 
 
 def partition_e2(prob, M_of, sweep_kwargs=None):
@@ -126,3 +144,104 @@ def partition_e2(prob, M_of, sweep_kwargs=None):
         parts.append(((a, b), e))
         total += e
     return total, parts
+
+
+# ------------------------------------------------------- E3 over partitions
+def sub_dets_to_full(sub, dets):
+    """Bit strings over a partition chain's orbitals -> bit strings over all
+    orbitals (chain orbital i is orbital sub.orbs[i]).  The chain keeps the
+    orbitals' relative order, so a determinant's sign convention (creators in
+    ascending spin-orbital order) is unchanged."""
+    out = np.zeros(len(dets), dtype=np.uint64)
+    for i, p in enumerate(sub.orbs):
+        out |= ((dets >> np.uint64(2 * i)) & np.uint64(3)) << np.uint64(2 * p)
+    return out
+
+
+def embed_vector(sub, dets, coefs, X):
+    """Psi1^P given on sub-chain determinants -> vector on the full space X."""
+    x = np.zeros(len(X))
+    if len(dets) == 0:
+        return x
+    idx = X.index(sub_dets_to_full(sub, dets))
+    if np.any(idx < 0):
+        raise ValueError("partition determinant outside the first-order space")
+    x[idx] = coefs
+    return x
+
+
+def mps_vector(sub, mps, X):
+    """An MPS on a partition chain -> its vector on the full space X."""
+    d, c = ci_to_dets(mps.to_dense(), sub.k)
+    return embed_vector(sub, d, c, X)
+
+
+def e3_split(prob, X, A, xs):
+    """Eq. 5 for x = sum(xs) on X by its plain definition:
+    E3 = <x|H|x> - <x|A|x> - (E0 + E1) <x|x>   (A = H0 - E0).
+    Returns (E3 of the sum, [E3 of each x_P], sum of the cross terms); the
+    cross sum is E3 of the sum minus the diagonal terms."""
+    H = operator_matrix(prob.hamiltonian_terms(), X)
+
+    def e3(x):
+        return float(x @ (H @ x) - x @ (A @ x) - (prob.E0 + prob.E1) * (x @ x))
+
+    diag = [e3(x) for x in xs]
+    tot = e3(np.sum(xs, axis=0)) if xs else 0.0
+    return tot, diag, tot - sum(diag)
+
+
+def embed_mps(prob, sub, mps):
+    """Psi1^P (MPS on its partition chain) written on the full chain: active
+    sites and the partition's virtual sites keep their tensors; every other
+    virtual orbital becomes an empty site that passes the bond through
+    (identity on the bond, local state |0>, even parity)."""
+    from .mps import MPS
+    ka = prob.k_act
+    A = [t.copy() for t in mps.A[:ka]]
+    q = [l.copy() for l in mps.q[:ka + 1]]
+    j = ka
+    for v in range(prob.k_virt):
+        if j < sub.k and sub.orbs[j] == ka + v:
+            A.append(mps.A[j].copy())
+            q.append(mps.q[j + 1].copy())
+            j += 1
+        else:
+            D = len(q[-1])
+            T = np.zeros((D, 4, D))
+            T[np.arange(D), 0, np.arange(D)] = 1.0
+            A.append(T)
+            q.append(q[-1].copy())
+    return MPS(A, q)
+
+
+def partition_psi1(prob, pairs, M_of, sweep_kwargs=None):
+    """MPS-PT2 sweep of every listed partition: [(sub, E2_P, Psi1^P MPS)]."""
+    from .mps import HylleraasSweep
+    out = []
+    for a, b in pairs:
+        sub = SubProblem(prob, a, b)
+        sw = HylleraasSweep(sub, M_of(a, b), allowed=sub.allowed, **(sweep_kwargs or {}))
+        out.append((sub, sw.run(), sw.psi1))
+    return out
+
+
+def partition_e3_mps(prob, subs_psis, WH=None, WA=None):
+    """E3 of Psi1 = sum of the listed partitions' MPSs by transfers on the
+    full chain: E3(Psi1^P) = <H> - <A> - (E0 + E1)<1> for each P, and
+    2 <Psi1^P|H|Psi1^P'> for each pair P < P' (pairs in list order).
+    Returns (total, [E3 of each], cross sum, {(i, j): <P_i|H|P_j>})."""
+    from .mpo import build_mpo
+    from .mps import expectation, overlap
+    k, ka = prob.k, prob.k_act
+    WH = WH or build_mpo(prob.hamiltonian_terms(), k, k_split=ka)
+    WA = WA or build_mpo(prob.h0_terms(), k, k_split=ka)
+    emb = [embed_mps(prob, sub, psi) for sub, psi in subs_psis]
+    diag = [expectation(e, WH, e) - expectation(e, WA, e) - (prob.E0 + prob.E1) * overlap(e, e) for e in emb]
+    h = {}
+    cross = 0.0
+    for i in range(len(emb)):
+        for j in range(i + 1, len(emb)):
+            h[(i, j)] = expectation(emb[i], WH, emb[j])
+            cross += 2.0 * h[(i, j)]
+    return sum(diag) + cross, diag, cross, h
