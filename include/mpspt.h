@@ -134,6 +134,9 @@ typedef struct {
                                  /* done by the end of each sweep                */
     double host_wait_ms;         /* host time blocked waiting for the device     */
                                  /* (partitioned: summed over the partitions)    */
+    double e3_ms;                /* mpspt_third_order_partitioned: wall time of  */
+    long long e3_transfers;      /*   the E3 phase and its MPO transfers (0 from  */
+                                 /*   every other call)                          */
 } mpspt_report;
 
 /* Fills *opt with defaults: device 0, default stream, FP64, 30 sweeps,
@@ -244,6 +247,31 @@ mpspt_status mpspt_minimize_partitioned(mpspt_ctx* ctx, mpspt_h0 h0, int n_part,
  * Hamiltonian MPO restricted to X), by one transfer sweep. */
 mpspt_status mpspt_third_order(mpspt_ctx* ctx, mpspt_h0 h0, const mpspt_mps* psi1,
                                double* e3);
+
+/* E3 (Eq. 5) over partitions: Psi1 = sum_P Psi1^P of the listed partitions,
+ * each solved as by mpspt_minimize_partitioned (same pair_ab, M_part,
+ * n_streams and the same E2 values).  The partitions occupy disjoint
+ * virtual-occupation patterns and H0 keeps every pattern, so for P != P'
+ * <Psi1^P|Psi1^P'> = <Psi1^P|H0|Psi1^P'> = 0, while V moves up to two
+ * electrons between orbitals and couples them:
+ *   E3 = sum_P E3(Psi1^P) + 2 sum_{P < P'} <Psi1^P|H|Psi1^P'>.
+ * Every Psi1^P is written on the full chain (empty virtual orbitals pass the
+ * bond through) and each term is one float64 MPO transfer (three for the
+ * E3(Psi1^P) terms); n_part (n_part + 5) / 2 transfers in all, run
+ * concurrently on the n_streams lanes.  With all k_v (k_v + 1) / 2
+ * partitions at their exact bond dimensions this is the full-space E3.
+ * Sums are taken in a fixed order (partitions in list order, then pairs
+ * i < j row by row), so the result does not depend on n_streams.
+ * Outputs: e2_total, e3_total, e3_cross (the pair sum) are required;
+ * e2_part, e3_part (n_part doubles) and h_pair (n_part * n_part doubles,
+ * row-major, <Psi1^i|H|Psi1^j> off the diagonal and 0 on it) may be NULL.
+ * rep: the partition solves' totals plus e3_ms and e3_transfers.  The
+ * partition MPSs are freed before return. */
+mpspt_status mpspt_third_order_partitioned(mpspt_ctx* ctx, mpspt_h0 h0, int n_part,
+                                           const int* pair_ab, const int* M_part, int n_streams,
+                                           double* e2_total, double* e3_total, double* e3_cross,
+                                           double* e2_part, double* e3_part, double* h_pair,
+                                           mpspt_report* rep);
 
 void mpspt_mps_free(mpspt_mps* mps);
 

@@ -51,7 +51,8 @@ class mpspt_report(ctypes.Structure):
                 ("sigma64_flops", ctypes.c_double), ("sigma64_ms", ctypes.c_double),
                 ("learned_used", ctypes.c_longlong), ("learned_rejected", ctypes.c_longlong),
                 ("converged", ctypes.c_int), ("max_discarded_per_sweep", ctypes.c_double * 64),
-                ("sigma_calls_cum", ctypes.c_longlong * 64), ("host_wait_ms", ctypes.c_double)]
+                ("sigma_calls_cum", ctypes.c_longlong * 64), ("host_wait_ms", ctypes.c_double),
+                ("e3_ms", ctypes.c_double), ("e3_transfers", ctypes.c_longlong)]
 
 
 class MpsptError(RuntimeError):
@@ -87,6 +88,8 @@ def load():
             "mpspt_extrapolate_e2": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, dp]),
             "mpspt_minimize_partitioned": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, ip, ctypes.c_int, dp, dp,
                                                           ctypes.POINTER(mpspt_report)]),
+            "mpspt_third_order_partitioned": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip, ip, ctypes.c_int,
+                                                             dp, dp, dp, dp, dp, dp, ctypes.POINTER(mpspt_report)]),
             "mpspt_mps_free": (None, [vp]),
             "mpspt_mps_import": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(vp)]),
             "mpspt_mps_shape": (ctypes.c_int, [vp, ip, ip]),
@@ -244,6 +247,23 @@ def mpspt_minimize_partitioned(ctx, h0, pairs, Ms, n_streams=0):
                                              Ms.ctypes.data_as(ipp), n_streams, ctypes.byref(e2), _dp(ep),
                                              ctypes.byref(rep)))
     return e2.value, ep, rep
+
+
+def mpspt_third_order_partitioned(ctx, h0, pairs, Ms, n_streams=0):
+    """Returns (E2, E3, E3 cross sum, E2 per partition, E3 per partition,
+    <Psi1^i|H|Psi1^j> matrix, report)."""
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    Ms = np.ascontiguousarray(np.asarray(Ms, dtype=np.int32).reshape(-1))
+    n = len(Ms)
+    e2, e3, ex = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    e2p, e3p, hp = np.zeros(n), np.zeros(n), np.zeros((n, n))
+    rep = mpspt_report()
+    ipp = ctypes.POINTER(ctypes.c_int)
+    _check(load().mpspt_third_order_partitioned(ctx, H0.get(h0, h0), n, pairs.ctypes.data_as(ipp),
+                                                Ms.ctypes.data_as(ipp), n_streams, ctypes.byref(e2),
+                                                ctypes.byref(e3), ctypes.byref(ex), _dp(e2p), _dp(e3p), _dp(hp),
+                                                ctypes.byref(rep)))
+    return e2.value, e3.value, ex.value, e2p, e3p, hp, rep
 
 
 def mpspt_extrapolate_e2(ctx, h0, Ms):

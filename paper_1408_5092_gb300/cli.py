@@ -3,7 +3,8 @@
     python -m paper_1408_5092_gb300.cli --config medium --M 256 --h0 dyall \
         --prec mixed [--sweeps 64] [--e_tol 1e-7] [--e3] [--verbose 1]
     python -m paper_1408_5092_gb300.cli --config medium --partitions 300 \
-        [--streams 8] [--M 0]      (partitioned mode, uneven seeded M_P)
+        [--streams 8] [--M 0] [--e3]   (partitioned mode, uneven seeded M_P;
+                                        --e3 adds E3 with the cross-partition terms)
     python -m paper_1408_5092_gb300.cli --config partitions --dmrg 256 \
         --partitions 1830 --M 0    (reference by the library's DMRG at M0)
 
@@ -94,6 +95,19 @@ def main(argv=None):
             pairs = [(x, y) for x in range(kv) for y in range(x, kv)][: a.partitions]
             Ms = synthetic.partition_bond_dims(len(pairs)) if a.M <= 0 else [a.M] * len(pairs)
             t = time.time()
+            if a.e3:
+                # E3 over the listed partitions needs all of them at once
+                e2, e3, ex, ep_, e3p, _, rep = L.mpspt_third_order_partitioned(ctx, a.h0, pairs, Ms,
+                                                                               n_streams=a.streams)
+                print(json.dumps({"config": a.config, "h0": a.h0, "prec": a.prec, "partitions": len(pairs),
+                                  "M_part": "seeded from {32,...,512}" if a.M <= 0 else a.M, "E2": e2,
+                                  "E3": e3, "E3_cross": ex, "E3_diag": e3 - ex, "wall_s": time.time() - t,
+                                  "e2_phase_s": rep.wall_ms / 1e3, "e3_phase_s": rep.e3_ms / 1e3,
+                                  "e3_transfers": rep.e3_transfers,
+                                  "transfers_per_s": rep.e3_transfers / max(rep.e3_ms / 1e3, 1e-9),
+                                  "streams": a.streams, "kernel_launches": rep.kernel_launches, **ref_info}),
+                      flush=True)
+                return 0
             step = a.chunk if a.chunk > 0 else len(pairs)
             eps, cg, launches, wait = [], 0, 0, 0.0
             for c0 in range(0, len(pairs), step):   # chunks: a progress line after each

@@ -299,6 +299,35 @@ mpspt_status mpspt_minimize_partitioned(mpspt_ctx* ctx, mpspt_h0 h0, int n_part,
     });
 }
 
+mpspt_status mpspt_third_order_partitioned(mpspt_ctx* ctx, mpspt_h0 h0, int n_part, const int* pair_ab,
+                                           const int* M_part, int n_streams, double* e2_total,
+                                           double* e3_total, double* e3_cross, double* e2_part,
+                                           double* e3_part, double* h_pair, mpspt_report* rep) {
+    if (!ctx || !e2_total || !e3_total || !e3_cross || n_part < 1 || !pair_ab || !M_part)
+        return MPSPT_ERR_INVALID;
+    return guard(ctx, [&] {
+        auto& c = *ctx->c;
+        MPSPT_CUDA(cudaSetDevice(c.opt.device));
+        std::vector<std::pair<int, int>> pairs(n_part);
+        std::vector<int> Ms(M_part, M_part + n_part);
+        for (int i = 0; i < n_part; ++i) pairs[i] = {pair_ab[2 * i], pair_ab[2 * i + 1]};
+        mpspt::PartE3 o;
+        mpspt::SweepResult r;
+        mpspt::third_order_partitioned(c, h0, pairs, Ms, n_streams > 0 ? n_streams : 8, o, r);
+        if (rep) {
+            fill_report(rep, r);
+            rep->e3_ms = o.e3_ms;
+            rep->e3_transfers = o.transfers;
+        }
+        if (e2_part) for (int i = 0; i < n_part; ++i) e2_part[i] = o.e2_part[i];
+        if (e3_part) for (int i = 0; i < n_part; ++i) e3_part[i] = o.e3_part[i];
+        if (h_pair) std::copy(o.h_pair.begin(), o.h_pair.end(), h_pair);
+        *e2_total = o.e2;
+        *e3_total = o.e3;
+        *e3_cross = o.e3_cross;
+    });
+}
+
 mpspt_status mpspt_third_order(mpspt_ctx* ctx, mpspt_h0 h0, const mpspt_mps* psi1, double* e3) {
     if (!ctx || !psi1 || !e3) return MPSPT_ERR_INVALID;
     return guard(ctx, [&] {

@@ -1841,9 +1841,8 @@ Chain partition_chain(Ctx& c, int h0, int a, int b, PartOps& ops) {
     return ch;
 }
 
-double minimize_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int>>& pairs,
-                            const std::vector<int>& Ms, int n_lanes, std::vector<double>& e2_part,
-                            SweepResult& res) {
+namespace {
+void check_pairs(Ctx& c, int h0, const std::vector<std::pair<int, int>>& pairs, const std::vector<int>& Ms) {
     require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
     require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
     require(pairs.size() == Ms.size(), "one bond dimension per partition");
@@ -1852,36 +1851,25 @@ double minimize_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int
                 "partition pair out of range (need 0 <= a <= b < k_virt)");
         require(Ms[i] >= 1, "bond dimension must be >= 1");
     }
-    const auto t0 = std::chrono::steady_clock::now();
-    const long long l0 = launch_count();
-    const int n = (int)pairs.size();
-    e2_part.assign(n, 0.0);
-    // longest first: cost grows like M^3
-    std::vector<int> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return Ms[x] > Ms[y]; });
-    n_lanes = std::max(1, std::min(n_lanes, n));
-    std::vector<std::unique_ptr<Lane>> lanes;
-    for (int l = 0; l < n_lanes; ++l) lanes.emplace_back(new Lane(nullptr, true));
-    std::atomic<int> next{0};
-    std::vector<SweepResult> rs(n);
+}
+
+// Runs fn(lane, worker index) on every lane, one host thread per lane; the
+// first error of any lane is rethrown after all threads have joined (a lane
+// that fails sets stop so that the others leave their loops).
+template <class F>
+void on_lanes(Ctx& c, std::vector<std::unique_ptr<Lane>>& lanes, std::atomic<bool>& stop, F fn) {
+    const int n_lanes = (int)lanes.size();
     std::vector<std::pair<mpspt_status, std::string>> errs(n_lanes, {MPSPT_OK, ""});
     auto work = [&](int l) {
         try {
             MPSPT_CUDA(cudaSetDevice(c.opt.device));
-            for (int j; (j = next.fetch_add(1)) < n;) {
-                const int idx = order[j];
-                PartOps ops;
-                Chain ch = partition_chain(c, h0, pairs[idx].first, pairs[idx].second, ops);
-                minimize(c, ch, Ms[idx], rs[idx], lanes[l].get());
-                e2_part[idx] = rs[idx].e2;
-            }
+            fn(*lanes[l], l);
         } catch (const Error& e) {
             errs[l] = {e.status, e.what()};
-            next.store(n);
+            stop.store(true);
         } catch (const std::exception& e) {
             errs[l] = {MPSPT_ERR_INVALID, e.what()};
-            next.store(n);
+            stop.store(true);
         }
     };
     std::vector<std::thread> th;
@@ -1890,6 +1878,39 @@ double minimize_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int
     for (auto& t : th) t.join();
     for (auto& e : errs)
         if (e.first != MPSPT_OK) throw Error(e.first, e.second);
+}
+
+// The listed partitions solved concurrently on the lanes, longest first
+// (cost grows like M^3); keep (if given) receives every partition's Psi1 on
+// its own chain, its device memory ordered on the lane that made it.
+double solve_partitions(Ctx& c, int h0, const std::vector<std::pair<int, int>>& pairs,
+                        const std::vector<int>& Ms, std::vector<std::unique_ptr<Lane>>& lanes,
+                        std::vector<double>& e2_part, SweepResult& res,
+                        std::vector<std::unique_ptr<MpsD>>* keep) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = launch_count();
+    const int n = (int)pairs.size();
+    e2_part.assign(n, 0.0);
+    if (keep) {
+        keep->clear();
+        keep->resize(n);
+    }
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return Ms[x] > Ms[y]; });
+    std::atomic<int> next{0};
+    std::atomic<bool> stop{false};
+    std::vector<SweepResult> rs(n);
+    on_lanes(c, lanes, stop, [&](Lane& ln, int) {
+        for (int j; !stop.load() && (j = next.fetch_add(1)) < n;) {
+            const int idx = order[j];
+            PartOps ops;
+            Chain ch = partition_chain(c, h0, pairs[idx].first, pairs[idx].second, ops);
+            std::unique_ptr<MpsD> psi = minimize(c, ch, Ms[idx], rs[idx], &ln);
+            e2_part[idx] = rs[idx].e2;
+            if (keep) (*keep)[idx] = std::move(psi);
+        }
+    });
     double tot = 0.0;
     for (int i = 0; i < n; ++i) tot += e2_part[i];   // fixed (pair) order
     res = SweepResult();
@@ -1915,24 +1936,46 @@ double minimize_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int
     return tot;
 }
 
+std::vector<std::unique_ptr<Lane>> make_lanes(int n_lanes, int n) {
+    n_lanes = std::max(1, std::min(n_lanes, n));
+    std::vector<std::unique_ptr<Lane>> lanes;
+    for (int l = 0; l < n_lanes; ++l) lanes.emplace_back(new Lane(nullptr, true));
+    return lanes;
+}
+}  // namespace
+
+double minimize_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int>>& pairs,
+                            const std::vector<int>& Ms, int n_lanes, std::vector<double>& e2_part,
+                            SweepResult& res) {
+    check_pairs(c, h0, pairs, Ms);
+    std::vector<std::unique_ptr<Lane>> lanes = make_lanes(n_lanes, (int)pairs.size());
+    return solve_partitions(c, h0, pairs, Ms, lanes, e2_part, res, nullptr);
+}
+
 double expectation(Ctx& c, const MPO& W, const MpsD& bra, const MpsD& ket) {
+    return expectation(c, W, bra, ket, c.st);
+}
+
+double expectation(Ctx& c, const MPO& W, const MpsD& bra, const MpsD& ket, cudaStream_t st) {
+    (void)c;
+    require(bra.nsite == ket.nsite && bra.nsite == W.nsite, "bra, ket and operator lengths differ");
     EnvT L, Ln;
-    L.build(W.dq[0], bra.bond[0], ket.bond[0], c.st);
+    L.build(W.dq[0], bra.bond[0], ket.bond[0], st);
     const double one = 1.0;
-    MPSPT_CUDA(cudaMemcpyAsync(L.d.get(), &one, sizeof(double), cudaMemcpyHostToDevice, c.st));
+    MPSPT_CUDA(cudaMemcpyAsync(L.d.get(), &one, sizeof(double), cudaMemcpyHostToDevice, st));
     EnvPlan ep;
     for (int i = 0; i < bra.nsite; ++i) {
-        Ln.build(W.dq[i + 1], bra.bond[i + 1], ket.bond[i + 1], c.st);
+        Ln.build(W.dq[i + 1], bra.bond[i + 1], ket.bond[i + 1], st);
         ep.build_left(W, i, L, bra.A[i], ket.A[i], bra.bond[i], ket.bond[i], bra.bond[i + 1],
-                      ket.bond[i + 1], Ln, c.st);
-        ep.run(c.st);
-        MPSPT_CUDA(cudaStreamSynchronize(c.st));
+                      ket.bond[i + 1], Ln, st);
+        ep.run(st);
+        MPSPT_CUDA(cudaStreamSynchronize(st));
         std::swap(L, Ln);
     }
     double v = 0.0;
     if (!L.blk.empty())
-        MPSPT_CUDA(cudaMemcpyAsync(&v, L.d.get(), sizeof(double), cudaMemcpyDeviceToHost, c.st));
-    MPSPT_CUDA(cudaStreamSynchronize(c.st));
+        MPSPT_CUDA(cudaMemcpyAsync(&v, L.d.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    MPSPT_CUDA(cudaStreamSynchronize(st));
     return v;
 }
 
@@ -1942,6 +1985,130 @@ double third_order(Ctx& c, int h0, const MpsD& psi1) {
     const double eh = expectation(c, c.H_mpo(), psi1, psi1);
     const double ea = expectation(c, c.A_mpo(h0), psi1, psi1);
     return eh - ea - c.P.e_ref * n2;   // <H> - <A> - (E0 + E1) <1>
+}
+
+namespace {
+// A site that carries every bond state through an empty orbital: identity on
+// each sector of B with local state |0> (the only non-zero blocks).
+void identity_site(const Bond& B, SiteT& A, cudaStream_t st) {
+    A.blk.clear();
+    A.idx.assign((size_t)B.nsec() * 4, -1);
+    A.n = 0;
+    for (int s = 0; s < B.nsec(); ++s) {
+        A.idx[(size_t)s * 4] = (int)A.blk.size();
+        A.blk.push_back({s, 0, s, A.n});
+        A.n += (size_t)B.sec[s].dim * B.sec[s].dim;
+    }
+    A.d.alloc(A.n * sizeof(double), st);
+    std::vector<double> h(A.n, 0.0);
+    for (const auto& b : A.blk) {
+        const int d = B.sec[b.sl].dim;
+        for (int i = 0; i < d; ++i) h[b.off + (size_t)i * d + i] = 1.0;
+    }
+    if (A.n) MPSPT_CUDA(cudaMemcpyAsync(A.d.get(), h.data(), A.n * sizeof(double), cudaMemcpyHostToDevice, st));
+    MPSPT_CUDA(cudaStreamSynchronize(st));
+}
+
+void view_site(const SiteT& src, SiteT& dst) {
+    dst.blk = src.blk;
+    dst.idx = src.idx;
+    dst.n = src.n;
+    dst.d.make_view(src.d.get(), src.n * sizeof(double));
+}
+}  // namespace
+
+// Psi1 of partition (a, b), given on its chain (active sites, then a, then b
+// if b != a), written on the full chain.  The active sites and the
+// partition's virtual sites are views of its tensors; every other virtual
+// orbital is an empty site that passes the bond through.  The chain keeps the
+// orbitals' relative order and an empty site has even parity, so the state is
+// the same vector of the full determinant space.
+void embed_partition(const Problem& P, const MpsD& part, int a, int b, MpsD& out, cudaStream_t st) {
+    require(part.nsite == P.ka + (a == b ? 1 : 2), "partition MPS length differs from its chain");
+    out.nsite = P.k;
+    out.bond.assign(part.bond.begin(), part.bond.begin() + P.ka + 1);
+    out.A.clear();
+    out.A.resize(P.k);
+    for (int s = 0; s < P.ka; ++s) view_site(part.A[s], out.A[s]);
+    int j = P.ka;   // next site of the partition chain
+    for (int v = 0; v < P.kv; ++v) {
+        const int want = (j == P.ka) ? a : b;
+        if (j < part.nsite && v == want) {
+            view_site(part.A[j], out.A[P.ka + v]);
+            out.bond.push_back(part.bond[j + 1]);
+            ++j;
+        } else {
+            const Bond B = out.bond.back();
+            identity_site(B, out.A[P.ka + v], st);
+            out.bond.push_back(B);
+        }
+    }
+    require(j == part.nsite, "partition sites not all placed");
+}
+
+double third_order_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int>>& pairs,
+                               const std::vector<int>& Ms, int n_lanes, PartE3& out, SweepResult& res) {
+    check_pairs(c, h0, pairs, Ms);
+    const int n = (int)pairs.size();
+    std::vector<std::unique_ptr<Lane>> lanes = make_lanes(n_lanes, std::max(n, n * (n - 1) / 2));
+    std::vector<std::unique_ptr<MpsD>> psi;   // destroyed before the lanes it was made on
+    out.e2 = solve_partitions(c, h0, pairs, Ms, lanes, out.e2_part, res, &psi);
+    for (auto& l : lanes) MPSPT_CUDA(cudaStreamSynchronize(l->st));
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = launch_count();
+    // operators of the E3 phase, built here before the lanes share them
+    const MPO& WH = c.H_mpo();
+    const MPO& WA = c.A_mpo(h0);
+    const MPO& WI = c.I_mpo();
+    std::vector<MpsD> emb(n);
+    for (int i = 0; i < n; ++i) embed_partition(c.P, *psi[i], pairs[i].first, pairs[i].second, emb[i], c.st);
+    MPSPT_CUDA(cudaStreamSynchronize(c.st));
+    // tasks: (i, i) = E3 of partition i (three transfers), (i, j) i < j =
+    // <Psi1^i|H|Psi1^j> (one transfer); the costliest (largest M_i M_j) first
+    struct Task { int i, j; long long w; };
+    std::vector<Task> tasks;
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) tasks.push_back({i, j, (long long)Ms[i] * Ms[j] * (i == j ? 3 : 1)});
+    std::stable_sort(tasks.begin(), tasks.end(), [](const Task& x, const Task& y) { return x.w > y.w; });
+    std::vector<double> val(tasks.size(), 0.0);
+    std::atomic<int> next{0};
+    std::atomic<bool> stop{false};
+    on_lanes(c, lanes, stop, [&](Lane& ln, int) {
+        RingScope rs(ln.ring.get());
+        for (int t; !stop.load() && (t = next.fetch_add(1)) < (int)tasks.size();) {
+            const Task& k = tasks[t];
+            if (k.i == k.j) {
+                const MpsD& x = emb[k.i];
+                const double n2 = expectation(c, WI, x, x, ln.st);
+                const double eh = expectation(c, WH, x, x, ln.st);
+                const double ea = expectation(c, WA, x, x, ln.st);
+                val[t] = eh - ea - c.P.e_ref * n2;   // <H> - <A> - (E0 + E1) <1>
+            } else {
+                val[t] = expectation(c, WH, emb[k.i], emb[k.j], ln.st);
+            }
+        }
+        MPSPT_CUDA(cudaStreamSynchronize(ln.st));
+    });
+    out.e3_part.assign(n, 0.0);
+    out.h_pair.assign((size_t)n * n, 0.0);
+    for (size_t t = 0; t < tasks.size(); ++t) {
+        const Task& k = tasks[t];
+        if (k.i == k.j) out.e3_part[k.i] = val[t];
+        else out.h_pair[(size_t)k.i * n + k.j] = out.h_pair[(size_t)k.j * n + k.i] = val[t];
+    }
+    // sums in a fixed order: partitions, then pairs (i < j) row by row
+    out.e3_cross = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) out.e3_cross += 2.0 * out.h_pair[(size_t)i * n + j];
+    double diag = 0.0;
+    for (int i = 0; i < n; ++i) diag += out.e3_part[i];
+    out.e3 = diag + out.e3_cross;
+    out.transfers = 3LL * n + (long long)n * (n - 1) / 2;
+    out.e3_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    res.launches += launch_count() - l0;
+    emb.clear();
+    MPSPT_CUDA(cudaStreamSynchronize(c.st));
+    return out.e3;
 }
 
 void local_apply(Ctx& c, int h0, const MpsD& psi1_in, int i, int op, const double* xh, double* out) {

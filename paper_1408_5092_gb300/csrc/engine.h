@@ -146,7 +146,23 @@ std::unique_ptr<MpsD> minimize(Ctx& c, int h0, int M, SweepResult& res);
 // the result as the reference and returns it (active sites only).
 std::unique_ptr<MpsD> ground_state(Ctx& c, int M0, double s2_penalty, SweepResult& res);
 double expectation(Ctx& c, const MPO& W, const MpsD& bra, const MpsD& ket);
+double expectation(Ctx& c, const MPO& W, const MpsD& bra, const MpsD& ket, cudaStream_t st);
 double third_order(Ctx& c, int h0, const MpsD& psi1);
+
+// E3 (Eq. 5) of Psi1 = sum of the listed partitions' Psi1: the partitions
+// are solved as in minimize_partitioned, kept, written on the full chain, and
+//   E3 = sum_P E3(Psi1^P) + 2 sum_{P < P'} <Psi1^P|H|Psi1^P'>
+// (partitions are orthogonal and H0 keeps every virtual occupation, so the
+// cross terms of H0 and of the norm vanish).
+struct PartE3 {
+    double e2 = 0.0, e3 = 0.0, e3_cross = 0.0, e3_ms = 0.0;
+    long long transfers = 0;
+    std::vector<double> e2_part, e3_part;
+    std::vector<double> h_pair;   // n x n, <Psi1^i|H|Psi1^j> off the diagonal, 0 on it
+};
+double third_order_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, int>>& pairs,
+                               const std::vector<int>& Ms, int n_lanes, PartE3& out, SweepResult& res);
+void embed_partition(const Problem& P, const MpsD& part, int a, int b, MpsD& out, cudaStream_t st);
 void local_apply(Ctx& c, int h0, const MpsD& psi1, int i, int op, const double* x, double* out);
 
 std::unique_ptr<MpsD> mps_upload(const MpsHost& h, cudaStream_t st);

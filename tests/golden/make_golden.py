@@ -74,6 +74,28 @@ def medium_partitions(M, h0, pairs):
     return out
 
 
+def medium_partition_e3(M, h0, pairs):
+    """E3 of the sum of a few medium partitions' MPS-PT2 solutions (Eq. 5 over
+    partitions, transfer route of oracle/partition.py), with every partition's
+    E2, E3 and the pair elements <Psi1^i|H|Psi1^j>."""
+    from oracle.mpo import build_mpo
+    from oracle.partition import partition_e3_mps, partition_psi1
+    h, L, c, ci = synthetic.config_reference("medium")
+    p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
+    t = time.time()
+    sp = partition_psi1(p, pairs, lambda a, b: M)
+    t_sweeps = time.time() - t
+    WH = build_mpo(p.hamiltonian_terms(), p.k, k_split=p.k_act)
+    t = time.time()
+    e3, diag, cross, hh = partition_e3_mps(p, [(s, m) for s, _, m in sp], WH=WH)
+    out = {"config": "medium", "h0": h0, "M": M, "pairs": [list(x) for x in pairs],
+           "E2_part": [e for _, e, _ in sp], "E3": e3, "E3_part": diag, "E3_cross": cross,
+           "H_pair": [[i, j, v] for (i, j), v in sorted(hh.items())],
+           "oracle_sweeps_s": t_sweeps, "oracle_e3_s": time.time() - t, "blas_threads": THREADS}
+    print(out, flush=True)
+    return out
+
+
 def medium(M, h0, sweeps, out_name):
     """Sweep history at bond dimension M; the file is rewritten after every
     sweep (with E3 of the state at that point), so a long run leaves usable
@@ -128,6 +150,9 @@ if __name__ == "__main__":
     elif what == "medium_partitions":
         res = medium_partitions(16, "fock", [(0, 0), (3, 17), (23, 23)])
         name = "oracle_medium_partitions_fock_M16.json"
+    elif what == "medium_partition_e3":
+        res = medium_partition_e3(16, "fock", [(0, 0), (0, 1), (1, 5), (5, 5), (23, 23)])
+        name = "oracle_medium_partition_e3_fock_M16.json"
     else:
         M = int(what.replace("medium", ""))
         h0 = sys.argv[2] if len(sys.argv) > 2 else "fock"

@@ -61,6 +61,8 @@ def test_null_arguments_are_rejected():
     assert lib.mpspt_minimize_hylleraas(None, 0, 16, None, None, None) == inv
     assert lib.mpspt_minimize_partitioned(None, 0, 1, None, None, 1, None, None, None) == inv
     assert lib.mpspt_third_order(None, 0, None, None) == inv
+    assert lib.mpspt_third_order_partitioned(None, 0, 1, None, None, 1, None, None, None,
+                                             None, None, None, None) == inv
     assert lib.mpspt_local_apply(None, 0, None, 0, 0, None, None) == inv
     assert lib.mpspt_mps_shape(None, None, None) == inv
     assert lib.mpspt_mps_export(None, None, None) == inv
