@@ -82,7 +82,9 @@ typedef struct {
     double cg_tol;              /* relative residual |r| <= cg_tol |g|          */
     int cg_max_iter;            /* per local solve                              */
     unsigned long long seed;    /* initial Psi1 (counter-based, see below)      */
-    int use_learned;            /* learned block preconditioner (0 = Jacobi)    */
+    int use_learned;            /* learned block preconditioner (0 = Jacobi);   */
+                                /* full-space calls only: partitioned calls     */
+                                /* keep the Jacobi start on every lane          */
     int verbose;                /* 1: one line per sweep on stderr              */
     int eig_fp64_only;          /* density-matrix eigensolver: 0 (default) =    */
                                 /* float32 Jacobi start, float64 Newton-Schulz  */
@@ -135,8 +137,13 @@ typedef struct {
     double host_wait_ms;         /* host time blocked waiting for the device     */
                                  /* (partitioned: summed over the partitions)    */
     double e3_ms;                /* mpspt_third_order_partitioned: wall time of  */
-    long long e3_transfers;      /*   the E3 phase and its MPO transfers (0 from  */
-                                 /*   every other call)                          */
+    long long e3_transfers;      /*   the E3 transfers, their number, the host   */
+    double e3_wait_ms;           /*   time the lanes spent waiting for the device */
+    double e3_flops;             /*   (summed over lanes), the float64 GEMM flops */
+    double e3_plan_bytes;        /*   and task-list bytes of the transfers, and  */
+    double e3_setup_ms;          /*   the wall time of building the operators    */
+                                 /*   (the full H MPO once per context); 0 from  */
+                                 /*   every other call                           */
 } mpspt_report;
 
 /* Fills *opt with defaults: device 0, default stream, FP64, 30 sweeps,

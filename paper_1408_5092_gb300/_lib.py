@@ -52,7 +52,9 @@ class mpspt_report(ctypes.Structure):
                 ("learned_used", ctypes.c_longlong), ("learned_rejected", ctypes.c_longlong),
                 ("converged", ctypes.c_int), ("max_discarded_per_sweep", ctypes.c_double * 64),
                 ("sigma_calls_cum", ctypes.c_longlong * 64), ("host_wait_ms", ctypes.c_double),
-                ("e3_ms", ctypes.c_double), ("e3_transfers", ctypes.c_longlong)]
+                ("e3_ms", ctypes.c_double), ("e3_transfers", ctypes.c_longlong), ("e3_wait_ms", ctypes.c_double),
+                ("e3_flops", ctypes.c_double), ("e3_plan_bytes", ctypes.c_double),
+                ("e3_setup_ms", ctypes.c_double)]
 
 
 class MpsptError(RuntimeError):

@@ -102,8 +102,11 @@ def main(argv=None):
                 print(json.dumps({"config": a.config, "h0": a.h0, "prec": a.prec, "partitions": len(pairs),
                                   "M_part": "seeded from {32,...,512}" if a.M <= 0 else a.M, "E2": e2,
                                   "E3": e3, "E3_cross": ex, "E3_diag": e3 - ex, "wall_s": time.time() - t,
-                                  "e2_phase_s": rep.wall_ms / 1e3, "e3_phase_s": rep.e3_ms / 1e3,
-                                  "e3_transfers": rep.e3_transfers,
+                                  "e2_phase_s": rep.wall_ms / 1e3, "e3_setup_s": rep.e3_setup_ms / 1e3,
+                                  "e3_transfers_s": rep.e3_ms / 1e3,
+                                  "e3_transfers": rep.e3_transfers, "e3_lane_wait_s": rep.e3_wait_ms / 1e3,
+                                  "e3_gflop": rep.e3_flops / 1e9, "e3_plan_mb": rep.e3_plan_bytes / 1e6,
+                                  "e3_fp64_tflops": rep.e3_flops / max(rep.e3_ms * 1e-3, 1e-9) / 1e12,
                                   "transfers_per_s": rep.e3_transfers / max(rep.e3_ms / 1e3, 1e-9),
                                   "streams": a.streams, "kernel_launches": rep.kernel_launches, **ref_info}),
                       flush=True)

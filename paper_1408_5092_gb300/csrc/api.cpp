@@ -318,6 +318,10 @@ mpspt_status mpspt_third_order_partitioned(mpspt_ctx* ctx, mpspt_h0 h0, int n_pa
             fill_report(rep, r);
             rep->e3_ms = o.e3_ms;
             rep->e3_transfers = o.transfers;
+            rep->e3_wait_ms = o.wait_ms;
+            rep->e3_flops = o.flops;
+            rep->e3_plan_bytes = o.plan_bytes;
+            rep->e3_setup_ms = o.setup_ms;
         }
         if (e2_part) for (int i = 0; i < n_part; ++i) e2_part[i] = o.e2_part[i];
         if (e3_part) for (int i = 0; i < n_part; ++i) e3_part[i] = o.e3_part[i];

@@ -13,6 +13,8 @@
 
 #include "hostla.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace mpspt {
 
 // ------------------------------------------------------------------ context
@@ -1547,19 +1549,25 @@ struct Sweeper {
         dia.run(ln.st);
         make_minv(w.minv.as<double>(), w.dg.as<double>(), n, ln.st);
         vec_scale_mask(w.b.as<double>(), w.g.as<double>(), -1.0, n, ln.st);
-        const bool learn = (c.net != nullptr && c.opt.use_learned) || c.harvesting;
+        // the network and the harvest are the context's, on its own stream:
+        // only a solve on the context's lane uses them (partition lanes, which
+        // run concurrently on their own streams, keep the plain start)
+        const bool main_lane = &ln == c.lane0.get();
+        const bool use_net = main_lane && c.net != nullptr && c.opt.use_learned && !c.harvesting;
+        const bool harvest_here = main_lane && c.harvesting;
+        const bool learn = use_net || harvest_here;
         if (learn) block_prepare(i);
-        if (c.harvesting)
+        if (harvest_here)
             MPSPT_CUDA(cudaMemcpyAsync(w.xw.get(), x, n * sizeof(double), cudaMemcpyDeviceToDevice, ln.st));
         if (lo_kind != GEMM_F64)
             sig_lo.build(oA, X, X, bL, bL, bR, bR, LA[i], RA[i + 2], WA.dq[i + 2], w.p.as<double>(),
                          w.Ap.as<double>(), ln.st);
         h_sig += since(th);
         if (c.opt.verbose >= 2) { MPSPT_CUDA(cudaStreamSynchronize(ln.st)); t_plan += since(t0); t0 = clk::now(); }
-        if (c.net != nullptr && c.opt.use_learned && !c.harvesting) learned_guess(n);
+        if (use_net) learned_guess(n);
         const double h = (lo_kind == GEMM_F64) ? solve_plain(n) : solve_refined(n);
         check_tc();
-        if (c.harvesting) harvest(n);
+        if (harvest_here) harvest(n);
         if (c.opt.verbose >= 2) { t_solve += since(t0); t0 = clk::now(); }
         th = clk::now();
         const double w0 = split_wait;
@@ -1842,6 +1850,11 @@ Chain partition_chain(Ctx& c, int h0, int a, int b, PartOps& ops) {
 }
 
 namespace {
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 void check_pairs(Ctx& c, int h0, const std::vector<std::pair<int, int>>& pairs, const std::vector<int>& Ms) {
     require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
     require(h0 == MPSPT_H0_FOCK || h0 == MPSPT_H0_DYALL, "unknown H0");
@@ -1979,6 +1992,107 @@ double expectation(Ctx& c, const MPO& W, const MpsD& bra, const MpsD& ket, cudaS
     return v;
 }
 
+// <bra|W|ket> where the sites flagged in `empty` are identity sites (local
+// state |0>) in both bra and ket: each maximal run of them is one sparse map
+// of MPO states (one mix launch), the other sites the full transfer.  Only
+// MPO states on some path from the left boundary to the right one are
+// carried: a state that needs an operator on an empty site dies there, and
+// a complementary operator that still needs one is never started.  On the
+// medium chain that keeps about 1/6 of the states deep in the virtual region
+// and 1/8 to 2/3 of them in the active region.
+// Buffers of the transfers one lane runs in turn: environments, plan task
+// lists and scratch keep their device memory from one transfer to the next
+// (all on the lane's stream), so a transfer makes no allocation once they
+// have grown.
+struct XferWs {
+    EnvT L, Ln;
+    EnvPlan ep;
+};
+
+double expectation_runs(XferWs& ws, const MPO& W, RunMaps& rm, const MpsD& bra, const MpsD& ket,
+                        const std::vector<char>& empty, cudaStream_t st, double* wait_ms, double* flops,
+                        double* plan_bytes) {
+    const int ns = bra.nsite;
+    require(ket.nsite == ns && W.nsite == ns && (int)empty.size() == ns,
+            "bra, ket, operator and site mask lengths differ");
+    // segments: single sites and maximal runs of empty sites
+    struct Seg { int i, j; const RunMap* T; };
+    std::vector<Seg> seg;
+    for (int i = 0; i < ns;) {
+        int j = i + 1;
+        if (empty[i]) {
+            while (j < ns && empty[j]) ++j;
+            seg.push_back({i, j, &rm.get(i, j)});
+        } else {
+            seg.push_back({i, j, nullptr});
+        }
+        i = j;
+    }
+    // states that can still reach the right boundary, at every segment's right cut
+    const int ng = (int)seg.size();
+    std::vector<std::vector<char>> back(ng + 1);
+    back[ng].assign(W.dim[ns], 1);
+    for (int g = ng - 1; g >= 0; --g) {
+        const Seg& S = seg[g];
+        back[g].assign(W.dim[S.i], 0);
+        if (S.T) {
+            for (int b = 0; b < W.dim[S.j]; ++b)
+                if (back[g + 1][b])
+                    for (int q = S.T->ptr[b]; q < S.T->ptr[b + 1]; ++q) back[g][S.T->col[q]] = 1;
+        } else {
+            const auto &ip = W.in_ptr[S.i], &ix = W.in_idx[S.i];
+            for (int b = 0; b < W.dim[S.j]; ++b)
+                if (back[g + 1][b])
+                    for (int q = ip[b]; q < ip[b + 1]; ++q) back[g][W.W[S.i][ix[q]].a] = 1;
+        }
+    }
+    EnvT &L = ws.L, &Ln = ws.Ln;
+    EnvPlan& ep = ws.ep;
+    std::vector<char> live = back[0], nlive;
+    L.build(W.dq[0], bra.bond[0], ket.bond[0], st, &live, true);
+    const double one = 1.0;
+    if (!L.blk.empty())
+        MPSPT_CUDA(cudaMemcpyAsync(L.d.get(), &one, sizeof(double), cudaMemcpyHostToDevice, st));
+    for (int g = 0; g < ng; ++g) {
+        const Seg& S = seg[g];
+        const std::vector<char>& bk = back[g + 1];
+        nlive.assign(W.dim[S.j], 0);
+        if (S.T) {
+            for (int b = 0; b < W.dim[S.j]; ++b)
+                if (bk[b])
+                    for (int q = S.T->ptr[b]; q < S.T->ptr[b + 1] && !nlive[b]; ++q) nlive[b] = live[S.T->col[q]];
+            Ln.build(W.dq[S.j], bra.bond[S.j], ket.bond[S.j], st, &nlive, true);
+            ep.build_left_run(*S.T, L, bra.bond[S.i], ket.bond[S.i], Ln, st);
+        } else {
+            const auto& op = W.out_ptr[S.i];
+            for (int a = 0; a < W.dim[S.i]; ++a)
+                if (live[a])
+                    for (int q = op[a]; q < op[a + 1]; ++q) {
+                        const int b = W.W[S.i][q].b;
+                        if (bk[b]) nlive[b] = 1;
+                    }
+            Ln.build(W.dq[S.j], bra.bond[S.j], ket.bond[S.j], st, &nlive, true);
+            ep.build_left(W, S.i, L, bra.A[S.i], ket.A[S.i], bra.bond[S.i], ket.bond[S.i], bra.bond[S.j],
+                          ket.bond[S.j], Ln, st);
+        }
+        live.swap(nlive);
+        if (flops) *flops += ep.flops();
+        if (plan_bytes) *plan_bytes += (double)ep.plan_bytes();
+        // no host wait between segments: every buffer the next plan replaces
+        // is released stream-ordered, so the host plans the next segment
+        // while the device still runs this one
+        ep.run(st);
+        std::swap(L, Ln);
+    }
+    double v = 0.0;
+    if (!L.blk.empty())
+        MPSPT_CUDA(cudaMemcpyAsync(&v, L.d.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    const auto tw = std::chrono::steady_clock::now();
+    MPSPT_CUDA(cudaStreamSynchronize(st));
+    if (wait_ms) *wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tw).count();
+    return v;
+}
+
 double third_order(Ctx& c, int h0, const MpsD& psi1) {
     require(c.P.have_ref, "mpspt_set_reference must come first", MPSPT_ERR_STATE);
     const double n2 = expectation(c, c.I_mpo(), psi1, psi1);
@@ -2054,15 +2168,29 @@ double third_order_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, 
     std::vector<std::unique_ptr<MpsD>> psi;   // destroyed before the lanes it was made on
     out.e2 = solve_partitions(c, h0, pairs, Ms, lanes, out.e2_part, res, &psi);
     for (auto& l : lanes) MPSPT_CUDA(cudaStreamSynchronize(l->st));
-    const auto t0 = std::chrono::steady_clock::now();
-    const long long l0 = launch_count();
-    // operators of the E3 phase, built here before the lanes share them
+    // operators of the E3 phase, built here before the lanes share them (the
+    // full H MPO is built once per context: seconds on the medium chain)
+    const auto ts = std::chrono::steady_clock::now();
     const MPO& WH = c.H_mpo();
     const MPO& WA = c.A_mpo(h0);
     const MPO& WI = c.I_mpo();
+    RunMaps rmH(WH), rmA(WA), rmI(WI);
+    const auto t0 = std::chrono::steady_clock::now();
+    out.setup_ms = std::chrono::duration<double, std::milli>(t0 - ts).count();
+    const long long l0 = launch_count();
     std::vector<MpsD> emb(n);
     for (int i = 0; i < n; ++i) embed_partition(c.P, *psi[i], pairs[i].first, pairs[i].second, emb[i], c.st);
     MPSPT_CUDA(cudaStreamSynchronize(c.st));
+    // sites that are empty in both partitions of a term
+    auto empty_mask = [&](int i, int j) {
+        std::vector<char> m(c.P.k, 0);
+        for (int v = 0; v < c.P.kv; ++v) m[c.P.ka + v] = 1;
+        for (int q : {i, j}) {
+            m[c.P.ka + pairs[q].first] = 0;
+            m[c.P.ka + pairs[q].second] = 0;
+        }
+        return m;
+    };
     // tasks: (i, i) = E3 of partition i (three transfers), (i, j) i < j =
     // <Psi1^i|H|Psi1^j> (one transfer); the costliest (largest M_i M_j) first
     struct Task { int i, j; long long w; };
@@ -2073,22 +2201,36 @@ double third_order_partitioned(Ctx& c, int h0, const std::vector<std::pair<int, 
     std::vector<double> val(tasks.size(), 0.0);
     std::atomic<int> next{0};
     std::atomic<bool> stop{false};
-    on_lanes(c, lanes, stop, [&](Lane& ln, int) {
+    std::vector<double> wait(lanes.size(), 0.0), fl(lanes.size(), 0.0), pb(lanes.size(), 0.0);
+    on_lanes(c, lanes, stop, [&](Lane& ln, int l) {
         RingScope rs(ln.ring.get());
+        NvtxRange nr("mpspt_e3_transfers");   // lets a profiler select this phase's kernels
+        XferWs ws;
+        ws.ep.set_tuner(c.tuner.get());
+        double* w = &wait[l];
+        double* f = &fl[l];
+        double* b = &pb[l];
         for (int t; !stop.load() && (t = next.fetch_add(1)) < (int)tasks.size();) {
             const Task& k = tasks[t];
+            const std::vector<char> m = empty_mask(k.i, k.j);
             if (k.i == k.j) {
                 const MpsD& x = emb[k.i];
-                const double n2 = expectation(c, WI, x, x, ln.st);
-                const double eh = expectation(c, WH, x, x, ln.st);
-                const double ea = expectation(c, WA, x, x, ln.st);
+                const double n2 = expectation_runs(ws, WI, rmI, x, x, m, ln.st, w, f, b);
+                const double eh = expectation_runs(ws, WH, rmH, x, x, m, ln.st, w, f, b);
+                const double ea = expectation_runs(ws, WA, rmA, x, x, m, ln.st, w, f, b);
                 val[t] = eh - ea - c.P.e_ref * n2;   // <H> - <A> - (E0 + E1) <1>
             } else {
-                val[t] = expectation(c, WH, emb[k.i], emb[k.j], ln.st);
+                val[t] = expectation_runs(ws, WH, rmH, emb[k.i], emb[k.j], m, ln.st, w, f, b);
             }
         }
         MPSPT_CUDA(cudaStreamSynchronize(ln.st));
     });
+    out.wait_ms = out.flops = out.plan_bytes = 0.0;
+    for (size_t l = 0; l < lanes.size(); ++l) {
+        out.wait_ms += wait[l];
+        out.flops += fl[l];
+        out.plan_bytes += pb[l];
+    }
     out.e3_part.assign(n, 0.0);
     out.h_pair.assign((size_t)n * n, 0.0);
     for (size_t t = 0; t < tasks.size(); ++t) {

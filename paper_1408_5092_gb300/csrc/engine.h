@@ -155,7 +155,12 @@ double third_order(Ctx& c, int h0, const MpsD& psi1);
 // (partitions are orthogonal and H0 keeps every virtual occupation, so the
 // cross terms of H0 and of the norm vanish).
 struct PartE3 {
-    double e2 = 0.0, e3 = 0.0, e3_cross = 0.0, e3_ms = 0.0;
+    double e2 = 0.0, e3 = 0.0, e3_cross = 0.0;
+    double setup_ms = 0.0;        // operators of the E3 phase (H, H0 - E0, 1 MPOs and run maps)
+    double e3_ms = 0.0;           // the transfers
+    double wait_ms = 0.0;         // E3 phase: host time blocked on the device, summed over lanes
+    double flops = 0.0;           // E3 phase: float64 GEMM flops of the transfers
+    double plan_bytes = 0.0;      // E3 phase: task-list bytes uploaded
     long long transfers = 0;
     std::vector<double> e2_part, e3_part;
     std::vector<double> h_pair;   // n x n, <Psi1^i|H|Psi1^j> off the diagonal, 0 on it

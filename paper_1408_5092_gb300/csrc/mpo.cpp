@@ -277,7 +277,28 @@ MPO build_mpo(const std::vector<Term>& terms, int nsite, int k_split) {
         });
     }
     out.ops = tab.mats;
+    out.index();
     return out;
+}
+
+void MPO::index() {
+    out_ptr.assign(nsite, {});
+    in_ptr.assign(nsite, {});
+    in_idx.assign(nsite, {});
+    for (int p = 0; p < nsite; ++p) {
+        const auto& E = W[p];
+        out_ptr[p].assign(dim[p] + 1, 0);
+        in_ptr[p].assign(dim[p + 1] + 1, 0);
+        for (const auto& e : E) {
+            ++out_ptr[p][e.a + 1];
+            ++in_ptr[p][e.b + 1];
+        }
+        for (int a = 0; a < dim[p]; ++a) out_ptr[p][a + 1] += out_ptr[p][a];
+        for (int b = 0; b < dim[p + 1]; ++b) in_ptr[p][b + 1] += in_ptr[p][b];
+        in_idx[p].resize(E.size());
+        std::vector<int> fill(in_ptr[p].begin(), in_ptr[p].end() - 1);
+        for (int q = 0; q < (int)E.size(); ++q) in_idx[p][fill[E[q].b]++] = q;
+    }
 }
 
 void add_one_body(std::vector<Term>& out, const std::vector<double>& t, int k,

@@ -30,8 +30,13 @@ struct MPO {
     int nsite = 0;
     std::vector<int> dim;                    // states per cut, cut = 0..nsite
     std::vector<std::vector<QN>> dq;         // QN change carried by each state
-    std::vector<std::vector<MpoEntry>> W;    // per site
+    std::vector<std::vector<MpoEntry>> W;    // per site, sorted by (a, b)
     std::vector<Mat4> ops;                   // local operator table
+    // Entry indices of each site by source state (W[p][out_ptr[p][a] ..
+    // out_ptr[p][a+1]]) and by target state (in_idx[p][in_ptr[p][b] ..
+    // in_ptr[p][b+1]], in increasing a); filled by index().
+    std::vector<std::vector<int>> out_ptr, in_ptr, in_idx;
+    void index();
 };
 
 // Builds the MPO of sum(terms) on nsite sites.  Sites >= k_split are the

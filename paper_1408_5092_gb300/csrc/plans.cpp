@@ -146,6 +146,26 @@ void GemmPlan::upload(cudaStream_t st) {
     mpspt::upload(dtasks, tasks, st);
 }
 
+void Autotuner::RawBuf::ensure(size_t bytes) {
+    if (bytes <= n) return;
+    const size_t want = std::max(bytes, 2 * n);
+    if (p) old.push_back(p);
+    p = nullptr;
+    n = 0;
+    MPSPT_CUDA(cudaMalloc(&p, want));
+    Registry::get().add(p, want);
+    n = want;
+}
+
+Autotuner::RawBuf::~RawBuf() {
+    old.push_back(p);
+    for (void* q : old)
+        if (q) {
+            Registry::get().remove(q);
+            cudaFree(q);
+        }
+}
+
 Autotuner::~Autotuner() {
     for (auto& e : ev)
         if (e) cudaEventDestroy(e);
@@ -179,7 +199,7 @@ std::pair<int, int> Autotuner::choose(const GemmPlan& g, cudaStream_t st) {
         MPSPT_CUDA(cudaEventCreate(&ev[0]));
         MPSPT_CUDA(cudaEventCreate(&ev[1]));
     }
-    scratch.ensure(cmax * sizeof(double) + 16, st);
+    scratch.ensure(cmax * sizeof(double) + 16);
     std::pair<int, int> win{cand[0][0], cand[0][1]};
     float tbest = 1e30f;
     std::vector<GemmTask> tt;
@@ -187,18 +207,19 @@ std::pair<int, int> Autotuner::choose(const GemmPlan& g, cudaStream_t st) {
         g.split(cand[c][0], cand[c][1], tt, nullptr);
         order_tasks(tt, nullptr, g.ops);
         for (auto& t : tt) {   // outputs go to scratch: dense m x n, no map; operands are the plan's
-            t.C = scratch.as<double>();
+            t.C = static_cast<double*>(scratch.p);
             t.ldc = t.n;
             t.cmap = nullptr;
             t.cmap_rows = 0;
         }
-        mpspt::upload(dtasks, tt, st);
+        dtasks.ensure(tt.size() * sizeof(GemmTask) + 16);
+        const GemmTask* dt = static_cast<const GemmTask*>(dtasks.p);
+        if (!tt.empty()) copy_h2d(dtasks.p, tt.data(), tt.size() * sizeof(GemmTask), st);
         const bool f32 = g.kind == GEMM_F32;
-        launch_gemm_tile(cand[c][0], cand[c][1], f32, dtasks.as<GemmTask>(), (int)tt.size(), g.dops.as<GemmOp>(), st);
+        launch_gemm_tile(cand[c][0], cand[c][1], f32, dt, (int)tt.size(), g.dops.as<GemmOp>(), st);
         MPSPT_CUDA(cudaEventRecord(ev[0], st));
         for (int r = 0; r < 3; ++r)
-            launch_gemm_tile(cand[c][0], cand[c][1], f32, dtasks.as<GemmTask>(), (int)tt.size(), g.dops.as<GemmOp>(),
-                             st);
+            launch_gemm_tile(cand[c][0], cand[c][1], f32, dt, (int)tt.size(), g.dops.as<GemmOp>(), st);
         MPSPT_CUDA(cudaEventRecord(ev[1], st));
         MPSPT_CUDA(cudaEventSynchronize(ev[1]));
         float ms_ = 0.f;
@@ -569,14 +590,21 @@ void EnvPlan::build_left(const MPO& W, int site, const EnvT& L, const SiteT& Abr
         g1.block(Yp + yoff[kb], nd, P, nd, 0, m0);
     }
     // mix: Z_(out, s) over the MPO entries e = (a -> b) and t
-    std::vector<std::vector<const MpoEntry*>> by_b(W.dim[site + 1]);
-    for (const auto& e : W.W[site]) by_b[e.b].push_back(&e);
+    const std::vector<MpoEntry>& We = W.W[site];
+    const std::vector<int>&in_ptr = W.in_ptr[site], &in_idx = W.in_idx[site];
     struct ZB { int nb, s, bb; size_t off; int rows, cols; };
     std::vector<ZB> zb;
     size_t zs = 0;
     for (int nbi = 0; nbi < (int)Lnew.blk.size(); ++nbi) {
         const auto& nb = Lnew.blk[nbi];
         const int nd = ketR.sec[nb.sk].dim;
+        // ket-side lookups depend on t only
+        int slk_t[4], kb_t[4];
+        for (int t = 0; t < 4; ++t) {
+            slk_t[t] = ketL.find(ketR.sec[nb.sk].q - site_qn(t));
+            kb_t[t] = slk_t[t] < 0 ? -1 : Aket.find(slk_t[t], t);
+            if (kb_t[t] >= 0 && (Aket.blk[kb_t[t]].sr != nb.sk || yoff[kb_t[t]] < 0)) kb_t[t] = -1;
+        }
         for (int s = 0; s < 4; ++s) {
             const int slb = braL.find(braR.sec[nb.sb].q - site_qn(s));
             if (slb < 0) continue;
@@ -584,18 +612,15 @@ void EnvPlan::build_left(const MPO& W, int site, const EnvT& L, const SiteT& Abr
             if (bb < 0 || Abra.blk[bb].sr != nb.sb) continue;
             const int rows = braL.sec[slb].dim;
             const int s0 = (int)ms.size();
-            for (const MpoEntry* e : by_b[nb.a]) {
+            for (int q = in_ptr[nb.a]; q < in_ptr[nb.a + 1]; ++q) {
+                const MpoEntry* e = &We[in_idx[q]];
                 const Mat4& op = W.ops[e->op];
                 for (int t = 0; t < 4; ++t) {
                     const double v = op[s * 4 + t];
-                    if (v == 0.0) continue;
-                    const int slk = ketL.find(ketR.sec[nb.sk].q - site_qn(t));
-                    if (slk < 0) continue;
-                    const int kb = Aket.find(slk, t);
-                    if (kb < 0 || Aket.blk[kb].sr != nb.sk || yoff[kb] < 0) continue;
-                    const int lb = L.find(e->a, slk);
+                    if (v == 0.0 || kb_t[t] < 0) continue;
+                    const int lb = L.find(e->a, slk_t[t]);
                     if (lb < 0 || L.blk[lb].sb != slb) continue;
-                    ms.push_back({Yp + yoff[kb] + (size_t)L.blk[lb].roff * nd, nd, 0, e->coef * v});
+                    ms.push_back({Yp + yoff[kb_t[t]] + (size_t)L.blk[lb].roff * nd, nd, 0, e->coef * v});
                 }
             }
             if ((int)ms.size() == s0) continue;
@@ -616,6 +641,85 @@ void EnvPlan::build_left(const MPO& W, int site, const EnvT& L, const SiteT& Abr
         for (; z < zb.size() && zb[z].nb == nbi; ++z)
             g2.op(Abra.ptr(Abra.blk[zb[z].bb]), md, Zp + zb[z].off, nd, zb[z].rows, 1, 1.0);
         g2.block(Lnew.ptr(nb), nd, md, nd, 0, m0);
+    }
+    upload_mix(st);
+}
+
+RunMaps::RunMaps(const MPO& W_) : W(W_) {
+    out.resize(W.nsite);
+    for (int s = 0; s < W.nsite; ++s) {
+        out[s].resize(W.dim[s]);
+        for (const auto& e : W.W[s]) {
+            const double v = W.ops[e.op][0];   // <0|o|0>
+            if (v != 0.0) out[s][e.a].push_back({e.b, e.coef * v});
+        }
+    }
+}
+
+const RunMap& RunMaps::get(int s0, int s1) {
+    require(s0 >= 0 && s0 < s1 && s1 <= W.nsite, "run of empty sites out of range");
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = maps.find({s0, s1});
+        if (it != maps.end()) return *it->second;
+    }
+    // propagate every source state through the run (frontiers are short:
+    // an operator string either passes an empty site unchanged or dies)
+    std::vector<std::vector<std::pair<int, double>>> to(W.dim[s1]);
+    std::vector<std::pair<int, double>> cur, nxt;
+    for (int a = 0; a < W.dim[s0]; ++a) {
+        cur.assign(1, {a, 1.0});
+        for (int s = s0; s < s1 && !cur.empty(); ++s) {
+            nxt.clear();
+            for (const auto& xw : cur)
+                for (const auto& bc : out[s][xw.first]) nxt.push_back({bc.first, xw.second * bc.second});
+            if (nxt.size() > 1) {   // merge paths that meet (sum in path order)
+                std::stable_sort(nxt.begin(), nxt.end(),
+                                 [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
+                                     return x.first < y.first;
+                                 });
+                size_t w = 0;
+                for (size_t r = 0; r < nxt.size(); ++r) {
+                    if (w > 0 && nxt[w - 1].first == nxt[r].first) nxt[w - 1].second += nxt[r].second;
+                    else nxt[w++] = nxt[r];
+                }
+                nxt.resize(w);
+            }
+            cur.swap(nxt);
+        }
+        for (const auto& bw : cur)
+            if (bw.second != 0.0) to[bw.first].push_back({a, bw.second});
+    }
+    std::unique_ptr<RunMap> m(new RunMap);
+    m->ptr.assign(W.dim[s1] + 1, 0);
+    for (int b = 0; b < W.dim[s1]; ++b) {
+        m->ptr[b + 1] = m->ptr[b] + (int)to[b].size();
+        for (const auto& aw : to[b]) {
+            m->col.push_back(aw.first);
+            m->val.push_back(aw.second);
+        }
+    }
+    std::lock_guard<std::mutex> g(mu);
+    auto& slot = maps[{s0, s1}];
+    if (!slot) slot = std::move(m);
+    return *slot;
+}
+
+void EnvPlan::build_left_run(const RunMap& T, const EnvT& L, const Bond& bra, const Bond& ket, EnvT& Lnew,
+                             cudaStream_t st) {
+    g1.clear();
+    g2.clear();
+    mt.clear();
+    ms.clear();
+    for (const auto& nb : Lnew.blk) {
+        const int rows = bra.sec[nb.sb].dim, cols = ket.sec[nb.sk].dim;
+        const int s0 = (int)ms.size();
+        for (int q = T.ptr[nb.a]; q < T.ptr[nb.a + 1]; ++q) {
+            const int lb = L.find(T.col[q], nb.sk);
+            if (lb < 0 || L.blk[lb].sb != nb.sb) continue;
+            ms.push_back({L.ptr(L.blk[lb]), cols, 0, T.val[q]});
+        }
+        mt.push_back({Lnew.ptr(nb), rows, cols, cols, s0, (int)ms.size(), 0});
     }
     upload_mix(st);
 }
@@ -649,27 +753,33 @@ void EnvPlan::build_right(const MPO& W, int site, const EnvT& R, const SiteT& Ab
         g1.block(Yp + yoff[kb], P, md, P, 0, m0);
     }
     // mix: Z_(out, s) = sum over e = (a -> b), t of W_ab(s, t) Y_(b, kb(t)), dim(sk) x dim(sr_b)
-    std::vector<std::vector<const MpoEntry*>> by_a(W.dim[site]);
-    for (const auto& e : W.W[site]) by_a[e.a].push_back(&e);
+    const std::vector<MpoEntry>& We = W.W[site];
+    const std::vector<int>& out_ptr = W.out_ptr[site];
     struct ZB { int nb, s, bb; size_t off; int rows, cols; };
     std::vector<ZB> zb;
     size_t zs = 0;
     for (int nbi = 0; nbi < (int)Rnew.blk.size(); ++nbi) {
         const auto& nbk = Rnew.blk[nbi];
         const int nd = ketL.sec[nbk.sk].dim;
+        int kb_t[4];   // ket-side lookups depend on t only
+        for (int t = 0; t < 4; ++t) {
+            kb_t[t] = Aket.find(nbk.sk, t);
+            if (kb_t[t] >= 0 && yoff[kb_t[t]] < 0) kb_t[t] = -1;
+        }
         for (int s = 0; s < 4; ++s) {
             const int bb = Abra.find(nbk.sb, s);
             if (bb < 0) continue;
             const int srb = Abra.blk[bb].sr;
             const int cols = braR.sec[srb].dim;
             const int s0 = (int)ms.size();
-            for (const MpoEntry* e : by_a[nbk.a]) {
+            for (int q = out_ptr[nbk.a]; q < out_ptr[nbk.a + 1]; ++q) {
+                const MpoEntry* e = &We[q];
                 const Mat4& op = W.ops[e->op];
                 for (int t = 0; t < 4; ++t) {
                     const double v = op[s * 4 + t];
                     if (v == 0.0) continue;
-                    const int kb = Aket.find(nbk.sk, t);
-                    if (kb < 0 || yoff[kb] < 0) continue;
+                    const int kb = kb_t[t];
+                    if (kb < 0) continue;
                     const int srk = Aket.blk[kb].sr;
                     const int rb = R.find(e->b, srk);
                     if (rb < 0 || R.blk[rb].sb != srb) continue;

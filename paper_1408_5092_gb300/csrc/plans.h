@@ -1,6 +1,7 @@
 // Planner: turns each contraction of the sweep into device task lists.
 #pragma once
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -28,7 +29,19 @@ struct Autotuner {
     std::mutex mu;
     std::map<Key, std::pair<int, int>> best;
     long long timed = 0, reused = 0;
-    DBuf scratch, dtasks;
+    // Scratch outputs and task list of the timing launches.  Plans on any
+    // lane call the tuner, and a lane's stream ends with its call, so these
+    // are plain (not stream-ordered) allocations that outlive every lane.
+    // A buffer that has to grow is kept (freed with the tuner) rather than
+    // freed while other lanes may be capturing graphs.
+    struct RawBuf {
+        void* p = nullptr;
+        size_t n = 0;
+        std::vector<void*> old;
+        void ensure(size_t bytes);
+        ~RawBuf();
+    };
+    RawBuf scratch, dtasks;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     ~Autotuner();
     // (tm, tn) for the plan (its blocks recorded, its ops uploaded)
@@ -171,6 +184,30 @@ void plan_product(GemmPlan& g, const TwoT& x, double* xd, const Bond& mid, const
 //        (right update: Y_kb = A_ket(kb) R_panel^T)
 //   mix: Z_(out, s) = sum over MPO entries and t of W_ab(s, t) Y_(a, kb(t))
 //   g2:  L_new(out) = sum_s A_bra(s)^T Z_(out, s)          (<= 4 products)
+// Transfer of MPO states across a run of sites [s0, s1) on which bra and ket
+// are both empty (identity sites, local state |0>): only the <0|o|0>
+// element of each site operator acts, so the run is a sparse linear map of
+// the MPO states at cut s0 to those at cut s1 (a state that needs a creator
+// or annihilator on the run dies; the rest pass with their coefficients).
+// CSR over the target states: sources of b are col[ptr[b] .. ptr[b+1]).
+struct RunMap {
+    std::vector<int> ptr, col;
+    std::vector<double> val;
+};
+
+// Run maps of one MPO, computed on first use and shared by threads.
+class RunMaps {
+  public:
+    explicit RunMaps(const MPO& W);
+    const RunMap& get(int s0, int s1);
+
+  private:
+    const MPO& W;
+    std::vector<std::vector<std::vector<std::pair<int, double>>>> out;   // site, a -> (b, coef <0|o|0>)
+    std::mutex mu;
+    std::map<std::pair<int, int>, std::unique_ptr<RunMap>> maps;
+};
+
 struct EnvPlan {
     GemmPlan g1, g2;
     void set_tuner(Autotuner* t) { g1.tuner = t; g2.tuner = t; }
@@ -183,12 +220,23 @@ struct EnvPlan {
     void build_right(const MPO& W, int site, const EnvT& R, const SiteT& Abra, const SiteT& Aket,
                      const Bond& braL, const Bond& ketL, const Bond& braR, const Bond& ketR,
                      EnvT& Rnew, cudaStream_t st);
+    // L_new = L carried across a run of empty sites (one mix launch; the
+    // bonds do not change across the run).
+    void build_left_run(const RunMap& T, const EnvT& L, const Bond& bra, const Bond& ket, EnvT& Lnew,
+                        cudaStream_t st);
     void run(cudaStream_t st) const {
         g1.run(st);
         launch_mix(dmt.as<MixTask>(), (int)mt.size(), dms.as<MixSrc>(), st);
         g2.run(st);
     }
     double flops() const { return g1.flops + g2.flops; }
+    // bytes of the task lists the last build uploads (GEMM tasks and operand
+    // lists, mix tasks and sources)
+    size_t plan_bytes() const {
+        return mt.size() * sizeof(MixTask) + ms.size() * sizeof(MixSrc) +
+               (g1.tasks.size() + g2.tasks.size()) * sizeof(GemmTask) +
+               (g1.ops.size() + g2.ops.size()) * sizeof(GemmOp);
+    }
 
   private:
     void upload_mix(cudaStream_t st);

@@ -48,7 +48,12 @@ struct EnvT {
     int nsk = 0;
     size_t n = 0;
     DBuf d;
-    void build(const std::vector<QN>& dq, const Bond& bra, const Bond& ket, cudaStream_t st) {
+    // live (optional): MPO states whose blocks exist; the others are known
+    // to be zero and are left out (find() returns -1 for them).  reuse: keep
+    // the device buffer when it is large enough (stream-ordered reuse by a
+    // caller that launches on one stream) instead of a fresh allocation.
+    void build(const std::vector<QN>& dq, const Bond& bra, const Bond& ket, cudaStream_t st,
+               const std::vector<char>* live = nullptr, bool reuse = false) {
         blk.clear();
         nsk = ket.nsec();
         idx.assign(dq.size() * (size_t)nsk, -1);
@@ -58,6 +63,7 @@ struct EnvT {
         for (int sk = 0; sk < nsk; ++sk) {
             poff[sk] = n;
             for (int a = 0; a < (int)dq.size(); ++a) {
+                if (live && !(*live)[a]) continue;
                 int sb = bra.find(ket.sec[sk].q + dq[a]);
                 if (sb < 0) continue;
                 idx[(size_t)a * nsk + sk] = (int)blk.size();
@@ -66,7 +72,8 @@ struct EnvT {
                 prows[sk] += bra.sec[sb].dim;
             }
         }
-        d.alloc(n * sizeof(double) + 8, st);
+        if (reuse) d.ensure(n * sizeof(double) + 8, st);
+        else d.alloc(n * sizeof(double) + 8, st);
     }
     int find(int a, int sk) const { return idx[(size_t)a * nsk + sk]; }
     double* ptr(const B& b) const { return d.as<double>() + b.off; }

@@ -87,3 +87,28 @@ def test_partitions_with_graphs(L):
         L.mpspt_destroy(ctx)
     assert np.array_equal(out[0][1], out[1][1]) and out[0][0] == out[1][0]
     assert out[1][2] < out[0][2]
+
+
+def test_partitions_with_autotune_and_graphs(L, tmp_path):
+    """Partition lanes share the context's tile tuner (its timing buffers
+    outlive the lanes' streams): tuned and untuned partition energies agree
+    bit for bit, the context is destroyed cleanly after the lanes are gone,
+    and a second context reads the tuned table back."""
+    h, Lc, c, ci = synthetic.config_reference("medium")
+    pairs = [(0, 0), (0, 5), (3, 17), (23, 23)]
+    cache = str(tmp_path / "tiles.txt")
+    out = []
+    for tune in (0, 1, 1):
+        o = L.mpspt_default_options()
+        o.cuda_graphs = 1
+        o.autotune = tune
+        if tune:
+            o.autotune_cache = cache.encode()
+        ctx = L.mpspt_create(o)
+        L.mpspt_set_integrals(ctx, c["k_act"], h.shape[0] - c["k_act"], c["n_elec"], h, Lc)
+        L.mpspt_set_reference_ci(ctx, ci)
+        tot, ep, _ = L.mpspt_minimize_partitioned(ctx, "fock", pairs, [16] * len(pairs), n_streams=4)
+        out.append(ep.copy())
+        L.mpspt_destroy(ctx)
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    assert os.path.getsize(cache) > 0
