@@ -270,6 +270,14 @@ def run_gpu(args):
     o.prec = L.PREC[args.prec]
     o.e_tol = args.e_tol
     o.max_sweeps = args.max_sweeps
+    # tuned GEMM tiles for the mixed arm: the warm-up context tunes, its table
+    # goes to a cache file when it is destroyed, and the end-to-end contexts
+    # read it back (the plain float64 arm keeps the default tiles)
+    import tempfile
+    tune_dir = tempfile.mkdtemp(prefix="mpspt_tiles_")
+    tune_cache = os.path.join(tune_dir, "tiles.txt").encode()
+    o.autotune = 1 if args.autotune else 0
+    o.autotune_cache = tune_cache if args.autotune else None
     ctx = L.mpspt_create(o)
     L.mpspt_set_integrals(ctx, c["k_act"], k - c["k_act"], c["n_elec"], h, Lc)
     L.mpspt_set_reference_ci(ctx, ci)
@@ -336,6 +344,8 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         value, ms_per_step = float(t[0]), float(t[1])
         dist.barrier()
+    L.mpspt_destroy(ctx)      # writes the tuned tile table for the end-to-end contexts
+    ctx = None
     # end to end through the public API: wall clock from mpspt_create to the
     # return of mpspt_minimize_hylleraas (integrals and CI vector copied from
     # host buffers, E2 read back), median of e2e_steps runs
@@ -379,6 +389,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "bf16x3+f64", "mixed_fp16": "f16x3+f64"}[args.prec],
         "data": "synthetic",
         "config": {"workload": _workload(args), "h0": args.h0, "M": args.M, "prec": args.prec, "l2_flush": True,
+                   "tuned_tiles": bool(args.autotune),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "E2": statistics.median(e2s), "E2_ref": e2_ref,
         "sweeps": [r.n_sweeps for r in reps],
@@ -397,7 +408,8 @@ def run_gpu(args):
         "roofline_fp64_sigma": _fp64_roofline(reps, peaks, src),
         "e2e": {"value": e2e, "unit": "s", "runs": args.e2e_steps,
                 "what": "wall clock mpspt_create -> set_integrals -> set_reference_ci -> minimize_hylleraas "
-                        "(to the e_tol stop) -> return, host buffers",
+                        "(to the e_tol stop) -> return, host buffers"
+                        + (", tile table read from the warm-up context's cache file" if args.autotune else ""),
                 "h2d_bytes_per_step": int(h.nbytes + Lc.nbytes + ci.nbytes), "d2h_bytes_per_step": 8},
         "gpu_launches": int(sum(r.kernel_launches for r in reps)),
         "clocks": clocks,
@@ -418,7 +430,6 @@ def run_gpu(args):
                                 "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    L.mpspt_destroy(ctx)
     if dist:
         dist.destroy_process_group()
 
@@ -436,6 +447,8 @@ def main():
     ap.add_argument("--e_tol", type=float, default=1e-7)
     ap.add_argument("--ref_e_tol", type=float, default=1e-9)
     ap.add_argument("--e2e_steps", type=int, default=3)
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="tuned GEMM tiles in the mixed arm (tuned during warm-up, cached for the e2e runs)")
     ap.add_argument("--fp64_steps", type=int, default=3,
                     help="timed repeats of the plain float64 arm (at most --steps)")
     ap.add_argument("--write_counts", action="store_true",

@@ -361,8 +361,8 @@ mpspt_status mpspt_set_preconditioner(mpspt_ctx* ctx, const mpspt_mlp* net);
 mpspt_status mpspt_train_preconditioner(mpspt_ctx* ctx, mpspt_h0 h0, int M, int max_samples, int epochs,
                                         const char* harvest_path, float* loss);
 
-/* The float64 eigensolver of the truncation step (row "a8": density-matrix
- * sectors rho_q = X_q X_q^T, paper text on the renormalisation step) on
+/* The float64 eigensolver of the truncation step (density-matrix sectors
+ * rho_q = X_q X_q^T, paper text on the renormalisation step) on
  * caller data: batched cyclic Jacobi with round-robin parallel rotations.
  * Device pointers; the batch's matrices are stored back to back: matrix i
  * has size n[i] (host array, 1 <= n[i] <= 2048) and starts at offset
