@@ -1,6 +1,10 @@
 // Matrix product operators (Eq. 4) built from second-quantised term lists.
 #pragma once
 #include <array>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "core.h"
@@ -42,6 +46,30 @@ struct MPO {
 // Builds the MPO of sum(terms) on nsite sites.  Sites >= k_split are the
 // "virtual" region (the centre rule differs there, see mpo.cpp).
 MPO build_mpo(const std::vector<Term>& terms, int nsite, int k_split);
+
+// Transfer of MPO states across a run of sites [s0, s1) on which bra and ket
+// are both empty (identity sites, local state |0>): only the <0|o|0>
+// element of each site operator acts, so the run is a sparse linear map of
+// the MPO states at cut s0 to those at cut s1 (a state that needs a creator
+// or annihilator on the run dies; the rest pass with their coefficients).
+// CSR over the target states: sources of b are col[ptr[b] .. ptr[b+1]).
+struct RunMap {
+    std::vector<int> ptr, col;
+    std::vector<double> val;
+};
+
+// Run maps of one MPO, computed on first use and shared by threads.
+class RunMaps {
+  public:
+    explicit RunMaps(const MPO& W);
+    const RunMap& get(int s0, int s1);
+
+  private:
+    const MPO& W;
+    std::vector<std::vector<std::vector<std::pair<int, double>>>> out;   // site, a -> (b, coef <0|o|0>)
+    std::mutex mu;
+    std::map<std::pair<int, int>, std::unique_ptr<RunMap>> maps;
+};
 
 // Term generators (orbital index = site index).
 void add_one_body(std::vector<Term>& out, const std::vector<double>& t, int k,

@@ -645,66 +645,6 @@ void EnvPlan::build_left(const MPO& W, int site, const EnvT& L, const SiteT& Abr
     upload_mix(st);
 }
 
-RunMaps::RunMaps(const MPO& W_) : W(W_) {
-    out.resize(W.nsite);
-    for (int s = 0; s < W.nsite; ++s) {
-        out[s].resize(W.dim[s]);
-        for (const auto& e : W.W[s]) {
-            const double v = W.ops[e.op][0];   // <0|o|0>
-            if (v != 0.0) out[s][e.a].push_back({e.b, e.coef * v});
-        }
-    }
-}
-
-const RunMap& RunMaps::get(int s0, int s1) {
-    require(s0 >= 0 && s0 < s1 && s1 <= W.nsite, "run of empty sites out of range");
-    {
-        std::lock_guard<std::mutex> g(mu);
-        auto it = maps.find({s0, s1});
-        if (it != maps.end()) return *it->second;
-    }
-    // propagate every source state through the run (frontiers are short:
-    // an operator string either passes an empty site unchanged or dies)
-    std::vector<std::vector<std::pair<int, double>>> to(W.dim[s1]);
-    std::vector<std::pair<int, double>> cur, nxt;
-    for (int a = 0; a < W.dim[s0]; ++a) {
-        cur.assign(1, {a, 1.0});
-        for (int s = s0; s < s1 && !cur.empty(); ++s) {
-            nxt.clear();
-            for (const auto& xw : cur)
-                for (const auto& bc : out[s][xw.first]) nxt.push_back({bc.first, xw.second * bc.second});
-            if (nxt.size() > 1) {   // merge paths that meet (sum in path order)
-                std::stable_sort(nxt.begin(), nxt.end(),
-                                 [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
-                                     return x.first < y.first;
-                                 });
-                size_t w = 0;
-                for (size_t r = 0; r < nxt.size(); ++r) {
-                    if (w > 0 && nxt[w - 1].first == nxt[r].first) nxt[w - 1].second += nxt[r].second;
-                    else nxt[w++] = nxt[r];
-                }
-                nxt.resize(w);
-            }
-            cur.swap(nxt);
-        }
-        for (const auto& bw : cur)
-            if (bw.second != 0.0) to[bw.first].push_back({a, bw.second});
-    }
-    std::unique_ptr<RunMap> m(new RunMap);
-    m->ptr.assign(W.dim[s1] + 1, 0);
-    for (int b = 0; b < W.dim[s1]; ++b) {
-        m->ptr[b + 1] = m->ptr[b] + (int)to[b].size();
-        for (const auto& aw : to[b]) {
-            m->col.push_back(aw.first);
-            m->val.push_back(aw.second);
-        }
-    }
-    std::lock_guard<std::mutex> g(mu);
-    auto& slot = maps[{s0, s1}];
-    if (!slot) slot = std::move(m);
-    return *slot;
-}
-
 void EnvPlan::build_left_run(const RunMap& T, const EnvT& L, const Bond& bra, const Bond& ket, EnvT& Lnew,
                              cudaStream_t st) {
     g1.clear();

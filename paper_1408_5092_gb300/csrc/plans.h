@@ -184,30 +184,6 @@ void plan_product(GemmPlan& g, const TwoT& x, double* xd, const Bond& mid, const
 //        (right update: Y_kb = A_ket(kb) R_panel^T)
 //   mix: Z_(out, s) = sum over MPO entries and t of W_ab(s, t) Y_(a, kb(t))
 //   g2:  L_new(out) = sum_s A_bra(s)^T Z_(out, s)          (<= 4 products)
-// Transfer of MPO states across a run of sites [s0, s1) on which bra and ket
-// are both empty (identity sites, local state |0>): only the <0|o|0>
-// element of each site operator acts, so the run is a sparse linear map of
-// the MPO states at cut s0 to those at cut s1 (a state that needs a creator
-// or annihilator on the run dies; the rest pass with their coefficients).
-// CSR over the target states: sources of b are col[ptr[b] .. ptr[b+1]).
-struct RunMap {
-    std::vector<int> ptr, col;
-    std::vector<double> val;
-};
-
-// Run maps of one MPO, computed on first use and shared by threads.
-class RunMaps {
-  public:
-    explicit RunMaps(const MPO& W);
-    const RunMap& get(int s0, int s1);
-
-  private:
-    const MPO& W;
-    std::vector<std::vector<std::vector<std::pair<int, double>>>> out;   // site, a -> (b, coef <0|o|0>)
-    std::mutex mu;
-    std::map<std::pair<int, int>, std::unique_ptr<RunMap>> maps;
-};
-
 struct EnvPlan {
     GemmPlan g1, g2;
     void set_tuner(Autotuner* t) { g1.tuner = t; g2.tuner = t; }

@@ -1,8 +1,13 @@
 // Host-only check of the library's MPO builder: reads integrals, builds the
 // MPO of one operator with the library's term generators, contracts it to a
 // dense 4^k x 4^k matrix and writes it out.  Used by tests/test_host_mpo.py.
-// usage: mpo_dense <in.bin> <out.bin>   (in: k ka which eps[k] h[k*k] eri[k^4] e0)
+// usage: mpo_dense <in.bin> <out.bin> [mask]   (in: k ka which eps[k] h[k*k] eri[k^4] e0)
+// mask: one character per site, '1' = the site is held empty (local state
+// |0> on both sides).  Each run of such sites is applied with the library's
+// run maps (RunMaps) instead of site by site, and the output is the operator
+// on the other sites' 4^(k - #empty) space.
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "../../paper_1408_5092_gb300/csrc/mpo.h"
@@ -10,7 +15,7 @@
 using namespace mpspt;
 
 int main(int argc, char** argv) {
-    if (argc != 3) return 2;
+    if (argc != 3 && argc != 4) return 2;
     FILE* f = std::fopen(argv[1], "rb");
     if (!f) return 3;
     int hdr[3];
@@ -41,10 +46,28 @@ int main(int argc, char** argv) {
         add_two_body(t, eri, k, 0, k, 0, k, -1);
     }
     MPO W = build_mpo(t, k, ka);
-    // dense contraction: T[a] is 4^c x 4^c
+    std::vector<char> empty(k, 0);
+    if (argc == 4) {
+        if ((int)std::strlen(argv[3]) != k) return 6;
+        for (int p = 0; p < k; ++p) empty[p] = argv[3][p] == '1';
+    }
+    RunMaps rm(W);
+    // dense contraction: T[a] is 4^c x 4^c (c = sites that are not held empty)
     std::vector<std::vector<double>> T(1, std::vector<double>(1, 1.0));
     int dim = 1;
-    for (int p = 0; p < k; ++p) {
+    for (int p = 0; p < k;) {
+        if (empty[p]) {   // a run [p, q): T_new[b] = sum_a map(a -> b) T[a]
+            int q = p + 1;
+            while (q < k && empty[q]) ++q;
+            const RunMap& R = rm.get(p, q);
+            std::vector<std::vector<double>> Tn(W.dim[q], std::vector<double>((size_t)dim * dim, 0.0));
+            for (int b = 0; b < W.dim[q]; ++b)
+                for (int r = R.ptr[b]; r < R.ptr[b + 1]; ++r)
+                    for (size_t x = 0; x < Tn[b].size(); ++x) Tn[b][x] += R.val[r] * T[R.col[r]][x];
+            T.swap(Tn);
+            p = q;
+            continue;
+        }
         std::vector<std::vector<double>> Tn(W.dim[p + 1]);
         const int nd = dim * 4;
         for (auto& v : Tn) v.assign((size_t)nd * nd, 0.0);
@@ -63,6 +86,7 @@ int main(int argc, char** argv) {
         }
         T.swap(Tn);
         dim = nd;
+        ++p;
     }
     FILE* g = std::fopen(argv[2], "wb");
     int d[2] = {dim, (int)W.dim.size()};
