@@ -45,14 +45,15 @@ def test_partition_sweep_reaches_exact(tiny, pair):
     assert abs(sw.run() - e_ex) < 1e-10
 
 
-def test_partition_e3_exact_limit_is_the_full_space_e3(tiny):
+@pytest.mark.parametrize("h0", ["fock", "dyall"])
+def test_partition_e3_exact_limit_is_the_full_space_e3(tiny, h0):
     """Eq. 5 for the sum of the exact partition solutions: the embedded
     vectors add up to the full-space Psi1*, their E3 is the full-space E3*,
     the cross-partition part is a sizeable share of it (so a dropped cross
     term fails), and distinct partitions are orthogonal with no H0 coupling."""
     from oracle.partition import e3_split, embed_vector
     h, L, c, ci = tiny
-    p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0="fock")
+    p = Problem(h, L, c["k_act"], c["n_elec"], ci, h0=h0)
     ex = ExactFirstOrder(p)
     ex.solve()
     xs = []
