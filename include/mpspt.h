@@ -401,9 +401,10 @@ mpspt_status mpspt_eigh_batched_ex(int device, void* stream, int batch, const in
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any
  * stream capture.  The caller's current device is restored before return.
- * All calls share the array and each overwrites what it uses: calls whose
- * GPU work overlaps (other streams, other host threads) race on it and must
- * be serialised by the caller. */
+ * All calls share the array and each writes every part of it that it reads
+ * (task table and matrix copy) before reading it, so nothing in it has to
+ * start at zero.  Calls whose GPU work overlaps (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
 mpspt_status mpspt_eigh_batched_noalloc(int device, void* stream, int batch, const int* n,
                                         const double* A, double* V, double* w);
 
